@@ -1,0 +1,216 @@
+"""FP64 CPU oracle for the MPBP loss and gradient (arXiv 2312.14907).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` use it; the product path never imports it.
+
+The arithmetic lives in ``mpbp_oracle.c`` (plain C, double precision, direct
+DFT, one OpenMP loop over frames); this module compiles it with gcc and calls
+it through ctypes with NumPy arrays.  It shares no code with the CUDA path.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mpbp_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force=False):
+    """Compile liboracle.so with gcc (-O2, IEEE arithmetic, OpenMP)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + ".%d.tmp" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp", "-fno-fast-math",
+           _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("n1", ctypes.c_int), ("n2", ctypes.c_int), ("ncomp", ctypes.c_int),
+                ("npeaks", ctypes.c_int), ("m", ctypes.c_int), ("nscan", ctypes.c_int),
+                ("G", ctypes.POINTER(ctypes.c_double)), ("scan", ctypes.POINTER(ctypes.c_int)),
+                ("phase_scale", ctypes.c_double), ("probe_per_peak", ctypes.c_int)]
+
+
+class StepParams(ctypes.Structure):
+    _fields_ = [("c_armijo", ctypes.c_double), ("grow", ctypes.c_double),
+                ("shrink", ctypes.c_double), ("t0", ctypes.c_double),
+                ("w_rho", ctypes.c_double), ("w_u", ctypes.c_double),
+                ("w_alpha", ctypes.c_double)]
+
+
+class StepState(ctypes.Structure):
+    _fields_ = [("f_prev", ctypes.c_double), ("gn2_prev", ctypes.c_double),
+                ("t", ctypes.c_double), ("f_last", ctypes.c_double),
+                ("k", ctypes.c_int), ("accepted", ctypes.c_int),
+                ("n_accept", ctypes.c_int), ("n_reject", ctypes.c_int)]
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        pp = ctypes.POINTER(Problem)
+        lib.oracle_dft2.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int]
+        lib.oracle_dft2.restype = None
+        lib.oracle_object_build.argtypes = [pp, dp, dp, dp, dp]
+        lib.oracle_object_build.restype = None
+        lib.oracle_forward.argtypes = [pp, dp, dp, dp, dp, dp, dp]
+        lib.oracle_forward.restype = None
+        lib.oracle_loss_grad.argtypes = [pp, dp, dp, dp, dp, dp, dp, ip, ctypes.c_int,
+                                         dp, dp, dp, dp, ctypes.c_int]
+        lib.oracle_loss_grad.restype = ctypes.c_double
+        lib.oracle_step.argtypes = [pp, dp, dp, dp, ctypes.POINTER(StepParams),
+                                    ctypes.POINTER(StepState), dp, dp, dp, dp, dp, dp,
+                                    dp, dp, dp, ctypes.c_int]
+        lib.oracle_step.restype = None
+        lib.oracle_max_threads.argtypes = []
+        lib.oracle_max_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _d(a):
+    """Contiguous float64 copy (complex arrays become interleaved pairs)."""
+    a = np.asarray(a)
+    if np.iscomplexobj(a):
+        a = np.ascontiguousarray(a, dtype=np.complex128).view(np.float64)
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _c(a):
+    """Contiguous complex128 array viewed as interleaved float64 pairs."""
+    return np.ascontiguousarray(a, dtype=np.complex128).view(np.float64)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def max_threads():
+    return _load().oracle_max_threads()
+
+
+def dft2(x, sign=-1):
+    """Direct unnormalised 2-D DFT of a square complex array; sign -1 = F, +1 = F^H."""
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.complex128)
+    m = x.shape[0]
+    assert x.shape == (m, m)
+    out = np.empty_like(x)
+    lib.oracle_dft2(m, _ptr(x.view(np.float64)), _ptr(out.view(np.float64)), int(sign))
+    return out
+
+
+class OracleProblem:
+    """Geometry of one MPBP problem (see mpbp_oracle.c for the layouts)."""
+
+    def __init__(self, n1, n2, ncomp, npeaks, m, scan, G, phase_scale=2 * np.pi,
+                 probe_per_peak=False):
+        self.G = _d(G).reshape(npeaks, ncomp)
+        self.scan = np.ascontiguousarray(scan, dtype=np.int32).reshape(-1, 2)
+        self.shape = (n1, n2)
+        self.ncomp, self.npeaks, self.m = ncomp, npeaks, m
+        self.nscan = self.scan.shape[0]
+        self.phase_scale = float(phase_scale)
+        self.probe_per_peak = bool(probe_per_peak)
+        self.c = Problem(n1, n2, ncomp, npeaks, m, self.nscan,
+                         _ptr(self.G), self.scan.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                         self.phase_scale, int(probe_per_peak))
+
+    @classmethod
+    def from_spec(cls, spec, scan):
+        return cls(spec.n1, spec.n2, spec.ncomp, spec.npeaks, spec.m, scan, spec.G,
+                   spec.phase_scale, spec.probe_per_peak)
+
+    @property
+    def nframes(self):
+        return self.npeaks * self.nscan
+
+    def object_build(self, rho, u, alpha):
+        lib = _load()
+        n1, n2 = self.shape
+        rho, u, alpha = _d(rho), _d(u), _d(alpha)
+        out = np.empty((self.npeaks, n1, n2), np.complex128)
+        lib.oracle_object_build(ctypes.byref(self.c), _ptr(rho), _ptr(u), _ptr(alpha),
+                                _ptr(out.view(np.float64)))
+        return out
+
+    def forward(self, rho, u, alpha, probe, bg=None):
+        lib = _load()
+        rho, u, alpha, probe = _d(rho), _d(u), _d(alpha), _c(probe)
+        bg = None if bg is None else _d(bg)
+        out = np.empty((self.npeaks, self.nscan, self.m, self.m), np.float64)
+        lib.oracle_forward(ctypes.byref(self.c), _ptr(rho), _ptr(u), _ptr(alpha),
+                           _ptr(probe), _ptr(bg), _ptr(out))
+        return out
+
+    def loss_grad(self, rho, u, alpha, probe, y, bg=None, frames=None, nthreads=0,
+                  frame_loss=False):
+        """Returns (loss, g_rho, g_u, g_alpha[, per-frame losses])."""
+        lib = _load()
+        n1, n2 = self.shape
+        rho, u, alpha, probe, y = _d(rho), _d(u), _d(alpha), _c(probe), _d(y)
+        bg = None if bg is None else _d(bg)
+        g_rho = np.empty((n1, n2))
+        g_u = np.empty((self.ncomp, n1, n2))
+        g_alpha = np.empty(self.npeaks)
+        fr = None
+        nfr = 0
+        if frames is not None:
+            fr = np.ascontiguousarray(frames, dtype=np.int32)
+            nfr = fr.size
+        fl = np.empty(nfr if fr is not None else self.nframes) if frame_loss else None
+        loss = lib.oracle_loss_grad(
+            ctypes.byref(self.c), _ptr(rho), _ptr(u), _ptr(alpha), _ptr(probe), _ptr(bg),
+            _ptr(y), None if fr is None else fr.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+            nfr, _ptr(g_rho), _ptr(g_u), _ptr(g_alpha), _ptr(fl), int(nthreads))
+        if frame_loss:
+            return loss, g_rho, g_u, g_alpha, fl
+        return loss, g_rho, g_u, g_alpha
+
+    def loss(self, rho, u, alpha, probe, y, bg=None, nthreads=0):
+        return self.loss_grad(rho, u, alpha, probe, y, bg=bg, nthreads=nthreads)[0]
+
+
+class OracleStepper:
+    """Lagged-Armijo gradient descent in FP64 (see oracle_step in mpbp_oracle.c)."""
+
+    def __init__(self, problem, probe, y, bg=None, c_armijo=1e-4, grow=1.25, shrink=0.5,
+                 t0=1.0, w_rho=1.0, w_u=1.0, w_alpha=1.0, nthreads=0):
+        self.p = problem
+        self.probe, self.y = _c(probe), _d(y)
+        self.bg = None if bg is None else _d(bg)
+        self.params = StepParams(c_armijo, grow, shrink, t0, w_rho, w_u, w_alpha)
+        self.state = StepState(0.0, 0.0, t0, 0.0, 0, 0, 0, 0)
+        n1, n2 = problem.shape
+        self.rho_prev = np.zeros((n1, n2))
+        self.u_prev = np.zeros((problem.ncomp, n1, n2))
+        self.alpha_prev = np.zeros(problem.npeaks)
+        self.grho_prev = np.zeros((n1, n2))
+        self.gu_prev = np.zeros((problem.ncomp, n1, n2))
+        self.galpha_prev = np.zeros(problem.npeaks)
+        self.nthreads = nthreads
+
+    def step(self, rho, u, alpha):
+        """Updates rho, u, alpha (float64 arrays) in place; returns the loss evaluated."""
+        lib = _load()
+        for a in (rho, u, alpha):
+            assert a.dtype == np.float64 and a.flags.c_contiguous
+        lib.oracle_step(ctypes.byref(self.p.c), _ptr(self.probe), _ptr(self.bg), _ptr(self.y),
+                        ctypes.byref(self.params), ctypes.byref(self.state),
+                        _ptr(rho), _ptr(u), _ptr(alpha), _ptr(self.rho_prev), _ptr(self.u_prev),
+                        _ptr(self.alpha_prev), _ptr(self.grho_prev), _ptr(self.gu_prev),
+                        _ptr(self.galpha_prev), int(self.nthreads))
+        return self.state.f_last

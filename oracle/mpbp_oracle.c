@@ -1,0 +1,416 @@
+/*
+ * mpbp_oracle.c -- plain FP64 CPU oracle for the multi-peak Bragg
+ * ptychography (MPBP) loss and gradient (Kandel et al., arXiv 2312.14907).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the independent reference that the
+ * CUDA path is checked against.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load it; the product library never does.
+ * It shares no code, header, table or helper with the CUDA sources.
+ *
+ * What it computes, in the paper's notation (thin-membrane form, R = identity):
+ *   Eq. 1 / Eq. 3   O_m(r)   = alpha_m rho(r) exp(i phi_m(r)),
+ *                   phi_m(r) = phase_scale * sum_c G_{m,c} u_c(r)
+ *                   (phase_scale = 2 pi reproduces the exponent 2 pi i u.G).
+ *   Eq. 2           I_{m,j}  = | F diag(P_m) S_j O_m |^2 + b_{m,j}
+ *                   S_j: integer shift, z(k) = O_m(s_j + k), zero outside the
+ *                   grid; F: unnormalised 2-D DFT with kernel exp(-2 pi i q.k/M),
+ *                   evaluated here as a direct separable sum (no FFT).
+ *   Eq. 4           f = 1/2 sum_{m,j,q} ( sqrt(I) - sqrt(y) )^2
+ *   gradient of Eq. 4 with respect to rho, u and alpha (what Alg. 1 feeds its
+ *   optimizer), by the chain rule through Eq. 2 and Eq. 3:
+ *     chi  = (sqrt(I) - sqrt(y)) Psi / sqrt(I)      (chi = 0 where I = 0)
+ *     ghat = F^H chi                                (conjugate transpose DFT)
+ *     g    = conj(P) ghat
+ *     df/drho(r)   += alpha_m Re( conj(g) e^{i phi_m(r)} )
+ *     df/dphi_m(r) += -Im( conj(g) O_m(r) )
+ *     df/dalpha_m  += Re( conj(g) rho(r) e^{i phi_m(r)} )
+ *     df/du_c(r)    = phase_scale * sum_m G_{m,c} df/dphi_m(r)
+ *
+ * Complex arrays are interleaved (re, im) doubles.  Layouts (row-major):
+ *   rho [n1][n2], u [C][n1][n2], alpha [D], G [D][C], scan [J][2] (row, col of
+ *   the frame's top-left pixel), probe [Dp][M][M] (Dp = D or 1), y / bg / I
+ *   [D][J][M][M]; frame index f = m*J + j.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+    int n1, n2;          /* object grid rows, columns                       */
+    int ncomp;           /* displacement components C                       */
+    int npeaks;          /* Bragg peaks D                                   */
+    int m;               /* frame (and probe) side M                        */
+    int nscan;           /* scan positions J per peak                       */
+    const double *G;     /* [D][C] scattering vectors                       */
+    const int *scan;     /* [J][2] top-left (row, col)                      */
+    double phase_scale;  /* phi = phase_scale * G.u                         */
+    int probe_per_peak;  /* 0: one probe for all peaks; 1: [D][M][M]        */
+} oracle_problem;
+
+typedef struct {
+    double c_armijo;     /* sufficient-decrease constant                    */
+    double grow;         /* step growth after an accepted step              */
+    double shrink;       /* step shrink after a rejected step               */
+    double t0;           /* initial step length                             */
+    double w_rho, w_u, w_alpha; /* per-block step weights (diagonal scaling) */
+} oracle_step_params;
+
+typedef struct {
+    double f_prev;       /* loss at the last accepted iterate               */
+    double gn2_prev;     /* weighted squared gradient norm there            */
+    double t;            /* step length of the current trial                */
+    double f_last;       /* loss evaluated by the last call                 */
+    int k;               /* number of calls so far                          */
+    int accepted;        /* 1 if the last call accepted its iterate         */
+    int n_accept, n_reject;
+} oracle_step_state;
+
+/* ------------------------------------------------------------------------ */
+/* Direct DFT                                                               */
+/* ------------------------------------------------------------------------ */
+
+/* cos/sin(2 pi t / m) for t in [0, m): the DFT kernel takes its exponent
+ * modulo M, so only these m values occur. */
+static void twiddles(int m, double *ct, double *st)
+{
+    for (int t = 0; t < m; ++t) {
+        double a = 2.0 * M_PI * (double)t / (double)m;
+        ct[t] = cos(a);
+        st[t] = sin(a);
+    }
+}
+
+/* out(q0,q1) = sum_{k0,k1} in(k0,k1) exp(sign * 2 pi i (q0 k0 + q1 k1) / m).
+ * sign = -1: the forward transform F of Eq. 2; sign = +1: F^H (no 1/m^2).
+ * Separable: a direct sum along rows, then along columns. */
+static void dft2_direct(int m, const double *in, double *out, int sign,
+                        const double *ct, const double *st, double *tmp)
+{
+    for (int k0 = 0; k0 < m; ++k0) {
+        for (int q1 = 0; q1 < m; ++q1) {
+            double sr = 0.0, si = 0.0;
+            for (int k1 = 0; k1 < m; ++k1) {
+                int t = (q1 * k1) % m;
+                double wr = ct[t], wi = sign * st[t];
+                double xr = in[2 * (k0 * m + k1)], xi = in[2 * (k0 * m + k1) + 1];
+                sr += xr * wr - xi * wi;
+                si += xr * wi + xi * wr;
+            }
+            tmp[2 * (k0 * m + q1)] = sr;
+            tmp[2 * (k0 * m + q1) + 1] = si;
+        }
+    }
+    for (int q0 = 0; q0 < m; ++q0) {
+        for (int q1 = 0; q1 < m; ++q1) {
+            double sr = 0.0, si = 0.0;
+            for (int k0 = 0; k0 < m; ++k0) {
+                int t = (q0 * k0) % m;
+                double wr = ct[t], wi = sign * st[t];
+                double xr = tmp[2 * (k0 * m + q1)], xi = tmp[2 * (k0 * m + q1) + 1];
+                sr += xr * wr - xi * wi;
+                si += xr * wi + xi * wr;
+            }
+            out[2 * (q0 * m + q1)] = sr;
+            out[2 * (q0 * m + q1) + 1] = si;
+        }
+    }
+}
+
+/* Exposed for the DFT pins: closed forms, Parseval, adjoint identity. */
+void oracle_dft2(int m, const double *in, double *out, int sign)
+{
+    double *ct = malloc(sizeof(double) * m), *st = malloc(sizeof(double) * m);
+    double *tmp = malloc(sizeof(double) * 2 * m * m);
+    twiddles(m, ct, st);
+    dft2_direct(m, in, out, sign, ct, st, tmp);
+    free(ct); free(st); free(tmp);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 1 / Eq. 3: the effective object of each Bragg peak                  */
+/* ------------------------------------------------------------------------ */
+
+static double phase_at(const oracle_problem *p, const double *u, int mpk, long r)
+{
+    long npix = (long)p->n1 * p->n2;
+    double s = 0.0;
+    for (int c = 0; c < p->ncomp; ++c)
+        s += p->G[mpk * p->ncomp + c] * u[c * npix + r];
+    return p->phase_scale * s;
+}
+
+void oracle_object_build(const oracle_problem *p, const double *rho, const double *u,
+                         const double *alpha, double *O)
+{
+    long npix = (long)p->n1 * p->n2;
+    for (int mpk = 0; mpk < p->npeaks; ++mpk) {
+        for (long r = 0; r < npix; ++r) {
+            double ph = phase_at(p, u, mpk, r);
+            O[2 * (mpk * npix + r)] = alpha[mpk] * rho[r] * cos(ph);
+            O[2 * (mpk * npix + r) + 1] = alpha[mpk] * rho[r] * sin(ph);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 2: exit wave of one frame and its far field                          */
+/* ------------------------------------------------------------------------ */
+
+/* psi(k) = P_m(k) * O_m(s_j + k), zero where s_j + k leaves the grid. */
+static void exit_wave(const oracle_problem *p, const double *O, const double *probe,
+                      int mpk, int j, double *psi)
+{
+    int m = p->m;
+    long npix = (long)p->n1 * p->n2;
+    const double *P = probe + (p->probe_per_peak ? (long)mpk * 2 * m * m : 0);
+    int s0 = p->scan[2 * j], s1 = p->scan[2 * j + 1];
+    for (int k0 = 0; k0 < m; ++k0) {
+        for (int k1 = 0; k1 < m; ++k1) {
+            int r0 = s0 + k0, r1 = s1 + k1;
+            double zr = 0.0, zi = 0.0;
+            if (r0 >= 0 && r0 < p->n1 && r1 >= 0 && r1 < p->n2) {
+                long r = (long)r0 * p->n2 + r1;
+                zr = O[2 * (mpk * npix + r)];
+                zi = O[2 * (mpk * npix + r) + 1];
+            }
+            double pr = P[2 * (k0 * m + k1)], pi = P[2 * (k0 * m + k1) + 1];
+            psi[2 * (k0 * m + k1)] = pr * zr - pi * zi;
+            psi[2 * (k0 * m + k1) + 1] = pr * zi + pi * zr;
+        }
+    }
+}
+
+void oracle_forward(const oracle_problem *p, const double *rho, const double *u,
+                    const double *alpha, const double *probe, const double *bg,
+                    double *I)
+{
+    int m = p->m;
+    long npix = (long)p->n1 * p->n2, mm = (long)m * m;
+    double *O = malloc(sizeof(double) * 2 * p->npeaks * npix);
+    oracle_object_build(p, rho, u, alpha, O);
+    long nfr = (long)p->npeaks * p->nscan;
+#pragma omp parallel
+    {
+        double *ct = malloc(sizeof(double) * m), *st = malloc(sizeof(double) * m);
+        double *psi = malloc(sizeof(double) * 2 * mm), *Psi = malloc(sizeof(double) * 2 * mm);
+        double *tmp = malloc(sizeof(double) * 2 * mm);
+        twiddles(m, ct, st);
+#pragma omp for schedule(static)
+        for (long f = 0; f < nfr; ++f) {
+            int mpk = (int)(f / p->nscan), j = (int)(f % p->nscan);
+            exit_wave(p, O, probe, mpk, j, psi);
+            dft2_direct(m, psi, Psi, -1, ct, st, tmp);
+            for (long q = 0; q < mm; ++q) {
+                double v = Psi[2 * q] * Psi[2 * q] + Psi[2 * q + 1] * Psi[2 * q + 1];
+                I[f * mm + q] = v + (bg ? bg[f * mm + q] : 0.0);
+            }
+        }
+        free(ct); free(st); free(psi); free(Psi); free(tmp);
+    }
+    free(O);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 4 and its gradient                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Loss and gradient over the frames listed in `frames` (all D*J frames when
+ * frames == NULL), i.e. the minibatch sum of Eq. 11 with the minibatch given.
+ * Gradient outputs are overwritten.  frame_loss (nullable) receives each
+ * listed frame's own term.  nthreads <= 0 uses the OpenMP default.
+ * Returns the loss. */
+double oracle_loss_grad(const oracle_problem *p, const double *rho, const double *u,
+                        const double *alpha, const double *probe, const double *bg,
+                        const double *y, const int *frames, int nframes,
+                        double *g_rho, double *g_u, double *g_alpha,
+                        double *frame_loss, int nthreads)
+{
+    int m = p->m, D = p->npeaks, C = p->ncomp;
+    long npix = (long)p->n1 * p->n2, mm = (long)m * m;
+    long nlist = frames ? nframes : (long)D * p->nscan;
+    double *O = malloc(sizeof(double) * 2 * D * npix);
+    double *E = malloc(sizeof(double) * 2 * D * npix);   /* e^{i phi_m(r)} */
+    oracle_object_build(p, rho, u, alpha, O);
+    for (int mpk = 0; mpk < D; ++mpk)
+        for (long r = 0; r < npix; ++r) {
+            double ph = phase_at(p, u, mpk, r);
+            E[2 * (mpk * npix + r)] = cos(ph);
+            E[2 * (mpk * npix + r) + 1] = sin(ph);
+        }
+
+    int nt = 1;
+#ifdef _OPENMP
+    nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#endif
+    /* per-thread accumulators, summed in thread order afterwards */
+    double *t_loss = calloc(nt, sizeof(double));
+    double *t_grho = calloc((size_t)nt * npix, sizeof(double));
+    double *t_gphi = calloc((size_t)nt * D * npix, sizeof(double));
+    double *t_galpha = calloc((size_t)nt * D, sizeof(double));
+
+#pragma omp parallel num_threads(nt)
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *ct = malloc(sizeof(double) * m), *st = malloc(sizeof(double) * m);
+        double *psi = malloc(sizeof(double) * 2 * mm), *Psi = malloc(sizeof(double) * 2 * mm);
+        double *chi = malloc(sizeof(double) * 2 * mm), *gh = malloc(sizeof(double) * 2 * mm);
+        double *tmp = malloc(sizeof(double) * 2 * mm);
+        double *grho = t_grho + (size_t)tid * npix;
+        double *gphi = t_gphi + (size_t)tid * D * npix;
+        double *galpha = t_galpha + (size_t)tid * D;
+        twiddles(m, ct, st);
+#pragma omp for schedule(static)
+        for (long i = 0; i < nlist; ++i) {
+            long f = frames ? frames[i] : i;
+            int mpk = (int)(f / p->nscan), j = (int)(f % p->nscan);
+            const double *P = probe + (p->probe_per_peak ? (long)mpk * 2 * mm : 0);
+            int s0 = p->scan[2 * j], s1 = p->scan[2 * j + 1];
+
+            exit_wave(p, O, probe, mpk, j, psi);
+            dft2_direct(m, psi, Psi, -1, ct, st, tmp);
+
+            /* amplitude residual, loss term and chi = 2 df/dconj(Psi) */
+            double fl = 0.0;
+            for (long q = 0; q < mm; ++q) {
+                double pr = Psi[2 * q], pi = Psi[2 * q + 1];
+                double I = pr * pr + pi * pi + (bg ? bg[f * mm + q] : 0.0);
+                double sI = sqrt(I);
+                double res = sI - sqrt(y[f * mm + q]);
+                fl += 0.5 * res * res;
+                double sc = (I > 0.0) ? res / sI : 0.0;
+                chi[2 * q] = sc * pr;
+                chi[2 * q + 1] = sc * pi;
+            }
+            t_loss[tid] += fl;
+            if (frame_loss) frame_loss[i] = fl;
+
+            dft2_direct(m, chi, gh, +1, ct, st, tmp);   /* ghat = F^H chi */
+
+            for (int k0 = 0; k0 < m; ++k0) {
+                for (int k1 = 0; k1 < m; ++k1) {
+                    int r0 = s0 + k0, r1 = s1 + k1;
+                    if (r0 < 0 || r0 >= p->n1 || r1 < 0 || r1 >= p->n2) continue;
+                    long r = (long)r0 * p->n2 + r1;
+                    long kk = (long)k0 * m + k1;
+                    /* g = conj(P) ghat ; cg = conj(g) = P conj(ghat) */
+                    double Pr = P[2 * kk], Pi = P[2 * kk + 1];
+                    double hr = gh[2 * kk], hi = gh[2 * kk + 1];
+                    double gr = Pr * hr + Pi * hi;     /* Re(conj(P) ghat) */
+                    double gi = Pr * hi - Pi * hr;     /* Im(conj(P) ghat) */
+                    double cgr = gr, cgi = -gi;        /* conj(g) */
+                    double er = E[2 * (mpk * npix + r)], ei = E[2 * (mpk * npix + r) + 1];
+                    double orr = O[2 * (mpk * npix + r)], oi = O[2 * (mpk * npix + r) + 1];
+                    double te_r = cgr * er - cgi * ei;         /* Re(conj(g) e) */
+                    double to_i = cgr * oi + cgi * orr;        /* Im(conj(g) O) */
+                    grho[r] += alpha[mpk] * te_r;
+                    gphi[mpk * npix + r] += -to_i;
+                    galpha[mpk] += rho[r] * te_r;
+                }
+            }
+        }
+        free(ct); free(st); free(psi); free(Psi); free(chi); free(gh); free(tmp);
+    }
+
+    double loss = 0.0;
+    for (long r = 0; r < npix; ++r) g_rho[r] = 0.0;
+    for (long r = 0; r < (long)C * npix; ++r) g_u[r] = 0.0;
+    for (int mpk = 0; mpk < D; ++mpk) g_alpha[mpk] = 0.0;
+    double *gphi = calloc((size_t)D * npix, sizeof(double));
+    for (int t = 0; t < nt; ++t) {
+        loss += t_loss[t];
+        for (long r = 0; r < npix; ++r) g_rho[r] += t_grho[(size_t)t * npix + r];
+        for (long r = 0; r < (long)D * npix; ++r) gphi[r] += t_gphi[(size_t)t * D * npix + r];
+        for (int mpk = 0; mpk < D; ++mpk) g_alpha[mpk] += t_galpha[(size_t)t * D + mpk];
+    }
+    /* d phi_m / d u_c = phase_scale * G_{m,c} */
+    for (int c = 0; c < C; ++c)
+        for (long r = 0; r < npix; ++r) {
+            double s = 0.0;
+            for (int mpk = 0; mpk < D; ++mpk)
+                s += p->G[mpk * C + c] * gphi[mpk * npix + r];
+            g_u[c * npix + r] = p->phase_scale * s;
+        }
+    free(gphi); free(t_loss); free(t_grho); free(t_gphi); free(t_galpha);
+    free(O); free(E);
+    return loss;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One gradient-descent iteration with a lagged Armijo line search          */
+/* ------------------------------------------------------------------------ */
+
+/* The optimizer iteration around the loss and gradient (the place of the
+ * update in Alg. 1; plain gradient descent instead of Adam):
+ *   1. f, g at the current iterate x.
+ *   2. Accept x when it is the first call, or when f is finite and
+ *      f <= f_prev - c * t * gn2_prev  (sufficient decrease along -w*g_prev).
+ *   3. Accepted: x_prev = x, g_prev = g, f_prev = f, gn2_prev = sum_b w_b |g_b|^2,
+ *      and t = grow * t (not on the first call).  Rejected: t = shrink * t.
+ *   4. x = x_prev - t * w * g_prev.  alpha_0 (the reference peak's scaling) is
+ *      not a variable: it is neither updated nor counted in gn2.
+ * x_prev and g_prev are caller-owned buffers of the same shapes as rho, u, alpha. */
+void oracle_step(const oracle_problem *p, const double *probe, const double *bg,
+                 const double *y, const oracle_step_params *prm, oracle_step_state *st,
+                 double *rho, double *u, double *alpha,
+                 double *rho_prev, double *u_prev, double *alpha_prev,
+                 double *grho_prev, double *gu_prev, double *galpha_prev, int nthreads)
+{
+    int D = p->npeaks, C = p->ncomp;
+    long npix = (long)p->n1 * p->n2;
+    double *grho = malloc(sizeof(double) * npix);
+    double *gu = malloc(sizeof(double) * C * npix);
+    double *galpha = malloc(sizeof(double) * D);
+    double f = oracle_loss_grad(p, rho, u, alpha, probe, bg, y, NULL, 0,
+                                grho, gu, galpha, NULL, nthreads);
+    int accept;
+    if (st->k == 0)
+        accept = isfinite(f);
+    else
+        accept = isfinite(f) && (f <= st->f_prev - prm->c_armijo * st->t * st->gn2_prev);
+    if (accept) {
+        double gn2 = 0.0, a = 0.0, b = 0.0, c = 0.0;
+        for (long r = 0; r < npix; ++r) a += grho[r] * grho[r];
+        for (long r = 0; r < (long)C * npix; ++r) b += gu[r] * gu[r];
+        for (int mpk = 1; mpk < D; ++mpk) c += galpha[mpk] * galpha[mpk];
+        gn2 = prm->w_rho * a + prm->w_u * b + prm->w_alpha * c;
+        memcpy(rho_prev, rho, sizeof(double) * npix);
+        memcpy(u_prev, u, sizeof(double) * C * npix);
+        memcpy(alpha_prev, alpha, sizeof(double) * D);
+        memcpy(grho_prev, grho, sizeof(double) * npix);
+        memcpy(gu_prev, gu, sizeof(double) * C * npix);
+        memcpy(galpha_prev, galpha, sizeof(double) * D);
+        if (st->k > 0) st->t *= prm->grow;
+        st->f_prev = f;
+        st->gn2_prev = gn2;
+        st->n_accept += 1;
+    } else {
+        st->t *= prm->shrink;
+        st->n_reject += 1;
+    }
+    st->accepted = accept;
+    st->f_last = f;
+    for (long r = 0; r < npix; ++r)
+        rho[r] = rho_prev[r] - st->t * prm->w_rho * grho_prev[r];
+    for (long r = 0; r < (long)C * npix; ++r)
+        u[r] = u_prev[r] - st->t * prm->w_u * gu_prev[r];
+    alpha[0] = alpha_prev[0];
+    for (int mpk = 1; mpk < D; ++mpk)
+        alpha[mpk] = alpha_prev[mpk] - st->t * prm->w_alpha * galpha_prev[mpk];
+    st->k += 1;
+    free(grho); free(gu); free(galpha);
+}
+
+int oracle_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
