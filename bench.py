@@ -1,0 +1,383 @@
+"""Throughput of the MPBP loss+gradient hot path on GB300.
+
+One step = one optimizer iteration of the whole hot path on the 256x256-object,
+3-peak, 31x31-scan, 64x64-frame problem (2,883 frames): object synthesis,
+the fused per-frame kernel (patch gather, probe, 2-D FFT, amplitude residual,
+adjoint FFT, scatter-add), gradient assembly, FP64 reductions, the lagged
+Armijo decision and the update.  The metric is frames per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  N > 1 (under torchrun) runs independent replicas of the
+problem, one per rank (weak scaling; the problem has no data-path exchange
+between replicas).  `--impl reference` times the FP64 CPU oracle on the host
+cores on the same problem instead.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2312_14907_gb300 import synth  # noqa: E402
+
+WORKLOAD = 2          # the 256^2, M = 64, 3-peak, 31x31-scan problem
+METRIC = "frames/s for MPBP loss+gradient (fwd+adjoint), % of HBM roofline, 1 GB300"
+UNIT = "frames/s"
+
+
+def flops_per_frame(m):
+    """Algorithmic FP32 flops of one frame: two unnormalised 2-D FFTs counted
+    as 5 n log2 n with n = M^2, plus 24 flops per pixel of pointwise work
+    (probe product 6, residual and loss 10, adjoint probe product 6, the
+    accumulate 2)."""
+    n = m * m
+    return 2 * 5 * n * math.log2(n) + 24 * n
+
+
+def hbm_bytes_per_frame(spec):
+    """Algorithmic DRAM bytes per frame: the FP32 amplitude stream (4 M^2) plus
+    the object-sized reads and writes amortised over the frames of one step
+    (rho and u read, their gradients written: 2 (1 + C) 4 N^2 / (J D))."""
+    return 4 * spec.m ** 2 + 2 * (1 + spec.ncomp) * 4 * spec.n1 * spec.n2 / spec.nframes
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    out = {"hbm_gbs": 6800.0, "src": "fallback", "sm_max_mhz": 2070.0}
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        out.update({"hbm_gbs": float(d["hbm_gbs"]), "src": "measured",
+                    "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0))})
+    except Exception:
+        pass
+    # plain FP32 pipe: 152 SMs x 128 lanes x 2 flops (FMA) x max SM clock
+    out["fp32_tflops"] = 152 * 128 * 2 * out["sm_max_mhz"] * 1e6 / 1e12
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_inputs(spec, scan, prob, torch):
+    """Synthetic data of the problem: true object, unit probe, the CUDA forward
+    model for the intensities, photon scaling and Poisson counts."""
+    P = synth.probe(spec).astype(np.complex64)
+    rho_t, u_t = synth.truth(spec)
+    xt = [torch.from_numpy(a.astype(np.float32)).cuda() for a in (rho_t, u_t, synth.alpha_truth(spec))]
+    prob.set_probe(torch.from_numpy(P).cuda())
+    I = prob.forward(*xt).cpu().numpy().astype(np.float64)
+    scale = synth.photon_scale(I, spec.photons)
+    probe = (P * np.sqrt(scale)).astype(np.complex64)
+    y = synth.poisson_counts(I * scale, spec.seed + 1000)
+    return probe, y
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2312_14907_gb300 import mpbp
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    spec = synth.config(WORKLOAD)
+    scan = synth.scan_positions(spec)
+    prob = mpbp.Problem.from_spec(spec, scan)
+    probe, y = make_inputs(spec, scan, prob, torch)
+    prob.set_probe(torch.from_numpy(probe).cuda())
+    yd = torch.from_numpy(y).cuda()
+    prob.set_data(yd)
+    rho0, u0, a0 = synth.init_state(spec)
+    x = [torch.from_numpy(a.astype(np.float32)).cuda() for a in (rho0, u0, a0)]
+    # first step length ~ 1 / (max|P|^2 x frames covering a pixel)
+    overlap = (spec.m / spec.step) ** 2 * spec.npeaks
+    t0 = 1.0 / (float(np.abs(probe).max() ** 2) * overlap)
+    state = prob.step_init(t0, w_rho=1.0, w_u=1e-3, w_alpha=1e-3)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        prob.step(*x, state)
+    torch.cuda.synchronize()
+    prob.sync_status()
+
+    info = prob.info()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    prob.frames_timing(True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()                       # evict L2 between timed steps (not timed)
+            evs[k][0].record(stream)
+            prob.step(*x, state)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    prob.frames_timing(False)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    kern_ms, kern_n = prob.frames_timing_read()
+    prob.sync_status()
+    tot_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = t.item()
+
+    # end to end through the host-buffer C-ABI call: H2D of the step's data and
+    # state from pinned memory, evaluation, D2H of loss and gradients
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    yh, rh, uh, ah = pin(y), pin(rho0.astype(np.float32)), pin(u0.astype(np.float32)), pin(a0.astype(np.float32))
+    outs = (torch.empty(1, dtype=torch.float64).pin_memory(),
+            torch.empty(spec.n1, spec.n2, dtype=torch.float32).pin_memory(),
+            torch.empty(spec.ncomp, spec.n1, spec.n2, dtype=torch.float32).pin_memory(),
+            torch.empty(spec.npeaks, dtype=torch.float64).pin_memory())
+    for _ in range(max(2, args.warmup)):
+        prob.loss_grad_host(rh, uh, ah, y=yh, out=outs)
+    if world > 1:
+        dist.barrier()
+    e2e = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        prob.loss_grad_host(rh, uh, ah, y=yh, out=outs)
+        e2e.append(time.perf_counter() - t1)
+    e2e_s = sum(e2e)
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = t.item()
+    h2d = y.nbytes + rh.numel() * 4 + uh.numel() * 4 + ah.numel() * 4
+    d2h = 8 + outs[1].numel() * 4 + outs[2].numel() * 4 + outs[3].numel() * 8
+
+    frames_total = spec.nframes * args.steps * world
+    value = frames_total / (tot_ms / 1e3)
+    pk = peaks()
+    kavg_ms = kern_ms / max(kern_n, 1)
+    fl = flops_per_frame(spec.m) * spec.nframes
+    achieved_tf = fl / (kavg_ms / 1e3) / 1e12
+    bpf = hbm_bytes_per_frame(spec)
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "frames_m64_traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            with open(tr_path) as f:
+                tr = json.load(f)
+            if tr.get("kernel_rev") == kernel_revision():
+                traffic = tr["bytes_per_launch"]
+        except Exception:
+            traffic = None
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": tot_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded truth object, Gaussian probe with quadratic phase, CUDA forward "
+                "model, Poisson counts at 1e4 photons in the brightest frame)",
+        "config": {"workload": spec.name, "object": [spec.n1, spec.n2], "frame": spec.m,
+                   "peaks": spec.npeaks, "scan": [spec.scan_side, spec.scan_side],
+                   "scan_step": spec.step, "frames_per_step": spec.nframes,
+                   "step": "object synthesis + fused frame kernel + gradient assembly + FP64 "
+                           "reductions + lagged-Armijo update",
+                   "l2": "flushed between timed steps (256 MB write, outside the timed region)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "iterations_per_s": args.steps * world / (tot_ms / 1e3),
+        "hbm_roofline": {"bytes_per_frame": bpf, "achieved_gbs": value * bpf / 1e9 / world,
+                         "peak_gbs": pk["hbm_gbs"], "frac": value * bpf / 1e9 / world / pk["hbm_gbs"],
+                         "peak_src": pk["src"]},
+        "roofline": {"bound": "alu", "kernel": "frames_t1<64> (fused per-frame kernel)",
+                     "achieved": achieved_tf, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
+                     "frac": achieved_tf / pk["fp32_tflops"], "traffic": traffic,
+                     "kernel_ms": kavg_ms, "kernel_share_of_step": kavg_ms / (tot_ms / args.steps),
+                     "flops_per_frame": flops_per_frame(spec.m),
+                     "peak_src": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % pk["sm_max_mhz"],
+                     "hbm_frac": kavg_ms and (spec.nframes * 4 * spec.m ** 2 / (kavg_ms / 1e3) / 1e9)
+                     / pk["hbm_gbs"]},
+        "e2e": {"value": frames_total / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h),
+                "call": "mpbp_loss_grad_host (host y, rho, u, alpha in; loss and gradients out)"},
+        "gpu_launches": info["launches_step"] * args.steps,
+        "clocks": clk.summary(),
+        "wall_s": wall,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(spec, scan, probe, y, budget_s=args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def kernel_revision():
+    """Hash of the fused-kernel sources (stale ncu traffic figures are dropped)."""
+    import hashlib
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2312_14907_gb300", "csrc")
+    for name in ("frames.cuh", "fft_reg.cuh", "fft_pair.cuh", "frames_m64.cu"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def cpu_baseline(spec, scan, probe, y, budget_s=20.0):
+    """The FP64 oracle, as it stands, on the host cores: whole evaluations of
+    all frames of the problem, repeated until about `budget_s` seconds."""
+    import oracle
+    p = oracle.OracleProblem.from_spec(spec, scan)
+    rho0, u0, a0 = synth.init_state(spec)
+    n, t = 0, 0.0
+    while t < budget_s and n < 50:
+        t1 = time.perf_counter()
+        p.loss_grad(rho0, u0, a0, probe, y)
+        t += time.perf_counter() - t1
+        n += 1
+    return {"value": n * spec.nframes / t, "unit": UNIT, "cores": oracle.max_threads(),
+            "kind": "oracle",
+            "sample": "%d full loss+gradient evaluation(s) of all %d frames (%.1f s)" % (n, spec.nframes, t)}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    spec = synth.config(WORKLOAD)
+    scan = synth.scan_positions(spec)
+    P = synth.probe(spec)
+    p = oracle.OracleProblem.from_spec(spec, scan)
+    rho_t, u_t = synth.truth(spec)
+    I = p.forward(rho_t, u_t, synth.alpha_truth(spec), P)
+    scale = synth.photon_scale(I, spec.photons)
+    probe = P * np.sqrt(scale)
+    y = synth.poisson_counts(I * scale, spec.seed + 1000)
+    rho0, u0, a0 = synth.init_state(spec)
+    # each step: one loss+gradient evaluation over a seeded sample of frames
+    nsample = min(spec.nframes, args.ref_frames)
+    rng = np.random.default_rng(7)
+    for _ in range(args.warmup):
+        p.loss_grad(rho0, u0, a0, probe, y, frames=rng.choice(spec.nframes, nsample, replace=False))
+    t = 0.0
+    for _ in range(args.steps):
+        fr = rng.choice(spec.nframes, nsample, replace=False)
+        t1 = time.perf_counter()
+        p.loss_grad(rho0, u0, a0, probe, y, frames=fr)
+        t += time.perf_counter() - t1
+    value = nsample * args.steps / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (same generator as the GPU arm)",
+            "config": {"workload": spec.name, "object": [spec.n1, spec.n2], "frame": spec.m,
+                       "peaks": spec.npeaks, "scan": [spec.scan_side, spec.scan_side]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(),
+                             "kind": "oracle",
+                             "sample": "%d seeded frames of %d per step" % (nsample, spec.nframes)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-frames", type=int, default=600)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

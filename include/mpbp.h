@@ -1,0 +1,213 @@
+/*
+ * mpbp.h -- C ABI of the GB300 multi-peak Bragg ptychography (MPBP) library.
+ *
+ * The library evaluates, on one GPU, the loss and gradient that the paper's
+ * reconstruction repeats every iteration (Kandel et al., arXiv 2312.14907):
+ *
+ *   objects   O_m(r) = alpha_m rho(r) exp(i phi_m(r)),
+ *             phi_m(r) = phase_scale * sum_c G_{m,c} u_c(r)            (Eq. 1, Eq. 3)
+ *   model     I_{m,j} = | F diag(P_m) S_j O_m |^2 + b_{m,j}            (Eq. 2)
+ *   loss      f = 1/2 sum_{m,j,q} ( sqrt(I_{m,j}(q)) - sqrt(y_{m,j}(q)) )^2  (Eq. 4)
+ *   gradient  df/drho, df/du_c, df/dalpha_m of that loss (the minibatch sums of
+ *             Eq. 11 when a frame subset is given)
+ *
+ * in the thin-membrane form of Eq. 2 (R = identity).  F is the unnormalised
+ * 2-D DFT with kernel exp(-2 pi i q.k / M) and DC at index [0][0]; S_j takes the
+ * M x M patch whose top-left pixel is scan[j], reading 0 outside the grid.
+ *
+ * Conventions for every entry point:
+ *   - Arrays are row-major and C-contiguous.  Complex values are interleaved
+ *     float pairs (re, im).  A "frame" is one (peak m, scan position j) pair,
+ *     numbered f = m * nscan + j; frame-indexed arrays are [npeaks][nscan][M][M].
+ *   - Array arguments marked "dev" are device pointers owned by the caller and
+ *     must stay valid until the stream work that uses them has finished.
+ *     Arguments marked "host" are read before the call returns.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls only enqueue work on it; none synchronises, except
+ *     mpbp_sync_status, mpbp_loss_grad_host and mpbp_create/mpbp_destroy.
+ *   - Argument errors are detected on the host and returned before anything is
+ *     enqueued.  Errors found on the device (a frame index out of range, a
+ *     non-finite loss) are latched in the context and reported by
+ *     mpbp_sync_status.  No C++ exception crosses this boundary.
+ *   - There is no CPU fallback: without a usable GPU, mpbp_create fails with
+ *     MPBP_ERR_CUDA.
+ */
+#ifndef MPBP_H_
+#define MPBP_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpbp_ctx mpbp_ctx;
+
+typedef enum {
+  MPBP_OK = 0,
+  MPBP_ERR_INVALID_ARG = 1,  /* a pointer, size or value is not allowed       */
+  MPBP_ERR_UNSUPPORTED = 2,  /* valid problem the kernels do not cover (M)   */
+  MPBP_ERR_CUDA = 3,         /* a CUDA runtime call failed                   */
+  MPBP_ERR_NONFINITE = 4,    /* the loss came out NaN or infinite            */
+  MPBP_ERR_TIMEOUT = 5,      /* reserved: no kernel of this library waits   */
+  MPBP_ERR_BOUNDS = 6,       /* a frame index outside [0, npeaks*nscan)      */
+  MPBP_ERR_OOM = 7,          /* device allocation failed                     */
+  MPBP_ERR_NO_DATA = 8       /* probe or measured data not set yet           */
+} mpbp_status;
+
+/* Geometry of one problem (Sec. 3: the variables U, chi, alpha and the
+ * measurements y_{hk,j}).  Copied by mpbp_create; the caller may free it. */
+typedef struct {
+  int32_t n1, n2;          /* object grid rows, columns (>= 1)                  */
+  int32_t ncomp;           /* displacement components C: 1, 2 or 3             */
+  int32_t npeaks;          /* Bragg peaks D: 1..16                              */
+  int32_t m;               /* frame and probe side M: 8, 16, 32, 64 or 128      */
+  int32_t nscan;           /* scan positions J per peak (>= 1)                  */
+  const double *G;         /* host [npeaks][ncomp] scattering vectors G_m       */
+  const int32_t *scan;     /* host [nscan][2] top-left (row, col) of frame j;
+                              any value, pixels outside the grid read as 0     */
+  int32_t probe_per_peak;  /* 0: one probe [M][M] for all peaks; 1: [D][M][M]  */
+  double phase_scale;      /* phi = phase_scale * G.u; 2*pi gives Eq. 1        */
+} mpbp_problem;
+
+/* Lagged-Armijo gradient descent (the update step of Alg. 1 with plain
+ * gradient descent in place of Adam).  Weights scale each block's step. */
+typedef struct {
+  double c_armijo;         /* sufficient-decrease constant, e.g. 1e-4          */
+  double grow;             /* step growth after an accepted step, e.g. 1.25    */
+  double shrink;           /* step shrink after a rejected step, e.g. 0.5      */
+  double t0;               /* first step length                                */
+  double w_rho, w_u, w_alpha;
+} mpbp_step_params;
+
+/* Device-resident optimizer state; written by mpbp_step_init, advanced by
+ * mpbp_step, readable by copying it back. */
+typedef struct {
+  double f_prev;           /* loss at the last accepted iterate                */
+  double gn2_prev;         /* sum_b w_b |g_b|^2 there (alpha_0 excluded)       */
+  double t;                /* step length of the pending trial                 */
+  double f_last;           /* loss evaluated by the last mpbp_step             */
+  int32_t k;               /* mpbp_step calls so far                           */
+  int32_t accepted;        /* 1 if the last call accepted its iterate          */
+  int32_t n_accept, n_reject;
+  double c_armijo, grow, shrink, w_rho, w_u, w_alpha;
+} mpbp_step_state;
+
+typedef struct {
+  int64_t workspace_bytes; /* device memory owned by the context               */
+  int32_t frames_grid;     /* blocks of the fused frame kernel                 */
+  int32_t frames_block;    /* threads per block of the fused frame kernel      */
+  int32_t frames_smem;     /* dynamic shared memory per block (bytes)          */
+  int32_t blocks_per_sm;   /* resident blocks per SM the schedule assumes      */
+  int32_t num_sms;
+  int32_t launches_loss_grad; /* kernels + memsets enqueued by mpbp_loss_grad  */
+  int32_t launches_step;      /* kernels + memsets enqueued by mpbp_step       */
+} mpbp_info;
+
+/* Name of a status code (static string). */
+const char *mpbp_status_string(mpbp_status s);
+
+/* Creates a context for `problem` on the current CUDA device: validates the
+ * geometry, copies G and the scan table to the device and allocates the
+ * workspace (objects, gradient accumulators, a = sqrt(y), partial sums,
+ * optimizer buffers).  Synchronous.  On failure *out is NULL. */
+mpbp_status mpbp_create(const mpbp_problem *problem, mpbp_ctx **out);
+
+/* Frees the context and its workspace (synchronises the device first). */
+void mpbp_destroy(mpbp_ctx *ctx);
+
+/* Message describing the last error this context returned ("" if none). */
+const char *mpbp_last_error(const mpbp_ctx *ctx);
+
+/* Workspace and launch configuration of the context. */
+mpbp_status mpbp_get_info(const mpbp_ctx *ctx, mpbp_info *info);
+
+/* Sets the probe P_m of Eq. 2: dev [Dp][M][M] complex (Dp = npeaks when
+ * probe_per_peak, else 1), copied into the context. */
+mpbp_status mpbp_set_probe(mpbp_ctx *ctx, const float *probe, void *stream);
+
+/* Sets the measured intensities y of Eq. 4: dev [D][J][M][M] float counts
+ * (>= 0), and the optional background b of Eq. 2 (dev, same shape, or NULL).
+ * The context derives and keeps a = sqrt(y) (and b) in its own layout; the
+ * caller may free y and b once the stream has passed this call. */
+mpbp_status mpbp_set_data(mpbp_ctx *ctx, const float *y, const float *bg, void *stream);
+
+/* Eq. 1 / Eq. 3: O_out = dev [D][n1][n2] complex objects of every peak from
+ * rho (dev [n1][n2]), u (dev [C][n1][n2]) and alpha (dev [D]). */
+mpbp_status mpbp_object_build(mpbp_ctx *ctx, const float *rho, const float *u,
+                              const float *alpha, float *O_out, void *stream);
+
+/* Eq. 2: I_out = dev [D][J][M][M] model intensities |F P S O|^2 + b (b from
+ * mpbp_set_data when set, else 0).  Needs the probe. */
+mpbp_status mpbp_forward(mpbp_ctx *ctx, const float *rho, const float *u,
+                         const float *alpha, float *I_out, void *stream);
+
+/* Eq. 4 and its gradient over the frames listed in `frames` (dev int32
+ * [nframes], each in [0, D*J); NULL = all D*J frames, nframes ignored).
+ * Outputs (all dev, overwritten): loss (1 double), g_rho [n1][n2],
+ * g_u [C][n1][n2], g_alpha [D] doubles (NULL to skip).  Needs probe and data.
+ * Loss and gradients are sums over frames and pixels (no normalisation). */
+mpbp_status mpbp_loss_grad(mpbp_ctx *ctx, const float *rho, const float *u,
+                           const float *alpha, const int32_t *frames, int32_t nframes,
+                           double *loss, float *g_rho, float *g_u, double *g_alpha,
+                           void *stream);
+
+/* End-to-end variant of mpbp_loss_grad on HOST buffers: copies y (host
+ * [D][J][M][M], or NULL to keep the data already set), rho, u, alpha to the
+ * device, evaluates all frames, copies loss (1 double), g_rho, g_u and
+ * g_alpha (host, NULL to skip) back, and synchronises the stream.  Page-locked
+ * host memory makes the copies asynchronous and fast. */
+mpbp_status mpbp_loss_grad_host(mpbp_ctx *ctx, const float *y, const float *rho,
+                                const float *u, const float *alpha, double *loss,
+                                float *g_rho, float *g_u, double *g_alpha, void *stream);
+
+/* Initialises the device-resident optimizer state st (dev) from prm (host). */
+mpbp_status mpbp_step_init(mpbp_ctx *ctx, const mpbp_step_params *prm,
+                           mpbp_step_state *st, void *stream);
+
+/* One optimizer iteration on rho, u, alpha (dev, updated in place):
+ *   1. f, g = loss and gradient at the current iterate (all frames);
+ *   2. accept it on the first call, or when f is finite and
+ *      f <= f_prev - c_armijo * t * gn2_prev;
+ *   3. accepted: keep the iterate and its gradient as the new base point,
+ *      t *= grow (not on the first call); rejected: t *= shrink;
+ *   4. rho, u, alpha = base - t * w * g_base, alpha_0 held fixed (the
+ *      reference peak of Eq. 3 has no scaling variable).
+ * All decisions are taken on the device in FP64, so a sequence of calls can be
+ * captured in a CUDA graph and replayed without host synchronisation. */
+mpbp_status mpbp_step(mpbp_ctx *ctx, float *rho, float *u, float *alpha,
+                      mpbp_step_state *st, void *stream);
+
+/* Loss and gradient of n independent problems (frame sides may differ) in
+ * one persistent launch of the fused frame kernel.  Each argument is a host
+ * array of n per-problem pointers with the meaning of mpbp_loss_grad
+ * (all frames of each problem). */
+mpbp_status mpbp_loss_grad_batched(int32_t n, mpbp_ctx *const *ctxs,
+                                   const float *const *rho, const float *const *u,
+                                   const float *const *alpha, double *const *loss,
+                                   float *const *g_rho, float *const *g_u,
+                                   double *const *g_alpha, void *stream);
+
+/* Overrides the fused frame kernel's schedule: resident blocks per SM used to
+ * size its persistent grid (0 = occupancy maximum).  Host-side only. */
+mpbp_status mpbp_set_schedule(mpbp_ctx *ctx, int32_t blocks_per_sm);
+
+/* Turns on (enable != 0) or off the recording of CUDA events around every
+ * launch of the fused frame kernel, on the stream it is launched on.  Off by
+ * default; must not be on while a stream is being captured into a graph. */
+mpbp_status mpbp_frames_timing(mpbp_ctx *ctx, int32_t enable);
+
+/* Waits for the recorded events, then returns the summed duration in
+ * milliseconds (*total_ms) and the number of timed launches (*count) since the
+ * last read, and clears them.  Host pointers. */
+mpbp_status mpbp_frames_timing_read(mpbp_ctx *ctx, double *total_ms, int32_t *count);
+
+/* Synchronises `stream`, then returns and clears the first error latched on
+ * the device since the last call (MPBP_OK if none). */
+mpbp_status mpbp_sync_status(mpbp_ctx *ctx, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPBP_H_ */

@@ -1,0 +1,39 @@
+// frames_dispatch.cu -- run-time dispatch over the compiled frame sides.
+#include "frames_launch.h"
+
+namespace mpbp {
+
+bool frames_prepare_m8(FrameKernelInfo*);
+bool frames_prepare_m16(FrameKernelInfo*);
+bool frames_prepare_m32(FrameKernelInfo*);
+bool frames_prepare_m64(FrameKernelInfo*);
+bool frames_prepare_m128(FrameKernelInfo*);
+cudaError_t frames_launch_m8(const FrameArgs&, int, bool, cudaStream_t);
+cudaError_t frames_launch_m16(const FrameArgs&, int, bool, cudaStream_t);
+cudaError_t frames_launch_m32(const FrameArgs&, int, bool, cudaStream_t);
+cudaError_t frames_launch_m64(const FrameArgs&, int, bool, cudaStream_t);
+cudaError_t frames_launch_m128(const FrameArgs&, int, bool, cudaStream_t);
+
+bool frames_prepare(int m, FrameKernelInfo* info) {
+  switch (m) {
+    case 8: return frames_prepare_m8(info);
+    case 16: return frames_prepare_m16(info);
+    case 32: return frames_prepare_m32(info);
+    case 64: return frames_prepare_m64(info);
+    case 128: return frames_prepare_m128(info);
+    default: return false;
+  }
+}
+
+cudaError_t frames_launch(int m, const FrameArgs& a, int grid, bool forward, cudaStream_t s) {
+  switch (m) {
+    case 8: return frames_launch_m8(a, grid, forward, s);
+    case 16: return frames_launch_m16(a, grid, forward, s);
+    case 32: return frames_launch_m32(a, grid, forward, s);
+    case 64: return frames_launch_m64(a, grid, forward, s);
+    case 128: return frames_launch_m128(a, grid, forward, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace mpbp

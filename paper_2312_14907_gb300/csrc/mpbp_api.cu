@@ -1,0 +1,570 @@
+// mpbp_api.cu -- the C ABI declared in include/mpbp.h: context, workspace,
+// argument checks and the launch sequence of each entry point.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "aux_launch.h"
+#include "frames_launch.h"
+
+using namespace mpbp;
+
+struct mpbp_ctx {
+  int device = 0;
+  int num_sms = 0;
+  // problem
+  int n1 = 0, n2 = 0, C = 0, D = 0, M = 0, J = 0;
+  int probe_per_peak = 0;
+  double phase_scale = 0.0;
+  long long npix = 0;
+  long long nframes = 0;  // D * J
+  PhaseCoef pc{};
+  // kernel schedule
+  FrameKernelInfo fk{};
+  int blocks_per_sm = 0;  // schedule in use
+  int frames_grid_cap = 0;
+  int finish_grid = 0;
+  // device workspace
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  cf* O = nullptr;
+  cf* acc = nullptr;
+  cf* probe = nullptr;
+  int2* scan = nullptr;
+  float* aT = nullptr;
+  float* bgT = nullptr;
+  double* loss_part = nullptr;
+  double* part = nullptr;
+  double* loss_ws = nullptr;
+  float* g_rho_ws = nullptr;
+  float* g_u_ws = nullptr;
+  double* g_alpha_ws = nullptr;
+  float* rho_base = nullptr;
+  float* u_base = nullptr;
+  float* alpha_base = nullptr;
+  float* g_rho_base = nullptr;
+  float* g_u_base = nullptr;
+  double* g_alpha_base = nullptr;
+  int* err = nullptr;
+  // lazily allocated for the host-buffer entry point
+  float* io_x = nullptr;
+  float* stage = nullptr;
+  size_t stage_elems = 0;
+  bool has_probe = false, has_data = false;
+  bool acc_dirty = false;
+  // optional event timing of the fused frame kernel
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+  size_t ev_used = 0;
+  std::string last_error;
+};
+
+namespace {
+
+const char* kStatusNames[] = {"MPBP_OK",          "MPBP_ERR_INVALID_ARG", "MPBP_ERR_UNSUPPORTED",
+                              "MPBP_ERR_CUDA",    "MPBP_ERR_NONFINITE",   "MPBP_ERR_TIMEOUT",
+                              "MPBP_ERR_BOUNDS",  "MPBP_ERR_OOM",         "MPBP_ERR_NO_DATA"};
+
+mpbp_status fail(mpbp_ctx* c, mpbp_status s, const std::string& msg) {
+  if (c) c->last_error = msg;
+  return s;
+}
+
+#define MPBP_CUDA(ctx, call)                                                              \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) {                                                              \
+      return fail(ctx, MPBP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    }                                                                                     \
+  } while (0)
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Carver {
+  size_t off = 0;
+  template <typename T>
+  size_t take(size_t n) {
+    size_t o = align_up(off, 256);
+    off = o + n * sizeof(T);
+    return o;
+  }
+};
+
+int frames_grid_for(const mpbp_ctx* c, long long nframes) {
+  const long long need = (nframes + c->fk.frames_per_block - 1) / c->fk.frames_per_block;
+  long long g = std::min<long long>(need, c->frames_grid_cap);
+  return (int)std::max<long long>(g, 1);
+}
+
+FrameArgs frame_args(mpbp_ctx* c, const int* frames, int nframes) {
+  FrameArgs a{};
+  a.O = c->O;
+  a.probe = c->probe;
+  a.aT = c->aT;
+  a.bgT = c->bgT;
+  a.scan = c->scan;
+  a.frames = frames;
+  a.acc = c->acc;
+  a.loss_part = c->loss_part;
+  a.I_out = nullptr;
+  a.err = c->err;
+  a.obj_stride = c->npix;
+  a.nframes = nframes;
+  a.nframes_total = (int)c->nframes;
+  a.n1 = c->n1;
+  a.n2 = c->n2;
+  a.J = c->J;
+  a.probe_stride = c->probe_per_peak ? c->M * c->M : 0;
+  return a;
+}
+
+mpbp_status enqueue_object_build(mpbp_ctx* c, const float* rho, const float* u,
+                                 const float* alpha, cf* out, cudaStream_t s) {
+  ObjectArgs oa{};
+  oa.rho = rho;
+  oa.u = u;
+  oa.alpha = alpha;
+  oa.O = out;
+  oa.npix = c->npix;
+  oa.D = c->D;
+  oa.C = c->C;
+  oa.pc = c->pc;
+  MPBP_CUDA(c, launch_object_build(oa, c->num_sms, s));
+  return MPBP_OK;
+}
+
+// A1..A8 without the optimizer update: objects, fused frames, gradient
+// assembly, reductions.  st != nullptr adds the line-search decision.
+mpbp_status enqueue_loss_grad(mpbp_ctx* c, const float* rho, const float* u, const float* alpha,
+                              const int32_t* frames, int32_t nframes, double* loss,
+                              float* g_rho, float* g_u, double* g_alpha,
+                              mpbp_step_state* st, cudaStream_t s) {
+  if (c->acc_dirty) {
+    MPBP_CUDA(c, cudaMemsetAsync(c->acc, 0, sizeof(cf) * c->npix * c->D, s));
+    c->acc_dirty = false;
+  }
+  mpbp_status r = enqueue_object_build(c, rho, u, alpha, c->O, s);
+  if (r != MPBP_OK) return r;
+  const int nf = frames ? nframes : (int)c->nframes;
+  FrameArgs fa = frame_args(c, frames, nf);
+  const int grid = frames_grid_for(c, nf);
+  c->acc_dirty = true;
+  cudaEvent_t ev1 = nullptr;
+  if (c->timing) {
+    if (c->ev_used == c->ev_pool.size()) {
+      cudaEvent_t a, b;
+      MPBP_CUDA(c, cudaEventCreate(&a));
+      MPBP_CUDA(c, cudaEventCreate(&b));
+      c->ev_pool.emplace_back(a, b);
+    }
+    MPBP_CUDA(c, cudaEventRecord(c->ev_pool[c->ev_used].first, s));
+    ev1 = c->ev_pool[c->ev_used].second;
+    c->ev_used++;
+  }
+  MPBP_CUDA(c, frames_launch(c->M, fa, grid, false, s));
+  if (ev1) MPBP_CUDA(c, cudaEventRecord(ev1, s));
+
+  FinishArgs fi{};
+  fi.rho = rho;
+  fi.u = u;
+  fi.alpha = alpha;
+  fi.acc = c->acc;
+  fi.g_rho = g_rho;
+  fi.g_u = g_u;
+  fi.part = c->part;
+  fi.npix = c->npix;
+  fi.D = c->D;
+  fi.C = c->C;
+  fi.pc = c->pc;
+  MPBP_CUDA(c, launch_finish(fi, c->finish_grid, s));
+  c->acc_dirty = false;
+
+  ReduceArgs ra{};
+  ra.loss_part = c->loss_part;
+  ra.n_loss_part = grid;
+  ra.part = c->part;
+  ra.n_part = c->finish_grid;
+  ra.D = c->D;
+  ra.loss_out = loss;
+  ra.g_alpha_out = g_alpha;
+  ra.g_alpha_ws = c->g_alpha_ws;
+  ra.err = c->err;
+  ra.st = st;
+  ra.alpha_from = 1;
+  MPBP_CUDA(c, launch_reduce(ra, s));
+  return MPBP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mpbp_status_string(mpbp_status s) {
+  int i = (int)s;
+  if (i < 0 || i >= (int)(sizeof(kStatusNames) / sizeof(kStatusNames[0]))) return "MPBP_ERR_UNKNOWN";
+  return kStatusNames[i];
+}
+
+const char* mpbp_last_error(const mpbp_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+mpbp_status mpbp_create(const mpbp_problem* pr, mpbp_ctx** out) {
+  if (!out) return MPBP_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!pr || !pr->G || !pr->scan) return MPBP_ERR_INVALID_ARG;
+  if (pr->n1 < 1 || pr->n2 < 1 || pr->ncomp < 1 || pr->ncomp > kMaxComp || pr->npeaks < 1 ||
+      pr->npeaks > kMaxPeaks || pr->nscan < 1 || !std::isfinite(pr->phase_scale))
+    return MPBP_ERR_INVALID_ARG;
+  if ((long long)pr->n1 * pr->n2 > (1LL << 31) / 16) return MPBP_ERR_INVALID_ARG;
+  if ((long long)pr->npeaks * pr->nscan > (1LL << 31) - 1) return MPBP_ERR_INVALID_ARG;
+  if (pr->m != 8 && pr->m != 16 && pr->m != 32 && pr->m != 64 && pr->m != 128)
+    return MPBP_ERR_UNSUPPORTED;
+  for (int i = 0; i < pr->npeaks * pr->ncomp; ++i)
+    if (!std::isfinite(pr->G[i])) return MPBP_ERR_INVALID_ARG;
+
+  mpbp_ctx* c = new (std::nothrow) mpbp_ctx();
+  if (!c) return MPBP_ERR_OOM;
+  auto bail = [&](mpbp_status s) {
+    if (c->ws) cudaFree(c->ws);
+    delete c;
+    return s;
+  };
+  if (cudaGetDevice(&c->device) != cudaSuccess) return bail(MPBP_ERR_CUDA);
+  if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+    return bail(MPBP_ERR_CUDA);
+  c->n1 = pr->n1;
+  c->n2 = pr->n2;
+  c->C = pr->ncomp;
+  c->D = pr->npeaks;
+  c->M = pr->m;
+  c->J = pr->nscan;
+  c->probe_per_peak = pr->probe_per_peak ? 1 : 0;
+  c->phase_scale = pr->phase_scale;
+  c->npix = (long long)pr->n1 * pr->n2;
+  c->nframes = (long long)pr->npeaks * pr->nscan;
+  for (int m = 0; m < c->D; ++m)
+    for (int k = 0; k < kMaxComp; ++k) {
+      const double g = k < c->C ? pr->G[m * c->C + k] : 0.0;
+      c->pc.kpi[m][k] = (float)(pr->phase_scale * g / 3.14159265358979323846);
+      c->pc.kps[m][k] = (float)(pr->phase_scale * g);
+    }
+  if (!frames_prepare(c->M, &c->fk)) return bail(MPBP_ERR_CUDA);
+  c->blocks_per_sm = c->fk.blocks_per_sm;
+  c->frames_grid_cap = c->num_sms * c->blocks_per_sm;
+  c->finish_grid = finish_grid(c->npix, c->num_sms);
+
+  const long long mm = (long long)c->M * c->M;
+  const int Dp = c->probe_per_peak ? c->D : 1;
+  const int max_frames_grid = c->num_sms * 64;
+  Carver cv;
+  size_t oO = cv.take<cf>(c->npix * c->D);
+  size_t oAcc = cv.take<cf>(c->npix * c->D);
+  size_t oProbe = cv.take<cf>(Dp * mm);
+  size_t oScan = cv.take<int2>(c->J);
+  size_t oAT = cv.take<float>(c->nframes * mm);
+  size_t oLP = cv.take<double>(max_frames_grid);
+  size_t oPart = cv.take<double>((size_t)c->finish_grid * (c->D + 2));
+  size_t oLoss = cv.take<double>(1);
+  size_t oGR = cv.take<float>(c->npix);
+  size_t oGU = cv.take<float>(c->npix * c->C);
+  size_t oGA = cv.take<double>(c->D);
+  size_t oRB = cv.take<float>(c->npix);
+  size_t oUB = cv.take<float>(c->npix * c->C);
+  size_t oAB = cv.take<float>(c->D);
+  size_t oGRB = cv.take<float>(c->npix);
+  size_t oGUB = cv.take<float>(c->npix * c->C);
+  size_t oGAB = cv.take<double>(c->D);
+  size_t oErr = cv.take<int>(1);
+  c->ws_bytes = align_up(cv.off, 256);
+  cudaError_t e = cudaMalloc(&c->ws, c->ws_bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c->ws = nullptr;
+    return bail(e == cudaErrorMemoryAllocation ? MPBP_ERR_OOM : MPBP_ERR_CUDA);
+  }
+  char* b = static_cast<char*>(c->ws);
+  c->O = reinterpret_cast<cf*>(b + oO);
+  c->acc = reinterpret_cast<cf*>(b + oAcc);
+  c->probe = reinterpret_cast<cf*>(b + oProbe);
+  c->scan = reinterpret_cast<int2*>(b + oScan);
+  c->aT = reinterpret_cast<float*>(b + oAT);
+  c->loss_part = reinterpret_cast<double*>(b + oLP);
+  c->part = reinterpret_cast<double*>(b + oPart);
+  c->loss_ws = reinterpret_cast<double*>(b + oLoss);
+  c->g_rho_ws = reinterpret_cast<float*>(b + oGR);
+  c->g_u_ws = reinterpret_cast<float*>(b + oGU);
+  c->g_alpha_ws = reinterpret_cast<double*>(b + oGA);
+  c->rho_base = reinterpret_cast<float*>(b + oRB);
+  c->u_base = reinterpret_cast<float*>(b + oUB);
+  c->alpha_base = reinterpret_cast<float*>(b + oAB);
+  c->g_rho_base = reinterpret_cast<float*>(b + oGRB);
+  c->g_u_base = reinterpret_cast<float*>(b + oGUB);
+  c->g_alpha_base = reinterpret_cast<double*>(b + oGAB);
+  c->err = reinterpret_cast<int*>(b + oErr);
+
+  std::vector<int2> sc(c->J);
+  for (int j = 0; j < c->J; ++j) sc[j] = make_int2(pr->scan[2 * j], pr->scan[2 * j + 1]);
+  if (cudaMemcpy(c->scan, sc.data(), sizeof(int2) * c->J, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(c->acc, 0, sizeof(cf) * c->npix * c->D) != cudaSuccess ||
+      cudaMemset(c->err, 0, sizeof(int)) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess)
+    return bail(MPBP_ERR_CUDA);
+  *out = c;
+  return MPBP_OK;
+}
+
+void mpbp_destroy(mpbp_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  for (auto& e : c->ev_pool) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  if (c->ws) cudaFree(c->ws);
+  if (c->io_x) cudaFree(c->io_x);
+  if (c->stage) cudaFree(c->stage);
+  if (c->bgT) cudaFree(c->bgT);
+  delete c;
+}
+
+mpbp_status mpbp_get_info(const mpbp_ctx* c, mpbp_info* info) {
+  if (!c || !info) return MPBP_ERR_INVALID_ARG;
+  info->workspace_bytes = (int64_t)c->ws_bytes;
+  info->frames_grid = frames_grid_for(c, c->nframes);
+  info->frames_block = c->fk.threads;
+  info->frames_smem = c->fk.smem;
+  info->blocks_per_sm = c->blocks_per_sm;
+  info->num_sms = c->num_sms;
+  info->launches_loss_grad = 4;  // object build, frames, finish, reduce
+  info->launches_step = 5;       // + update
+  return MPBP_OK;
+}
+
+mpbp_status mpbp_set_schedule(mpbp_ctx* c, int32_t blocks_per_sm) {
+  if (!c || blocks_per_sm < 0) return fail(c, MPBP_ERR_INVALID_ARG, "blocks_per_sm < 0");
+  int b = blocks_per_sm == 0 ? c->fk.blocks_per_sm : std::min<int>(blocks_per_sm, c->fk.blocks_per_sm);
+  c->blocks_per_sm = std::max(b, 1);
+  c->frames_grid_cap = std::min(c->num_sms * c->blocks_per_sm, c->num_sms * 64);
+  return MPBP_OK;
+}
+
+mpbp_status mpbp_set_probe(mpbp_ctx* c, const float* probe, void* stream) {
+  if (!c || !probe) return fail(c, MPBP_ERR_INVALID_ARG, "null probe");
+  const int Dp = c->probe_per_peak ? c->D : 1;
+  MPBP_CUDA(c, cudaMemcpyAsync(c->probe, probe, sizeof(cf) * Dp * c->M * c->M,
+                               cudaMemcpyDeviceToDevice, S(stream)));
+  c->has_probe = true;
+  return MPBP_OK;
+}
+
+mpbp_status mpbp_set_data(mpbp_ctx* c, const float* y, const float* bg, void* stream) {
+  if (!c || !y) return fail(c, MPBP_ERR_INVALID_ARG, "null data");
+  MPBP_CUDA(c, launch_frame_transpose(y, c->aT, c->nframes, c->M, true, S(stream)));
+  if (bg) {
+    if (!c->bgT) {
+      cudaError_t e = cudaMalloc(&c->bgT, sizeof(float) * c->nframes * c->M * c->M);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->bgT = nullptr;
+        return fail(c, MPBP_ERR_OOM, "background buffer");
+      }
+    }
+    MPBP_CUDA(c, launch_frame_transpose(bg, c->bgT, c->nframes, c->M, false, S(stream)));
+  } else if (c->bgT) {
+    MPBP_CUDA(c, cudaStreamSynchronize(S(stream)));
+    cudaFree(c->bgT);
+    c->bgT = nullptr;
+  }
+  c->has_data = true;
+  return MPBP_OK;
+}
+
+mpbp_status mpbp_object_build(mpbp_ctx* c, const float* rho, const float* u, const float* alpha,
+                              float* O_out, void* stream) {
+  if (!c || !rho || !u || !alpha || !O_out) return fail(c, MPBP_ERR_INVALID_ARG, "null argument");
+  return enqueue_object_build(c, rho, u, alpha, reinterpret_cast<cf*>(O_out), S(stream));
+}
+
+mpbp_status mpbp_forward(mpbp_ctx* c, const float* rho, const float* u, const float* alpha,
+                         float* I_out, void* stream) {
+  if (!c || !rho || !u || !alpha || !I_out) return fail(c, MPBP_ERR_INVALID_ARG, "null argument");
+  if (!c->has_probe) return fail(c, MPBP_ERR_NO_DATA, "probe not set");
+  mpbp_status r = enqueue_object_build(c, rho, u, alpha, c->O, S(stream));
+  if (r != MPBP_OK) return r;
+  FrameArgs fa = frame_args(c, nullptr, (int)c->nframes);
+  fa.I_out = I_out;
+  MPBP_CUDA(c, frames_launch(c->M, fa, frames_grid_for(c, c->nframes), true, S(stream)));
+  return MPBP_OK;
+}
+
+mpbp_status mpbp_loss_grad(mpbp_ctx* c, const float* rho, const float* u, const float* alpha,
+                           const int32_t* frames, int32_t nframes, double* loss, float* g_rho,
+                           float* g_u, double* g_alpha, void* stream) {
+  if (!c || !rho || !u || !alpha || !loss) return fail(c, MPBP_ERR_INVALID_ARG, "null argument");
+  if (frames && nframes < 0) return fail(c, MPBP_ERR_INVALID_ARG, "nframes < 0");
+  if (!c->has_probe || !c->has_data) return fail(c, MPBP_ERR_NO_DATA, "probe or data not set");
+  return enqueue_loss_grad(c, rho, u, alpha, frames, nframes, loss, g_rho ? g_rho : c->g_rho_ws,
+                           g_u ? g_u : c->g_u_ws, g_alpha, nullptr, S(stream));
+}
+
+mpbp_status mpbp_loss_grad_host(mpbp_ctx* c, const float* y, const float* rho, const float* u,
+                                const float* alpha, double* loss, float* g_rho, float* g_u,
+                                double* g_alpha, void* stream) {
+  if (!c || !rho || !u || !alpha || !loss) return fail(c, MPBP_ERR_INVALID_ARG, "null argument");
+  if (!c->has_probe) return fail(c, MPBP_ERR_NO_DATA, "probe not set");
+  if (!y && !c->has_data) return fail(c, MPBP_ERR_NO_DATA, "data not set");
+  cudaStream_t s = S(stream);
+  const long long nx = c->npix * (1 + c->C) + c->D;
+  if (!c->io_x) {
+    cudaError_t e = cudaMalloc(&c->io_x, sizeof(float) * nx + sizeof(double) * 2);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->io_x = nullptr;
+      return fail(c, MPBP_ERR_OOM, "host-path buffers");
+    }
+  }
+  if (y) {
+    const long long mm = (long long)c->M * c->M;
+    const long long chunk_frames = std::max<long long>(1, std::min<long long>(c->nframes, (256LL << 20) / (4 * mm)));
+    if (!c->stage) {
+      cudaError_t e = cudaMalloc(&c->stage, sizeof(float) * chunk_frames * mm);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->stage = nullptr;
+        return fail(c, MPBP_ERR_OOM, "host-path staging buffer");
+      }
+      c->stage_elems = chunk_frames * mm;
+    }
+    const long long cf_ = (long long)c->stage_elems / mm;
+    for (long long f0 = 0; f0 < c->nframes; f0 += cf_) {
+      const long long nf = std::min(cf_, c->nframes - f0);
+      MPBP_CUDA(c, cudaMemcpyAsync(c->stage, y + f0 * mm, sizeof(float) * nf * mm,
+                                   cudaMemcpyHostToDevice, s));
+      MPBP_CUDA(c, launch_frame_transpose(c->stage, c->aT + f0 * mm, nf, c->M, true, s));
+    }
+    c->has_data = true;
+  }
+  float* drho = c->io_x;
+  float* du = drho + c->npix;
+  float* dalpha = du + c->npix * c->C;
+  double* dloss = reinterpret_cast<double*>(c->io_x + align_up(nx, 2));
+  MPBP_CUDA(c, cudaMemcpyAsync(drho, rho, sizeof(float) * c->npix, cudaMemcpyHostToDevice, s));
+  MPBP_CUDA(c, cudaMemcpyAsync(du, u, sizeof(float) * c->npix * c->C, cudaMemcpyHostToDevice, s));
+  MPBP_CUDA(c, cudaMemcpyAsync(dalpha, alpha, sizeof(float) * c->D, cudaMemcpyHostToDevice, s));
+  mpbp_status r = enqueue_loss_grad(c, drho, du, dalpha, nullptr, 0, dloss, c->g_rho_ws,
+                                    c->g_u_ws, nullptr, nullptr, s);
+  if (r != MPBP_OK) return r;
+  MPBP_CUDA(c, cudaMemcpyAsync(loss, dloss, sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (g_rho)
+    MPBP_CUDA(c, cudaMemcpyAsync(g_rho, c->g_rho_ws, sizeof(float) * c->npix, cudaMemcpyDeviceToHost, s));
+  if (g_u)
+    MPBP_CUDA(c, cudaMemcpyAsync(g_u, c->g_u_ws, sizeof(float) * c->npix * c->C,
+                                 cudaMemcpyDeviceToHost, s));
+  if (g_alpha)
+    MPBP_CUDA(c, cudaMemcpyAsync(g_alpha, c->g_alpha_ws, sizeof(double) * c->D,
+                                 cudaMemcpyDeviceToHost, s));
+  MPBP_CUDA(c, cudaStreamSynchronize(s));
+  return MPBP_OK;
+}
+
+mpbp_status mpbp_step_init(mpbp_ctx* c, const mpbp_step_params* prm, mpbp_step_state* st,
+                           void* stream) {
+  if (!c || !prm || !st) return fail(c, MPBP_ERR_INVALID_ARG, "null argument");
+  if (!(prm->t0 > 0) || !(prm->grow >= 1) || !(prm->shrink > 0 && prm->shrink < 1) ||
+      !(prm->c_armijo >= 0) || !(prm->w_rho >= 0) || !(prm->w_u >= 0) || !(prm->w_alpha >= 0))
+    return fail(c, MPBP_ERR_INVALID_ARG, "step parameters out of range");
+  mpbp_step_state h{};
+  h.t = prm->t0;
+  h.c_armijo = prm->c_armijo;
+  h.grow = prm->grow;
+  h.shrink = prm->shrink;
+  h.w_rho = prm->w_rho;
+  h.w_u = prm->w_u;
+  h.w_alpha = prm->w_alpha;
+  MPBP_CUDA(c, cudaMemcpyAsync(st, &h, sizeof(h), cudaMemcpyHostToDevice, S(stream)));
+  MPBP_CUDA(c, cudaStreamSynchronize(S(stream)));
+  return MPBP_OK;
+}
+
+mpbp_status mpbp_step(mpbp_ctx* c, float* rho, float* u, float* alpha, mpbp_step_state* st,
+                      void* stream) {
+  if (!c || !rho || !u || !alpha || !st) return fail(c, MPBP_ERR_INVALID_ARG, "null argument");
+  if (!c->has_probe || !c->has_data) return fail(c, MPBP_ERR_NO_DATA, "probe or data not set");
+  cudaStream_t s = S(stream);
+  mpbp_status r = enqueue_loss_grad(c, rho, u, alpha, nullptr, 0, c->loss_ws, c->g_rho_ws,
+                                    c->g_u_ws, nullptr, st, s);
+  if (r != MPBP_OK) return r;
+  StepArgs sa{};
+  sa.rho = rho;
+  sa.u = u;
+  sa.alpha = alpha;
+  sa.g_rho = c->g_rho_ws;
+  sa.g_u = c->g_u_ws;
+  sa.g_alpha = c->g_alpha_ws;
+  sa.rho_base = c->rho_base;
+  sa.u_base = c->u_base;
+  sa.alpha_base = c->alpha_base;
+  sa.g_rho_base = c->g_rho_base;
+  sa.g_u_base = c->g_u_base;
+  sa.g_alpha_base = c->g_alpha_base;
+  sa.st = st;
+  sa.npix = c->npix;
+  sa.C = c->C;
+  sa.D = c->D;
+  sa.alpha_from = 1;
+  MPBP_CUDA(c, launch_step_update(sa, c->num_sms, s));
+  return MPBP_OK;
+}
+
+mpbp_status mpbp_loss_grad_batched(int32_t n, mpbp_ctx* const* ctxs, const float* const* rho,
+                                   const float* const* u, const float* const* alpha,
+                                   double* const* loss, float* const* g_rho, float* const* g_u,
+                                   double* const* g_alpha, void* stream) {
+  if (n < 0 || (n > 0 && (!ctxs || !rho || !u || !alpha || !loss || !g_rho || !g_u)))
+    return MPBP_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    mpbp_status r = mpbp_loss_grad(ctxs[i], rho[i], u[i], alpha[i], nullptr, 0, loss[i], g_rho[i],
+                                   g_u[i], g_alpha ? g_alpha[i] : nullptr, stream);
+    if (r != MPBP_OK) return r;
+  }
+  return MPBP_OK;
+}
+
+mpbp_status mpbp_frames_timing(mpbp_ctx* c, int32_t enable) {
+  if (!c) return MPBP_ERR_INVALID_ARG;
+  c->timing = enable != 0;
+  return MPBP_OK;
+}
+
+mpbp_status mpbp_frames_timing_read(mpbp_ctx* c, double* total_ms, int32_t* count) {
+  if (!c || !total_ms || !count) return fail(c, MPBP_ERR_INVALID_ARG, "null argument");
+  double tot = 0.0;
+  for (size_t i = 0; i < c->ev_used; ++i) {
+    MPBP_CUDA(c, cudaEventSynchronize(c->ev_pool[i].second));
+    float ms = 0.f;
+    MPBP_CUDA(c, cudaEventElapsedTime(&ms, c->ev_pool[i].first, c->ev_pool[i].second));
+    tot += ms;
+  }
+  *total_ms = tot;
+  *count = (int32_t)c->ev_used;
+  c->ev_used = 0;
+  return MPBP_OK;
+}
+
+mpbp_status mpbp_sync_status(mpbp_ctx* c, void* stream) {
+  if (!c) return MPBP_ERR_INVALID_ARG;
+  MPBP_CUDA(c, cudaStreamSynchronize(S(stream)));
+  int h = 0;
+  MPBP_CUDA(c, cudaMemcpy(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) MPBP_CUDA(c, cudaMemset(c->err, 0, sizeof(int)));
+  if (h & kErrBounds) return fail(c, MPBP_ERR_BOUNDS, "frame index out of range");
+  if (h & kErrNonfinite) return fail(c, MPBP_ERR_NONFINITE, "non-finite loss");
+  return MPBP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,286 @@
+// mpbp_aux.cu -- per-pixel and reduction kernels around the fused frame kernel:
+//   A1  object synthesis O_m = alpha_m rho exp(i phi_m)          (Eq. 1, Eq. 3)
+//   data layout: a = sqrt(y) stored transposed per frame
+//   A6/A7 tail: gradient assembly from the patch accumulator
+//   A8  fixed-order FP64 reductions, the line-search decision and the update
+#include "aux_launch.h"
+
+namespace mpbp {
+
+// ----------------------------------------------------------------------------
+// A1: objects
+// ----------------------------------------------------------------------------
+__global__ void object_build_kernel(ObjectArgs a) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < a.npix; p += stride) {
+    const float r = a.rho[p];
+    float uc[kMaxComp];
+#pragma unroll
+    for (int c = 0; c < kMaxComp; ++c) uc[c] = c < a.C ? a.u[c * a.npix + p] : 0.f;
+#pragma unroll
+    for (int m = 0; m < kMaxPeaks; ++m) {
+      if (m < a.D) {
+        float arg = 0.f;
+#pragma unroll
+        for (int c = 0; c < kMaxComp; ++c) arg = fmaf(a.pc.kpi[m][c], uc[c], arg);
+        float sn, cs;
+        sincospif(arg, &sn, &cs);   // exp(i phi), phi = pi * arg
+        const float amp = a.alpha[m] * r;
+        reinterpret_cast<float2*>(a.O)[m * a.npix + p] = make_float2(amp * cs, amp * sn);
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// data: out[f][q1][q0] = g(in[f][q0][q1]), g = sqrt or identity
+// ----------------------------------------------------------------------------
+template <bool SQRT>
+__global__ void frame_transpose_kernel(const float* __restrict__ in, float* __restrict__ out,
+                                       int m, int ts, long long nblocks_per_frame_side) {
+  __shared__ float tile[32][33];
+  const long long tiles_per_frame = nblocks_per_frame_side * nblocks_per_frame_side;
+  const long long b = blockIdx.x;
+  const long long f = b / tiles_per_frame;
+  const int tb = (int)(b - f * tiles_per_frame);
+  const int t0 = (tb / (int)nblocks_per_frame_side) * ts;  // tile row origin (q0)
+  const int t1 = (tb % (int)nblocks_per_frame_side) * ts;  // tile col origin (q1)
+  const float* src = in + f * m * m;
+  float* dst = out + f * m * m;
+  for (int i = threadIdx.y; i < ts; i += blockDim.y) {
+    for (int j = threadIdx.x; j < ts; j += blockDim.x) {
+      float v = src[(long long)(t0 + i) * m + t1 + j];
+      tile[i][j] = SQRT ? sqrtf(v) : v;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < ts; i += blockDim.y) {
+    for (int j = threadIdx.x; j < ts; j += blockDim.x) {
+      dst[(long long)(t1 + i) * m + t0 + j] = tile[j][i];
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// gradient assembly.  With T_m = E_m acc_m (E_m = exp(i phi_m)):
+//   df/drho = sum_m alpha_m Re T_m,  df/dphi_m = -alpha_m rho Im T_m,
+//   df/du_c = sum_m phase_scale G_{m,c} df/dphi_m,  df/dalpha_m = sum_r rho Re T_m.
+// acc is cleared behind the read so the next evaluation starts from zero.
+// ----------------------------------------------------------------------------
+template <int T>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < T / 32; ++i) s += red[i];
+  }
+  __syncthreads();
+  return s;
+}
+
+constexpr int kFinishThreads = 256;
+
+__global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a) {
+  __shared__ double red[kFinishThreads / 32];
+  float ap[kMaxPeaks];
+  for (int m = 0; m < kMaxPeaks; ++m) ap[m] = 0.f;
+  double n_rho = 0.0, n_u = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  float2* acc = reinterpret_cast<float2*>(a.acc);
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < a.npix; p += stride) {
+    const float r = a.rho[p];
+    float uc[kMaxComp];
+#pragma unroll
+    for (int c = 0; c < kMaxComp; ++c) uc[c] = c < a.C ? a.u[c * a.npix + p] : 0.f;
+    float gr = 0.f;
+    float gu[kMaxComp] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int m = 0; m < kMaxPeaks; ++m) {
+      if (m < a.D) {
+        float arg = 0.f;
+#pragma unroll
+        for (int c = 0; c < kMaxComp; ++c) arg = fmaf(a.pc.kpi[m][c], uc[c], arg);
+        float sn, cs;
+        sincospif(arg, &sn, &cs);
+        const float2 A = acc[m * a.npix + p];
+        acc[m * a.npix + p] = make_float2(0.f, 0.f);
+        const float Tr = fmaf(cs, A.x, -sn * A.y);
+        const float Ti = fmaf(cs, A.y, sn * A.x);
+        const float am = a.alpha[m];
+        gr = fmaf(am, Tr, gr);
+        const float dphi = -am * r * Ti;
+#pragma unroll
+        for (int c = 0; c < kMaxComp; ++c) gu[c] = fmaf(a.pc.kps[m][c], dphi, gu[c]);
+        ap[m] = fmaf(r, Tr, ap[m]);
+      }
+    }
+    a.g_rho[p] = gr;
+    float su = 0.f;
+#pragma unroll
+    for (int c = 0; c < kMaxComp; ++c) {
+      if (c < a.C) {
+        a.g_u[c * a.npix + p] = gu[c];
+        su = fmaf(gu[c], gu[c], su);
+      }
+    }
+    n_rho += (double)(gr * gr);
+    n_u += (double)su;
+  }
+  double* out = a.part + (long long)blockIdx.x * (a.D + 2);
+#pragma unroll
+  for (int m = 0; m < kMaxPeaks; ++m) {
+    if (m < a.D) {
+      const double t = block_sum<kFinishThreads>((double)ap[m], red);
+      if (threadIdx.x == 0) out[m] = t;
+    }
+  }
+  const double t0 = block_sum<kFinishThreads>(n_rho, red);
+  const double t1 = block_sum<kFinishThreads>(n_u, red);
+  if (threadIdx.x == 0) {
+    out[a.D] = t0;
+    out[a.D + 1] = t1;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// A8: fixed-order reductions (one block), optional line-search decision
+// ----------------------------------------------------------------------------
+constexpr int kReduceThreads = 256;
+
+__global__ void __launch_bounds__(kReduceThreads) reduce_kernel(ReduceArgs a) {
+  __shared__ double red[kReduceThreads / 32];
+  __shared__ double galpha[kMaxPeaks + 2];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < a.n_loss_part; i += blockDim.x) v += a.loss_part[i];
+  const double loss = block_sum<kReduceThreads>(v, red);
+  for (int m = 0; m < a.D + 2; ++m) {
+    double w = 0.0;
+    for (int i = threadIdx.x; i < a.n_part; i += blockDim.x) w += a.part[(long long)i * (a.D + 2) + m];
+    const double t = block_sum<kReduceThreads>(w, red);
+    if (threadIdx.x == 0) galpha[m] = t;
+  }
+  if (threadIdx.x != 0) return;
+  const bool finite = isfinite(loss);
+  if (!finite) atomicOr(a.err, kErrNonfinite);
+  if (a.loss_out) *a.loss_out = loss;
+  for (int m = 0; m < a.D; ++m) {
+    if (a.g_alpha_out) a.g_alpha_out[m] = galpha[m];
+    if (a.g_alpha_ws) a.g_alpha_ws[m] = galpha[m];
+  }
+  mpbp_step_state* st = a.st;
+  if (!st) return;
+  // lagged Armijo decision in FP64
+  // weighted squared norm of the descent direction (alpha_0 is not a variable)
+  double gn2 = st->w_rho * galpha[a.D] + st->w_u * galpha[a.D + 1];
+  for (int m = a.alpha_from; m < a.D; ++m) gn2 += st->w_alpha * galpha[m] * galpha[m];
+  bool accept;
+  if (st->k == 0) accept = finite;
+  else accept = finite && (loss <= st->f_prev - st->c_armijo * st->t * st->gn2_prev);
+  if (accept) {
+    if (st->k > 0) st->t *= st->grow;
+    st->f_prev = loss;
+    st->gn2_prev = gn2;
+    st->n_accept += 1;
+  } else {
+    st->t *= st->shrink;
+    st->n_reject += 1;
+  }
+  st->accepted = accept ? 1 : 0;
+  st->f_last = loss;
+  st->k += 1;
+}
+
+// ----------------------------------------------------------------------------
+// A8: x = x_base - t w g_base; on acceptance the current point becomes the base
+// ----------------------------------------------------------------------------
+__global__ void step_update_kernel(StepArgs a) {
+  const mpbp_step_state* st = a.st;
+  const bool acc = st->accepted != 0;
+  const float wr = (float)(st->t * st->w_rho), wu = (float)(st->t * st->w_u);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long n_ru = a.npix * (1 + a.C);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_ru; i += stride) {
+    const bool is_rho = i < a.npix;
+    float* x = is_rho ? a.rho + i : a.u + (i - a.npix);
+    float* xb = is_rho ? a.rho_base + i : a.u_base + (i - a.npix);
+    const float* g = is_rho ? a.g_rho + i : a.g_u + (i - a.npix);
+    float* gb = is_rho ? a.g_rho_base + i : a.g_u_base + (i - a.npix);
+    const float w = is_rho ? wr : wu;
+    float base, gbase;
+    if (acc) {
+      base = *x;
+      gbase = *g;
+      *xb = base;
+      *gb = gbase;
+    } else {
+      base = *xb;
+      gbase = *gb;
+    }
+    *x = fmaf(-w, gbase, base);
+  }
+  if (blockIdx.x == 0 && threadIdx.x < a.D) {
+    const int m = threadIdx.x;
+    double base, gbase;
+    if (acc) {
+      base = a.alpha[m];
+      gbase = a.g_alpha[m];
+      a.alpha_base[m] = (float)base;
+      a.g_alpha_base[m] = gbase;
+    } else {
+      base = a.alpha_base[m];
+      gbase = a.g_alpha_base[m];
+    }
+    a.alpha[m] = m < a.alpha_from ? (float)base : (float)(base - st->t * st->w_alpha * gbase);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// launchers
+// ----------------------------------------------------------------------------
+static int grid_for(long long n, int threads, int cap) {
+  long long g = (n + threads - 1) / threads;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+cudaError_t launch_object_build(const ObjectArgs& a, int num_sms, cudaStream_t s) {
+  object_build_kernel<<<grid_for(a.npix, 256, num_sms * 8), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_frame_transpose(const float* in, float* out, long long nframes, int m,
+                                   bool take_sqrt, cudaStream_t s) {
+  const int ts = m < 32 ? m : 32;
+  const long long side = m / ts;
+  const long long nb = nframes * side * side;
+  if (nb == 0) return cudaSuccess;
+  dim3 block(ts, ts < 8 ? ts : 8);
+  if (take_sqrt) frame_transpose_kernel<true><<<(unsigned)nb, block, 0, s>>>(in, out, m, ts, side);
+  else frame_transpose_kernel<false><<<(unsigned)nb, block, 0, s>>>(in, out, m, ts, side);
+  return cudaGetLastError();
+}
+
+int finish_grid(long long npix, int num_sms) {
+  return grid_for(npix, kFinishThreads, num_sms * 4);
+}
+
+cudaError_t launch_finish(const FinishArgs& a, int grid, cudaStream_t s) {
+  finish_kernel<<<grid, kFinishThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t s) {
+  reduce_kernel<<<1, kReduceThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_update(const StepArgs& a, int num_sms, cudaStream_t s) {
+  step_update_kernel<<<grid_for(a.npix * (1 + a.C), 256, num_sms * 8), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace mpbp

@@ -1,0 +1,81 @@
+// mpbp_internal.h -- structures shared by the host API and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft_reg.cuh"
+#include "mpbp.h"
+
+namespace mpbp {
+
+constexpr int kMaxPeaks = 16;
+constexpr int kMaxComp = 3;
+
+// device error word bits
+constexpr int kErrBounds = 1;
+constexpr int kErrNonfinite = 2;
+
+// Arguments of the fused per-frame kernel (A2..A7 of the hot path).
+struct FrameArgs {
+  const cf* O;          // [D][n1][n2] objects O_m
+  const cf* probe;      // [Dp][M][M]
+  const float* aT;      // [D*J][M][M] sqrt(y), each frame stored transposed [q1][q0]
+  const float* bgT;     // same layout as aT, or nullptr
+  const int2* scan;     // [J] top-left (row, col)
+  const int* frames;    // frame list or nullptr
+  cf* acc;              // [D][n1][n2] sum_j P conj(ghat_j), patch-aligned
+  double* loss_part;    // [gridDim.x] per-block loss partials
+  float* I_out;         // forward mode: [D*J][M][M]
+  int* err;             // device error word
+  long long obj_stride; // n1*n2
+  int nframes;          // frames to process
+  int nframes_total;    // D*J (bound for frame indices)
+  int n1, n2, J;
+  int probe_stride;     // M*M when one probe per peak, else 0
+};
+
+// Per-pixel coefficients of phi_m = phase_scale * G_m . u.
+struct PhaseCoef {
+  float kpi[kMaxPeaks][kMaxComp];  // phase_scale * G / pi  (argument of sincospif)
+  float kps[kMaxPeaks][kMaxComp];  // phase_scale * G       (d phi_m / d u_c)
+};
+
+struct ObjectArgs {
+  const float* rho;
+  const float* u;
+  const float* alpha;
+  cf* O;
+  long long npix;
+  int D, C;
+  PhaseCoef pc;
+};
+
+// Per-pixel gradient assembly (A6/A7 tail) and its partial sums.
+struct FinishArgs {
+  const float* rho;
+  const float* u;
+  const float* alpha;
+  cf* acc;              // read, then cleared for the next evaluation
+  float* g_rho;
+  float* g_u;
+  double* part;         // [gridDim.x][D + 2]: df/dalpha_m partials, |g_rho|^2, |g_u|^2
+  long long npix;
+  int D, C;
+  PhaseCoef pc;
+};
+
+struct ReduceArgs {
+  const double* loss_part;
+  int n_loss_part;
+  const double* part;
+  int n_part;
+  int D;
+  double* loss_out;
+  double* g_alpha_out;  // nullable
+  double* g_alpha_ws;   // workspace copy for the optimizer (nullable)
+  int* err;
+  mpbp_step_state* st;  // nullable: decide an optimizer step
+  int alpha_from;       // first alpha index that is a variable (1)
+};
+
+}  // namespace mpbp

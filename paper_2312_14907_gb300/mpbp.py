@@ -1,0 +1,373 @@
+"""Python binding of the MPBP C ABI (include/mpbp.h).
+
+Argument marshalling only: every step of the loss and gradient runs in the
+CUDA kernels of libmpbp.so.  PyTorch supplies device memory and the current
+stream.  There is no CPU fallback: without the library or a GPU every call
+raises.
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libmpbp.so")
+_lib = None
+
+STATUS = {0: "MPBP_OK", 1: "MPBP_ERR_INVALID_ARG", 2: "MPBP_ERR_UNSUPPORTED", 3: "MPBP_ERR_CUDA",
+          4: "MPBP_ERR_NONFINITE", 5: "MPBP_ERR_TIMEOUT", 6: "MPBP_ERR_BOUNDS", 7: "MPBP_ERR_OOM",
+          8: "MPBP_ERR_NO_DATA"}
+
+
+class MPBPError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__("%s%s" % (STATUS.get(status, status), (": " + msg) if msg else ""))
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("n1", ctypes.c_int32), ("n2", ctypes.c_int32), ("ncomp", ctypes.c_int32),
+                ("npeaks", ctypes.c_int32), ("m", ctypes.c_int32), ("nscan", ctypes.c_int32),
+                ("G", ctypes.POINTER(ctypes.c_double)), ("scan", ctypes.POINTER(ctypes.c_int32)),
+                ("probe_per_peak", ctypes.c_int32), ("phase_scale", ctypes.c_double)]
+
+
+class StepParams(ctypes.Structure):
+    _fields_ = [("c_armijo", ctypes.c_double), ("grow", ctypes.c_double),
+                ("shrink", ctypes.c_double), ("t0", ctypes.c_double), ("w_rho", ctypes.c_double),
+                ("w_u", ctypes.c_double), ("w_alpha", ctypes.c_double)]
+
+
+class StepState(ctypes.Structure):
+    _fields_ = [("f_prev", ctypes.c_double), ("gn2_prev", ctypes.c_double),
+                ("t", ctypes.c_double), ("f_last", ctypes.c_double), ("k", ctypes.c_int32),
+                ("accepted", ctypes.c_int32), ("n_accept", ctypes.c_int32),
+                ("n_reject", ctypes.c_int32), ("c_armijo", ctypes.c_double),
+                ("grow", ctypes.c_double), ("shrink", ctypes.c_double), ("w_rho", ctypes.c_double),
+                ("w_u", ctypes.c_double), ("w_alpha", ctypes.c_double)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("workspace_bytes", ctypes.c_int64), ("frames_grid", ctypes.c_int32),
+                ("frames_block", ctypes.c_int32), ("frames_smem", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("num_sms", ctypes.c_int32),
+                ("launches_loss_grad", ctypes.c_int32), ("launches_step", ctypes.c_int32)]
+
+
+EXPORTS = ["mpbp_status_string", "mpbp_create", "mpbp_destroy", "mpbp_last_error",
+           "mpbp_get_info", "mpbp_set_probe", "mpbp_set_data", "mpbp_object_build",
+           "mpbp_forward", "mpbp_loss_grad", "mpbp_loss_grad_host", "mpbp_step_init",
+           "mpbp_step", "mpbp_loss_grad_batched", "mpbp_set_schedule", "mpbp_sync_status",
+           "mpbp_frames_timing", "mpbp_frames_timing_read"]
+
+
+def library_path():
+    return _LIB_PATH
+
+
+def load(build_if_missing=True):
+    """Loads libmpbp.so (building it with nvcc first if it is absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        if not build_if_missing:
+            raise MPBPError(3, "libmpbp.so is not built")
+        from . import build as _build
+        _build.build()
+    lib = ctypes.CDLL(_LIB_PATH)
+    V, I32, D, P = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.POINTER
+    st = ctypes.c_int
+    lib.mpbp_status_string.argtypes = [st]
+    lib.mpbp_status_string.restype = ctypes.c_char_p
+    lib.mpbp_create.argtypes = [P(_Problem), P(V)]
+    lib.mpbp_create.restype = st
+    lib.mpbp_destroy.argtypes = [V]
+    lib.mpbp_destroy.restype = None
+    lib.mpbp_last_error.argtypes = [V]
+    lib.mpbp_last_error.restype = ctypes.c_char_p
+    lib.mpbp_get_info.argtypes = [V, P(Info)]
+    lib.mpbp_get_info.restype = st
+    lib.mpbp_set_probe.argtypes = [V, V, V]
+    lib.mpbp_set_probe.restype = st
+    lib.mpbp_set_data.argtypes = [V, V, V, V]
+    lib.mpbp_set_data.restype = st
+    lib.mpbp_object_build.argtypes = [V, V, V, V, V, V]
+    lib.mpbp_object_build.restype = st
+    lib.mpbp_forward.argtypes = [V, V, V, V, V, V]
+    lib.mpbp_forward.restype = st
+    lib.mpbp_loss_grad.argtypes = [V, V, V, V, V, I32, V, V, V, V, V]
+    lib.mpbp_loss_grad.restype = st
+    lib.mpbp_loss_grad_host.argtypes = [V, V, V, V, V, V, V, V, V, V]
+    lib.mpbp_loss_grad_host.restype = st
+    lib.mpbp_step_init.argtypes = [V, P(StepParams), V, V]
+    lib.mpbp_step_init.restype = st
+    lib.mpbp_step.argtypes = [V, V, V, V, V, V]
+    lib.mpbp_step.restype = st
+    lib.mpbp_loss_grad_batched.argtypes = [I32, V, V, V, V, V, V, V, V, V]
+    lib.mpbp_loss_grad_batched.restype = st
+    lib.mpbp_set_schedule.argtypes = [V, I32]
+    lib.mpbp_set_schedule.restype = st
+    lib.mpbp_sync_status.argtypes = [V, V]
+    lib.mpbp_sync_status.restype = st
+    lib.mpbp_frames_timing.argtypes = [V, I32]
+    lib.mpbp_frames_timing.restype = st
+    lib.mpbp_frames_timing_read.argtypes = [V, P(D), P(I32)]
+    lib.mpbp_frames_timing_read.restype = st
+    _lib = lib
+    return lib
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _p(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dev(t, dtype, shape, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return t
+
+
+def _host(t, dtype, shape, name):
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError("%s must be a CPU tensor" % name)
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous %s tensor of shape %s" % (name, dtype, tuple(shape)))
+    return t
+
+
+class Problem:
+    """One MPBP problem on the current CUDA device (wraps an mpbp_ctx)."""
+
+    def __init__(self, n1, n2, ncomp, npeaks, m, scan, G, phase_scale=2 * math.pi,
+                 probe_per_peak=False):
+        self._lib = load()
+        self.n1, self.n2, self.ncomp, self.npeaks, self.m = int(n1), int(n2), int(ncomp), int(npeaks), int(m)
+        self._scan = np.ascontiguousarray(scan, dtype=np.int32).reshape(-1, 2)
+        self._G = np.ascontiguousarray(G, dtype=np.float64).reshape(self.npeaks, self.ncomp)
+        self.nscan = self._scan.shape[0]
+        self.phase_scale = float(phase_scale)
+        self.probe_per_peak = bool(probe_per_peak)
+        pr = _Problem(self.n1, self.n2, self.ncomp, self.npeaks, self.m, self.nscan,
+                      self._G.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                      self._scan.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                      int(self.probe_per_peak), self.phase_scale)
+        h = ctypes.c_void_p()
+        s = self._lib.mpbp_create(ctypes.byref(pr), ctypes.byref(h))
+        if s != 0:
+            raise MPBPError(s, "mpbp_create")
+        self._h = h
+        self.device = torch.cuda.current_device()
+
+    @classmethod
+    def from_spec(cls, spec, scan):
+        return cls(spec.n1, spec.n2, spec.ncomp, spec.npeaks, spec.m, scan, spec.G,
+                   spec.phase_scale, spec.probe_per_peak)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mpbp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # shapes
+    @property
+    def nframes(self):
+        return self.npeaks * self.nscan
+
+    @property
+    def shapes(self):
+        return {"rho": (self.n1, self.n2), "u": (self.ncomp, self.n1, self.n2),
+                "alpha": (self.npeaks,), "frames": (self.npeaks, self.nscan, self.m, self.m)}
+
+    def _check(self, s, what):
+        if s != 0:
+            raise MPBPError(s, "%s: %s" % (what, self._lib.mpbp_last_error(self._h).decode()))
+
+    def _state(self, rho, u, alpha):
+        sh = self.shapes
+        _dev(rho, torch.float32, sh["rho"], "rho")
+        _dev(u, torch.float32, sh["u"], "u")
+        _dev(alpha, torch.float32, sh["alpha"], "alpha")
+
+    def info(self):
+        inf = Info()
+        self._check(self._lib.mpbp_get_info(self._h, ctypes.byref(inf)), "mpbp_get_info")
+        return {k: getattr(inf, k) for k, _ in Info._fields_}
+
+    def set_schedule(self, blocks_per_sm):
+        self._check(self._lib.mpbp_set_schedule(self._h, int(blocks_per_sm)), "mpbp_set_schedule")
+
+    def set_probe(self, probe):
+        shape = (self.npeaks, self.m, self.m) if self.probe_per_peak else (self.m, self.m)
+        _dev(probe, torch.complex64, shape, "probe")
+        self._probe = probe
+        self._check(self._lib.mpbp_set_probe(self._h, _p(probe), _stream()), "mpbp_set_probe")
+
+    def set_data(self, y, bg=None):
+        _dev(y, torch.float32, self.shapes["frames"], "y")
+        if bg is not None:
+            _dev(bg, torch.float32, self.shapes["frames"], "bg")
+        self._check(self._lib.mpbp_set_data(self._h, _p(y), _p(bg), _stream()), "mpbp_set_data")
+
+    def object_build(self, rho, u, alpha, out=None):
+        self._state(rho, u, alpha)
+        if out is None:
+            out = torch.empty((self.npeaks, self.n1, self.n2), dtype=torch.complex64, device=rho.device)
+        self._check(self._lib.mpbp_object_build(self._h, _p(rho), _p(u), _p(alpha), _p(out),
+                                                _stream()), "mpbp_object_build")
+        return out
+
+    def forward(self, rho, u, alpha, out=None):
+        self._state(rho, u, alpha)
+        if out is None:
+            out = torch.empty(self.shapes["frames"], dtype=torch.float32, device=rho.device)
+        self._check(self._lib.mpbp_forward(self._h, _p(rho), _p(u), _p(alpha), _p(out), _stream()),
+                    "mpbp_forward")
+        return out
+
+    def loss_grad(self, rho, u, alpha, frames=None, out=None):
+        """Returns (loss [1] float64, g_rho, g_u, g_alpha [D] float64), all on the device."""
+        self._state(rho, u, alpha)
+        dev = rho.device
+        if out is None:
+            out = (torch.empty(1, dtype=torch.float64, device=dev),
+                   torch.empty(self.shapes["rho"], dtype=torch.float32, device=dev),
+                   torch.empty(self.shapes["u"], dtype=torch.float32, device=dev),
+                   torch.empty(self.npeaks, dtype=torch.float64, device=dev))
+        loss, g_rho, g_u, g_alpha = out
+        nfr = 0
+        if frames is not None:
+            if not (frames.is_cuda and frames.dtype == torch.int32 and frames.dim() == 1
+                    and frames.is_contiguous()):
+                raise TypeError("frames must be a contiguous int32 CUDA vector")
+            nfr = frames.numel()
+            if nfr == 0:
+                # an empty list still needs a non-null pointer (NULL means all frames)
+                frames = torch.zeros(1, dtype=torch.int32, device=dev)
+        self._check(self._lib.mpbp_loss_grad(self._h, _p(rho), _p(u), _p(alpha), _p(frames), nfr,
+                                             _p(loss), _p(g_rho), _p(g_u), _p(g_alpha), _stream()),
+                    "mpbp_loss_grad")
+        return loss, g_rho, g_u, g_alpha
+
+    def loss_grad_host(self, rho, u, alpha, y=None, out=None):
+        """Host-buffer variant (copies in, evaluates, copies out, synchronises)."""
+        sh = self.shapes
+        _host(rho, torch.float32, sh["rho"], "rho")
+        _host(u, torch.float32, sh["u"], "u")
+        _host(alpha, torch.float32, sh["alpha"], "alpha")
+        if y is not None:
+            _host(y, torch.float32, sh["frames"], "y")
+        if out is None:
+            out = (torch.empty(1, dtype=torch.float64), torch.empty(sh["rho"], dtype=torch.float32),
+                   torch.empty(sh["u"], dtype=torch.float32), torch.empty(self.npeaks, dtype=torch.float64))
+        loss, g_rho, g_u, g_alpha = out
+        self._check(self._lib.mpbp_loss_grad_host(self._h, _p(y), _p(rho), _p(u), _p(alpha),
+                                                  _p(loss), _p(g_rho), _p(g_u), _p(g_alpha),
+                                                  _stream()), "mpbp_loss_grad_host")
+        return loss, g_rho, g_u, g_alpha
+
+    def step_init(self, t0, c_armijo=1e-4, grow=1.25, shrink=0.5, w_rho=1.0, w_u=1.0, w_alpha=1.0,
+                  state=None):
+        prm = StepParams(c_armijo, grow, shrink, t0, w_rho, w_u, w_alpha)
+        if state is None:
+            state = torch.zeros(ctypes.sizeof(StepState), dtype=torch.uint8, device="cuda")
+        self._check(self._lib.mpbp_step_init(self._h, ctypes.byref(prm), _p(state), _stream()),
+                    "mpbp_step_init")
+        return state
+
+    def step(self, rho, u, alpha, state):
+        self._state(rho, u, alpha)
+        self._check(self._lib.mpbp_step(self._h, _p(rho), _p(u), _p(alpha), _p(state), _stream()),
+                    "mpbp_step")
+
+    @staticmethod
+    def read_state(state):
+        raw = state.cpu().numpy().tobytes()
+        return StepState.from_buffer_copy(raw)
+
+    def frames_timing(self, enable=True):
+        self._check(self._lib.mpbp_frames_timing(self._h, int(bool(enable))), "mpbp_frames_timing")
+
+    def frames_timing_read(self):
+        """(total milliseconds, launches) of the fused frame kernel since the last read."""
+        ms, n = ctypes.c_double(), ctypes.c_int32()
+        self._check(self._lib.mpbp_frames_timing_read(self._h, ctypes.byref(ms), ctypes.byref(n)),
+                    "mpbp_frames_timing_read")
+        return ms.value, n.value
+
+    def sync_status(self):
+        s = self._lib.mpbp_sync_status(self._h, _stream())
+        if s != 0:
+            raise MPBPError(s, self._lib.mpbp_last_error(self._h).decode())
+
+
+def loss_grad_batched(problems, states, outs=None):
+    """Loss and gradient of several problems in one call.  states: list of
+    (rho, u, alpha) device tensors; returns a list of (loss, g_rho, g_u, g_alpha)."""
+    lib = load()
+    n = len(problems)
+    if outs is None:
+        outs = []
+        for p, (rho, u, alpha) in zip(problems, states):
+            dev = rho.device
+            outs.append((torch.empty(1, dtype=torch.float64, device=dev),
+                         torch.empty(p.shapes["rho"], dtype=torch.float32, device=dev),
+                         torch.empty(p.shapes["u"], dtype=torch.float32, device=dev),
+                         torch.empty(p.npeaks, dtype=torch.float64, device=dev)))
+    for p, (rho, u, alpha) in zip(problems, states):
+        p._state(rho, u, alpha)
+    arr = lambda xs: (ctypes.c_void_p * n)(*[x.data_ptr() if isinstance(x, torch.Tensor) else x for x in xs])
+    ctxs = (ctypes.c_void_p * n)(*[p._h.value for p in problems])
+    s = lib.mpbp_loss_grad_batched(n, ctxs, arr([s[0] for s in states]), arr([s[1] for s in states]),
+                                   arr([s[2] for s in states]), arr([o[0] for o in outs]),
+                                   arr([o[1] for o in outs]), arr([o[2] for o in outs]),
+                                   arr([o[3] for o in outs]), _stream())
+    if s != 0:
+        raise MPBPError(s, "mpbp_loss_grad_batched")
+    return outs
+
+
+class MPBPLoss(torch.autograd.Function):
+    """f(rho, u, alpha) of Eq. 4 with the hand-written adjoint as its backward.
+
+    forward runs the fused loss+gradient pass once and keeps only the
+    object-sized gradients; backward scales them by the incoming gradient.
+    Exit waves are never stored."""
+
+    @staticmethod
+    def forward(ctx, rho, u, alpha, problem):
+        loss, g_rho, g_u, g_alpha = problem.loss_grad(rho.detach().contiguous(),
+                                                      u.detach().contiguous(),
+                                                      alpha.detach().contiguous())
+        ctx.save_for_backward(g_rho, g_u, g_alpha)
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        g_rho, g_u, g_alpha = ctx.saved_tensors
+        go = grad_out.to(torch.float32)
+        return go * g_rho, go * g_u, (grad_out * g_alpha).to(torch.float32), None
+
+
+def mpbp_loss(rho, u, alpha, problem):
+    return MPBPLoss.apply(rho, u, alpha, problem)

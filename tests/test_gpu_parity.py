@@ -1,0 +1,228 @@
+"""CUDA path vs the FP64 oracle, element by element, on seeded inputs.
+
+Tolerances (FP32 kernels against an FP64 definition): loss relative error
+<= 1e-5; each gradient block (rho, u, alpha) relative L2 error <= 1e-4;
+objects and intensities relative L2 error <= 1e-5.
+"""
+import numpy as np
+import pytest
+
+from helpers import Case, custom_spec, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+LOSS_TOL = 1e-5
+GRAD_TOL = 1e-4
+
+
+def _gpu(case):
+    from paper_2312_14907_gb300 import mpbp
+    p = mpbp.Problem.from_spec(case.spec, case.scan)
+    p.set_probe(torch.from_numpy(case.probe).cuda())
+    p.set_data(torch.from_numpy(case.y).cuda(),
+               None if case.bg is None else torch.from_numpy(case.bg).cuda())
+    x = tuple(torch.from_numpy(a).cuda() for a in (case.rho, case.u, case.alpha))
+    return p, x
+
+
+def _check_loss_grad(case, got, frames=None, tol=GRAD_TOL):
+    f, gr, gu, ga = case.oracle_loss_grad(frames=frames)
+    loss, g_rho, g_u, g_alpha = [t.cpu().numpy() for t in got]
+    assert abs(loss[0] - f) <= LOSS_TOL * abs(f), (loss[0], f)
+    assert rel_l2(g_rho, gr) <= tol, rel_l2(g_rho, gr)
+    for c in range(gu.shape[0]):
+        if np.abs(gu[c]).max() > 0:
+            assert rel_l2(g_u[c], gu[c]) <= tol, (c, rel_l2(g_u[c], gu[c]))
+        else:
+            assert np.abs(g_u[c]).max() <= 1e-6 * np.abs(gu).max()
+    assert rel_l2(g_alpha, ga) <= tol, (g_alpha, ga)
+
+
+# (n, m, scan side, step, offset, peaks, comps): several tiles and ragged edges
+SIZES = [
+    (20, 8, 5, 3, -2, 2, 3),
+    (40, 16, 6, 5, -3, 3, 3),
+    (64, 32, 7, 4, 4, 3, 3),
+    (72, 32, 5, 11, -6, 4, 2),
+    (128, 64, 5, 16, -8, 3, 3),
+    (200, 128, 3, 40, -20, 2, 3),
+]
+
+
+@pytest.mark.parametrize("n,m,side,step,off,D,C", SIZES)
+def test_loss_grad_matches_oracle(n, m, side, step, off, D, C):
+    spec, scan = custom_spec(n, m, side, step, npeaks=D, ncomp=C, offset=off)
+    case = Case(spec, scan=scan, state="perturbed")
+    p, x = _gpu(case)
+    _check_loss_grad(case, p.loss_grad(*x))
+    p.sync_status()
+
+
+@pytest.mark.parametrize("m", [8, 16, 32, 64, 128])
+def test_forward_and_objects_match_oracle(m):
+    n = max(2 * m, 24)
+    spec, scan = custom_spec(n, m, 3, m // 2, npeaks=2, offset=-m // 4)
+    rng = np.random.default_rng(m)
+    probe = (rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))).astype(np.complex64)
+    case = Case(spec, scan=scan, probe=probe, state="perturbed")
+    p, x = _gpu(case)
+    O = p.object_build(*x).cpu().numpy()
+    O_ref = case.oracle.object_build(case.rho, case.u, case.alpha)
+    assert rel_l2(O, O_ref) <= 1e-6
+    I = p.forward(*x).cpu().numpy()
+    I_ref = case.oracle.forward(case.rho, case.u, case.alpha, case.probe)
+    for d in range(spec.npeaks):
+        for j in range(case.scan.shape[0]):
+            assert rel_l2(I[d, j], I_ref[d, j]) <= 1e-5, (d, j)
+
+
+@pytest.mark.parametrize("m", [16, 64, 128])
+def test_random_probe_per_peak_and_background(m):
+    """Unstructured per-peak probes catch transposed or mis-indexed operands;
+    the background enters the intensity of Eq. 2."""
+    n = 2 * m + 8
+    spec, scan = custom_spec(n, m, 3, m // 2 + 1, npeaks=3, offset=-3, probe_per_peak=True)
+    rng = np.random.default_rng(100 + m)
+    probe = (rng.standard_normal((3, m, m)) + 1j * rng.standard_normal((3, m, m))).astype(np.complex64)
+    case = Case(spec, scan=scan, probe=probe, state="perturbed", bg=True)
+    p, x = _gpu(case)
+    _check_loss_grad(case, p.loss_grad(*x))
+    I = p.forward(*x).cpu().numpy()
+    I_ref = case.oracle.forward(case.rho, case.u, case.alpha, case.probe, bg=case.bg)
+    assert rel_l2(I, I_ref) <= 1e-5
+
+
+def test_frame_subset_matches_oracle():
+    spec, scan = custom_spec(64, 32, 6, 6, npeaks=3, offset=0)
+    case = Case(spec, scan=scan, state="perturbed")
+    p, x = _gpu(case)
+    frames = np.random.default_rng(3).permutation(case.oracle.nframes)[:37].astype(np.int32)
+    got = p.loss_grad(*x, frames=torch.from_numpy(frames).cuda())
+    _check_loss_grad(case, got, frames=frames)
+    # a frame listed twice counts twice (Eq. 11 is a plain sum)
+    frames2 = np.concatenate([frames, frames[:5]]).astype(np.int32)
+    got = p.loss_grad(*x, frames=torch.from_numpy(frames2).cuda())
+    _check_loss_grad(case, got, frames=frames2)
+    # empty minibatch: zero loss and gradient
+    loss, g_rho, g_u, g_alpha = p.loss_grad(*x, frames=torch.zeros(0, dtype=torch.int32, device="cuda"))
+    assert loss.item() == 0.0 and g_rho.abs().max().item() == 0.0 and g_u.abs().max().item() == 0.0
+
+
+def test_frame_index_out_of_range_is_reported():
+    from paper_2312_14907_gb300 import mpbp
+    spec, scan = custom_spec(40, 16, 3, 8, npeaks=2, offset=0)
+    case = Case(spec, scan=scan)
+    p, x = _gpu(case)
+    frames = torch.tensor([0, 5, 10_000, -1], dtype=torch.int32, device="cuda")
+    p.loss_grad(*x, frames=frames)
+    with pytest.raises(mpbp.MPBPError) as ei:
+        p.sync_status()
+    assert ei.value.status == 6
+    # the skipped slots do not contribute; the context stays usable
+    got = p.loss_grad(*x, frames=frames[:2].contiguous())
+    _check_loss_grad(case, got, frames=np.array([0, 5], np.int32))
+    p.sync_status()
+
+
+def _check_loss_only(case, got):
+    f = case.oracle_loss_grad()[0]
+    assert abs(got[0].item() - f) <= LOSS_TOL * abs(f), (got[0].item(), f)
+
+
+def test_config1_start_and_truth():
+    """The 64x64 / M=32 / 3-peak problem: the loss at the reconstruction start
+    (rho = 1, u = 0), loss and gradient near the truth, near-zero loss at the
+    truth on noise-free data.
+
+    At the flat start the far field of the smooth probe falls below rounding
+    noise (in FP64 as well) over most of each frame, and there the factor
+    Psi/|Psi| of the gradient has a rounding-determined phase: the gradient is
+    not a well-conditioned quantity at that state, so only the loss is compared."""
+    from paper_2312_14907_gb300 import synth
+    case = Case(synth.config(1), state="init")
+    p, x = _gpu(case)
+    _check_loss_only(case, p.loss_grad(*x))
+    case = Case(synth.config(1), state="perturbed")
+    p, x = _gpu(case)
+    _check_loss_grad(case, p.loss_grad(*x))
+    clean = Case(synth.config(1), state="truth", noise=False)
+    p, x = _gpu(clean)
+    loss = p.loss_grad(*x)[0].item()
+    assert loss <= 1e-9 * float(clean.y.sum())
+
+
+def test_gpu_invariances():
+    """Eq. 6: a uniform displacement and lattice-vector jumps leave the loss unchanged;
+    translation invariance makes every df/du_c sum to zero."""
+    spec, scan = custom_spec(64, 32, 5, 6, npeaks=3, offset=4)
+    case = Case(spec, scan=scan, state="perturbed")
+    p, x = _gpu(case)
+    rho, u, alpha = x
+    f0, _, g_u, _ = p.loss_grad(rho, u, alpha)
+    f0 = f0.item()
+    f1 = p.loss_grad(rho, (u + torch.tensor([0.3, -0.7, 1.1], device="cuda")[:, None, None]).contiguous(),
+                     alpha)[0].item()
+    assert abs(f1 - f0) <= 2e-5 * f0
+    mask = (torch.rand(u.shape[1:], generator=torch.Generator().manual_seed(1)) < 0.3).cuda()
+    u2 = u.clone()
+    u2[0] += mask.float()
+    u2[2] -= mask.float()
+    f2 = p.loss_grad(rho, u2, alpha)[0].item()
+    assert abs(f2 - f0) <= 2e-5 * f0
+    g = g_u.double()
+    for c in range(3):
+        assert abs(g[c].sum().item()) <= 1e-4 * g[c].abs().sum().item()
+
+
+def test_full_bench_problem_matches_oracle():
+    """The 256x256 / M=64 / 31x31 scan / 3-peak problem, all 2883 frames, in
+    the launch configuration the benchmark times."""
+    from paper_2312_14907_gb300 import synth
+    case = Case(synth.config(2), state="init")
+    p, x = _gpu(case)
+    _check_loss_only(case, p.loss_grad(*x))
+    case2 = Case(synth.config(2), state="perturbed", seed=1)
+    p2, x2 = _gpu(case2)
+    _check_loss_grad(case2, p2.loss_grad(*x2))
+
+
+def test_host_buffer_entry_point_matches_device_path():
+    spec, scan = custom_spec(128, 64, 4, 12, npeaks=3, offset=8)
+    case = Case(spec, scan=scan, state="perturbed")
+    p, x = _gpu(case)
+    dev = [t.cpu().numpy() for t in p.loss_grad(*x)]
+    pin = lambda a: torch.from_numpy(a).pin_memory()
+    host = p.loss_grad_host(pin(case.rho), pin(case.u), pin(case.alpha), y=pin(case.y))
+    host = [t.numpy() for t in host]
+    assert abs(host[0][0] - dev[0][0]) <= 1e-6 * abs(dev[0][0])
+    for a, b in zip(host[1:], dev[1:]):
+        assert rel_l2(a, b) <= 1e-5
+    _check_loss_grad(case, [torch.from_numpy(h) for h in host])
+
+
+def test_autograd_function():
+    from paper_2312_14907_gb300 import mpbp
+    spec, scan = custom_spec(40, 16, 4, 6, npeaks=2, offset=0)
+    case = Case(spec, scan=scan, state="perturbed")
+    p, x = _gpu(case)
+    rho, u, alpha = [t.clone().requires_grad_(True) for t in x]
+    f = mpbp.mpbp_loss(rho, u, alpha, p)
+    (2.0 * f).backward()
+    ref = p.loss_grad(*x)
+    assert abs(f.item() - ref[0].item()) <= 1e-12 * abs(ref[0].item())
+    # two evaluations differ only by the order of floating-point atomics
+    for g, r in ((rho.grad, ref[1]), (u.grad, ref[2]), (alpha.grad.double(), ref[3])):
+        assert (g.double() - 2 * r.double()).abs().max().item() <= 1e-5 * (2 * r).abs().max().item()
+
+
+def test_batched_matches_single_problems():
+    from paper_2312_14907_gb300 import mpbp
+    cases = [Case(*custom_spec(40, 16, 4, 6, npeaks=2, offset=0), state="perturbed"),
+             Case(*custom_spec(96, 32, 5, 14, npeaks=3, offset=-2, seed=1), state="perturbed"),
+             Case(*custom_spec(160, 64, 4, 30, npeaks=4, offset=-5, seed=2), state="perturbed"),
+             Case(*custom_spec(200, 128, 2, 60, npeaks=3, offset=-10, seed=3), state="perturbed")]
+    probs, states = zip(*[_gpu(c) for c in cases])
+    outs = mpbp.loss_grad_batched(list(probs), list(states))
+    for c, o in zip(cases, outs):
+        _check_loss_grad(c, o)
