@@ -27,8 +27,8 @@ cudaError_t launch_object_build(const ObjectArgs& a, int num_sms, cudaStream_t s
 cudaError_t launch_frame_transpose(const float* in, float* out, long long nframes, int m,
                                    bool take_sqrt, cudaStream_t s);
 int finish_grid(long long npix, int num_sms);
-cudaError_t launch_finish(const FinishArgs& a, int grid, cudaStream_t s);
-cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t s);
+// gradient assembly, then (last block to finish) the reductions and decision
+cudaError_t launch_finish(const FinishArgs& a, const ReduceArgs& r, int grid, cudaStream_t s);
 cudaError_t launch_step_update(const StepArgs& a, int num_sms, cudaStream_t s);
 
 }  // namespace mpbp

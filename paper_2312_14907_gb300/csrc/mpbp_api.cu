@@ -50,6 +50,7 @@ struct mpbp_ctx {
   float* g_u_base = nullptr;
   double* g_alpha_base = nullptr;
   int* err = nullptr;
+  unsigned* arrivals = nullptr;
   // lazily allocated for the host-buffer entry point
   float* io_x = nullptr;
   float* stage = nullptr;
@@ -114,6 +115,7 @@ FrameArgs frame_args(mpbp_ctx* c, const int* frames, int nframes) {
   a.loss_part = c->loss_part;
   a.I_out = nullptr;
   a.err = c->err;
+  a.arrivals = c->arrivals;
   a.obj_stride = c->npix;
   a.nframes = nframes;
   a.nframes_total = (int)c->nframes;
@@ -182,8 +184,7 @@ mpbp_status enqueue_loss_grad(mpbp_ctx* c, const float* rho, const float* u, con
   fi.D = c->D;
   fi.C = c->C;
   fi.pc = c->pc;
-  MPBP_CUDA(c, launch_finish(fi, c->finish_grid, s));
-  c->acc_dirty = false;
+  fi.arrivals = c->arrivals;
 
   ReduceArgs ra{};
   ra.loss_part = c->loss_part;
@@ -197,7 +198,8 @@ mpbp_status enqueue_loss_grad(mpbp_ctx* c, const float* rho, const float* u, con
   ra.err = c->err;
   ra.st = st;
   ra.alpha_from = 1;
-  MPBP_CUDA(c, launch_reduce(ra, s));
+  MPBP_CUDA(c, launch_finish(fi, ra, c->finish_grid, s));
+  c->acc_dirty = false;
   return MPBP_OK;
 }
 
@@ -280,6 +282,7 @@ mpbp_status mpbp_create(const mpbp_problem* pr, mpbp_ctx** out) {
   size_t oGUB = cv.take<float>(c->npix * c->C);
   size_t oGAB = cv.take<double>(c->D);
   size_t oErr = cv.take<int>(1);
+  size_t oArr = cv.take<unsigned>(1);
   c->ws_bytes = align_up(cv.off, 256);
   cudaError_t e = cudaMalloc(&c->ws, c->ws_bytes);
   if (e != cudaSuccess) {
@@ -306,12 +309,14 @@ mpbp_status mpbp_create(const mpbp_problem* pr, mpbp_ctx** out) {
   c->g_u_base = reinterpret_cast<float*>(b + oGUB);
   c->g_alpha_base = reinterpret_cast<double*>(b + oGAB);
   c->err = reinterpret_cast<int*>(b + oErr);
+  c->arrivals = reinterpret_cast<unsigned*>(b + oArr);
 
   std::vector<int2> sc(c->J);
   for (int j = 0; j < c->J; ++j) sc[j] = make_int2(pr->scan[2 * j], pr->scan[2 * j + 1]);
   if (cudaMemcpy(c->scan, sc.data(), sizeof(int2) * c->J, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(c->acc, 0, sizeof(cf) * c->npix * c->D) != cudaSuccess ||
       cudaMemset(c->err, 0, sizeof(int)) != cudaSuccess ||
+      cudaMemset(c->arrivals, 0, sizeof(unsigned)) != cudaSuccess ||
       cudaDeviceSynchronize() != cudaSuccess)
     return bail(MPBP_ERR_CUDA);
   *out = c;
@@ -340,8 +345,8 @@ mpbp_status mpbp_get_info(const mpbp_ctx* c, mpbp_info* info) {
   info->frames_smem = c->fk.smem;
   info->blocks_per_sm = c->blocks_per_sm;
   info->num_sms = c->num_sms;
-  info->launches_loss_grad = 4;  // object build, frames, finish, reduce
-  info->launches_step = 5;       // + update
+  info->launches_loss_grad = 3;  // object build, frames, gradient assembly + reductions
+  info->launches_step = 4;       // + update
   return MPBP_OK;
 }
 
@@ -398,6 +403,7 @@ mpbp_status mpbp_forward(mpbp_ctx* c, const float* rho, const float* u, const fl
   if (r != MPBP_OK) return r;
   FrameArgs fa = frame_args(c, nullptr, (int)c->nframes);
   fa.I_out = I_out;
+  fa.arrivals = nullptr;
   MPBP_CUDA(c, frames_launch(c->M, fa, frames_grid_for(c, c->nframes), true, S(stream)));
   return MPBP_OK;
 }

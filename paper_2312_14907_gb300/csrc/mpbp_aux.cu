@@ -81,9 +81,66 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
+// ----------------------------------------------------------------------------
+// A8: fixed-order FP64 reductions and the optional line-search decision, run
+// by the last block of the gradient-assembly grid to finish (one warp per
+// reduced quantity, partials read in a fixed order, so the result does not
+// depend on which block finishes last)
+// ----------------------------------------------------------------------------
+template <int T>
+__device__ void final_reduce(const ReduceArgs& a) {
+  __shared__ double vals[kMaxPeaks + 3];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nq = a.D + 3;   // loss, df/dalpha_m (D), |g_rho|^2, |g_u|^2
+  for (int q = w; q < nq; q += T / 32) {
+    double v = 0.0;
+    if (q == 0) {
+      for (int i = lane; i < a.n_loss_part; i += 32) v += __ldcg(a.loss_part + i);
+    } else {
+      const int m = q - 1;
+      for (int i = lane; i < a.n_part; i += 32) v += __ldcg(a.part + (long long)i * (a.D + 2) + m);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) vals[q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const double loss = vals[0];
+  const double* galpha = vals + 1;
+  const bool finite = isfinite(loss);
+  if (!finite) atomicOr(a.err, kErrNonfinite);
+  if (a.loss_out) *a.loss_out = loss;
+  for (int m = 0; m < a.D; ++m) {
+    if (a.g_alpha_out) a.g_alpha_out[m] = galpha[m];
+    if (a.g_alpha_ws) a.g_alpha_ws[m] = galpha[m];
+  }
+  mpbp_step_state* st = a.st;
+  if (!st) return;
+  // lagged Armijo decision in FP64; weighted squared norm of the descent
+  // direction (alpha_0 is not a variable)
+  double gn2 = st->w_rho * galpha[a.D] + st->w_u * galpha[a.D + 1];
+  for (int m = a.alpha_from; m < a.D; ++m) gn2 += st->w_alpha * galpha[m] * galpha[m];
+  bool accept;
+  if (st->k == 0) accept = finite;
+  else accept = finite && (loss <= st->f_prev - st->c_armijo * st->t * st->gn2_prev);
+  if (accept) {
+    if (st->k > 0) st->t *= st->grow;
+    st->f_prev = loss;
+    st->gn2_prev = gn2;
+    st->n_accept += 1;
+  } else {
+    st->t *= st->shrink;
+    st->n_reject += 1;
+  }
+  st->accepted = accept ? 1 : 0;
+  st->f_last = loss;
+  st->k += 1;
+}
+
 constexpr int kFinishThreads = 256;
 
-__global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a) {
+__global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a, ReduceArgs ra) {
   __shared__ double red[kFinishThreads / 32];
   float ap[kMaxPeaks];
   for (int m = 0; m < kMaxPeaks; ++m) ap[m] = 0.f;
@@ -139,58 +196,17 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a) {
   }
   const double t0 = block_sum<kFinishThreads>(n_rho, red);
   const double t1 = block_sum<kFinishThreads>(n_u, red);
+  __shared__ bool last;
   if (threadIdx.x == 0) {
     out[a.D] = t0;
     out[a.D + 1] = t1;
+    __threadfence();   // publish this block's partials before counting it in
+    last = atomicAdd(a.arrivals, 1u) == gridDim.x - 1;
   }
-}
-
-// ----------------------------------------------------------------------------
-// A8: fixed-order reductions (one block), optional line-search decision
-// ----------------------------------------------------------------------------
-constexpr int kReduceThreads = 256;
-
-__global__ void __launch_bounds__(kReduceThreads) reduce_kernel(ReduceArgs a) {
-  __shared__ double red[kReduceThreads / 32];
-  __shared__ double galpha[kMaxPeaks + 2];
-  double v = 0.0;
-  for (int i = threadIdx.x; i < a.n_loss_part; i += blockDim.x) v += a.loss_part[i];
-  const double loss = block_sum<kReduceThreads>(v, red);
-  for (int m = 0; m < a.D + 2; ++m) {
-    double w = 0.0;
-    for (int i = threadIdx.x; i < a.n_part; i += blockDim.x) w += a.part[(long long)i * (a.D + 2) + m];
-    const double t = block_sum<kReduceThreads>(w, red);
-    if (threadIdx.x == 0) galpha[m] = t;
-  }
-  if (threadIdx.x != 0) return;
-  const bool finite = isfinite(loss);
-  if (!finite) atomicOr(a.err, kErrNonfinite);
-  if (a.loss_out) *a.loss_out = loss;
-  for (int m = 0; m < a.D; ++m) {
-    if (a.g_alpha_out) a.g_alpha_out[m] = galpha[m];
-    if (a.g_alpha_ws) a.g_alpha_ws[m] = galpha[m];
-  }
-  mpbp_step_state* st = a.st;
-  if (!st) return;
-  // lagged Armijo decision in FP64
-  // weighted squared norm of the descent direction (alpha_0 is not a variable)
-  double gn2 = st->w_rho * galpha[a.D] + st->w_u * galpha[a.D + 1];
-  for (int m = a.alpha_from; m < a.D; ++m) gn2 += st->w_alpha * galpha[m] * galpha[m];
-  bool accept;
-  if (st->k == 0) accept = finite;
-  else accept = finite && (loss <= st->f_prev - st->c_armijo * st->t * st->gn2_prev);
-  if (accept) {
-    if (st->k > 0) st->t *= st->grow;
-    st->f_prev = loss;
-    st->gn2_prev = gn2;
-    st->n_accept += 1;
-  } else {
-    st->t *= st->shrink;
-    st->n_reject += 1;
-  }
-  st->accepted = accept ? 1 : 0;
-  st->f_last = loss;
-  st->k += 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  final_reduce<kFinishThreads>(ra);
 }
 
 // ----------------------------------------------------------------------------
@@ -268,13 +284,8 @@ int finish_grid(long long npix, int num_sms) {
   return grid_for(npix, kFinishThreads, num_sms * 4);
 }
 
-cudaError_t launch_finish(const FinishArgs& a, int grid, cudaStream_t s) {
-  finish_kernel<<<grid, kFinishThreads, 0, s>>>(a);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t s) {
-  reduce_kernel<<<1, kReduceThreads, 0, s>>>(a);
+cudaError_t launch_finish(const FinishArgs& a, const ReduceArgs& r, int grid, cudaStream_t s) {
+  finish_kernel<<<grid, kFinishThreads, 0, s>>>(a, r);
   return cudaGetLastError();
 }
 

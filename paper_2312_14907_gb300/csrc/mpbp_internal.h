@@ -27,6 +27,8 @@ struct FrameArgs {
   double* loss_part;    // [gridDim.x] per-block loss partials
   float* I_out;         // forward mode: [D*J][M][M]
   int* err;             // device error word
+  unsigned* arrivals;   // block counter of the gradient assembly that follows;
+                        // cleared here, before that kernel can start
   long long obj_stride; // n1*n2
   int nframes;          // frames to process
   int nframes_total;    // D*J (bound for frame indices)
@@ -59,6 +61,7 @@ struct FinishArgs {
   float* g_rho;
   float* g_u;
   double* part;         // [gridDim.x][D + 2]: df/dalpha_m partials, |g_rho|^2, |g_u|^2
+  unsigned* arrivals;   // blocks done (the last one runs the final reduction)
   long long npix;
   int D, C;
   PhaseCoef pc;
