@@ -142,7 +142,7 @@ def make_inputs(spec, scan, prob, torch):
 def run_gpu(args):
     import torch
     import torch.distributed as dist
-    from paper_2312_14907_gb300 import mpbp
+    from paper_2312_14907_gb300 import mpbp, replicas
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -194,11 +194,7 @@ def run_gpu(args):
     step_ms = [a.elapsed_time(b) for a, b in evs]
     kern_ms, kern_n = prob.frames_timing_read()
     prob.sync_status()
-    tot_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = t.item()
+    tot_ms = replicas.max_over_ranks(sum(step_ms), device="cuda")
 
     # end to end through the host-buffer C-ABI call: H2D of the step's data and
     # state from pinned memory, evaluation, D2H of loss and gradients
@@ -219,16 +215,12 @@ def run_gpu(args):
         t1 = time.perf_counter()
         prob.loss_grad_host(rh, uh, ah, y=yh, out=outs)
         e2e.append(time.perf_counter() - t1)
-    e2e_s = sum(e2e)
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = t.item()
+    e2e_s = replicas.max_over_ranks(sum(e2e), device="cuda")
     h2d = y.nbytes + rh.numel() * 4 + uh.numel() * 4 + ah.numel() * 4
     d2h = 8 + outs[1].numel() * 4 + outs[2].numel() * 4 + outs[3].numel() * 8
 
     frames_total = spec.nframes * args.steps * world
-    value = frames_total / (tot_ms / 1e3)
+    value = replicas.whole_job_rate(spec.nframes, args.steps, world, tot_ms)
     pk = peaks()
     kavg_ms = kern_ms / max(kern_n, 1)
     fl = flops_per_frame(spec.m) * spec.nframes

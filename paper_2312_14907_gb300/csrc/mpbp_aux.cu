@@ -67,19 +67,6 @@ __global__ void frame_transpose_kernel(const float* __restrict__ in, float* __re
 //   df/du_c = sum_m phase_scale G_{m,c} df/dphi_m,  df/dalpha_m = sum_r rho Re T_m.
 // acc is cleared behind the read so the next evaluation starts from zero.
 // ----------------------------------------------------------------------------
-template <int T>
-__device__ __forceinline__ double block_sum(double v, double* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < T / 32; ++i) s += red[i];
-  }
-  __syncthreads();
-  return s;
-}
 
 // ----------------------------------------------------------------------------
 // A8: fixed-order FP64 reductions and the optional line-search decision, run
@@ -139,12 +126,17 @@ __device__ void final_reduce(const ReduceArgs& a) {
 }
 
 constexpr int kFinishThreads = 256;
+constexpr int kFinishPixelsPerThread = 4;
 
 __global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a, ReduceArgs ra) {
-  __shared__ double red[kFinishThreads / 32];
-  float ap[kMaxPeaks];
+  constexpr int NW = kFinishThreads / 32;
+  constexpr int NQ = kMaxPeaks + 2;
+  __shared__ double wsum[NW][NQ];
+  __shared__ bool last;
+  float ap[kMaxPeaks];   // df/dalpha_m partials of this thread
+#pragma unroll
   for (int m = 0; m < kMaxPeaks; ++m) ap[m] = 0.f;
-  double n_rho = 0.0, n_u = 0.0;
+  float n_rho = 0.f, n_u = 0.f;
   const long long stride = (long long)gridDim.x * blockDim.x;
   float2* acc = reinterpret_cast<float2*>(a.acc);
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < a.npix; p += stride) {
@@ -183,26 +175,32 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a, Re
         su = fmaf(gu[c], gu[c], su);
       }
     }
-    n_rho += (double)(gr * gr);
-    n_u += (double)su;
+    n_rho = fmaf(gr, gr, n_rho);
+    n_u += su;
   }
-  double* out = a.part + (long long)blockIdx.x * (a.D + 2);
+  // partial sums: FP32 within the warp (a few pixels per lane), FP64 across
+  // warps and blocks; one barrier for all D + 2 quantities
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-  for (int m = 0; m < kMaxPeaks; ++m) {
-    if (m < a.D) {
-      const double t = block_sum<kFinishThreads>((double)ap[m], red);
-      if (threadIdx.x == 0) out[m] = t;
+  for (int q = 0; q < NQ; ++q) {
+    if (q < a.D + 2) {
+      float v = q < a.D ? ap[q < kMaxPeaks ? q : 0] : (q == a.D ? n_rho : n_u);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) wsum[w][q] = (double)v;
     }
   }
-  const double t0 = block_sum<kFinishThreads>(n_rho, red);
-  const double t1 = block_sum<kFinishThreads>(n_u, red);
-  __shared__ bool last;
-  if (threadIdx.x == 0) {
-    out[a.D] = t0;
-    out[a.D + 1] = t1;
+  __syncthreads();
+  double* out = a.part + (long long)blockIdx.x * (a.D + 2);
+  if (w == 0 && lane < a.D + 2) {
+    double t = 0.0;
+#pragma unroll
+    for (int i = 0; i < NW; ++i) t += wsum[i][lane];
+    out[lane] = t;
     __threadfence();   // publish this block's partials before counting it in
-    last = atomicAdd(a.arrivals, 1u) == gridDim.x - 1;
   }
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(a.arrivals, 1u) == gridDim.x - 1;
   __syncthreads();
   if (!last) return;
   __threadfence();
@@ -281,7 +279,8 @@ cudaError_t launch_frame_transpose(const float* in, float* out, long long nframe
 }
 
 int finish_grid(long long npix, int num_sms) {
-  return grid_for(npix, kFinishThreads, num_sms * 4);
+  return grid_for((npix + kFinishPixelsPerThread - 1) / kFinishPixelsPerThread, kFinishThreads,
+                  num_sms * 2);
 }
 
 cudaError_t launch_finish(const FinishArgs& a, const ReduceArgs& r, int grid, cudaStream_t s) {
