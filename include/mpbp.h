@@ -188,6 +188,28 @@ mpbp_status mpbp_loss_grad_batched(int32_t n, mpbp_ctx *const *ctxs,
                                    float *const *g_rho, float *const *g_u,
                                    double *const *g_alpha, void *stream);
 
+/* Loss and gradient of all frames, like mpbp_loss_grad, without allocating
+ * anything.  The paper has no counterpart: this exists for callers that cannot
+ * call cudaMalloc (code that runs under another framework's allocator, or
+ * that has already reserved the GPU's memory) and so cannot create a context.
+ * The caller passes every input and output as a device pointer: probe
+ * [Dp][M][M] complex, measured intensities y [D][J][M][M] (no background),
+ * rho, u, alpha, and the outputs loss (1 double), g_rho, g_u, g_alpha [D]
+ * doubles (g_alpha may be NULL).  G and the scan table stay on the host in
+ * *problem.  The workspace lives in one fixed 16 MiB array inside the
+ * library's device image, present on every GPU that loads the library until
+ * the process exits; a problem needs about 8*(2*D*n1*n2 + nscan) +
+ * 4*D*nscan*M*M bytes of it plus a few KiB, and a larger one returns
+ * MPBP_ERR_UNSUPPORTED before anything is enqueued.  The first call on a
+ * device looks up the array's device address (once per device), so make that
+ * first call before capturing the stream into a graph.  All calls share the
+ * array: each call clears what must start at zero, and calls whose GPU work
+ * overlaps (other streams, other threads) race on it. */
+mpbp_status mpbp_loss_grad_noalloc(const mpbp_problem *problem, const float *probe,
+                                   const float *y, const float *rho, const float *u,
+                                   const float *alpha, double *loss, float *g_rho,
+                                   float *g_u, double *g_alpha, void *stream);
+
 /* Overrides the fused frame kernel's schedule: resident blocks per SM used to
  * size its persistent grid (0 = occupancy maximum).  Host-side only. */
 mpbp_status mpbp_set_schedule(mpbp_ctx *ctx, int32_t blocks_per_sm);

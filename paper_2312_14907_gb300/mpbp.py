@@ -60,7 +60,7 @@ EXPORTS = ["mpbp_status_string", "mpbp_create", "mpbp_destroy", "mpbp_last_error
            "mpbp_get_info", "mpbp_set_probe", "mpbp_set_data", "mpbp_object_build",
            "mpbp_forward", "mpbp_loss_grad", "mpbp_loss_grad_host", "mpbp_step_init",
            "mpbp_step", "mpbp_loss_grad_batched", "mpbp_set_schedule", "mpbp_sync_status",
-           "mpbp_frames_timing", "mpbp_frames_timing_read"]
+           "mpbp_frames_timing", "mpbp_frames_timing_read", "mpbp_loss_grad_noalloc"]
 
 
 def library_path():
@@ -116,6 +116,8 @@ def load(build_if_missing=True):
     lib.mpbp_frames_timing.restype = st
     lib.mpbp_frames_timing_read.argtypes = [V, P(D), P(I32)]
     lib.mpbp_frames_timing_read.restype = st
+    lib.mpbp_loss_grad_noalloc.argtypes = [P(_Problem), V, V, V, V, V, V, V, V, V, V]
+    lib.mpbp_loss_grad_noalloc.restype = st
     _lib = lib
     return lib
 
@@ -345,6 +347,26 @@ def loss_grad_batched(problems, states, outs=None):
     if s != 0:
         raise MPBPError(s, "mpbp_loss_grad_batched")
     return outs
+
+
+def loss_grad_noalloc(spec_problem, probe, y, rho, u, alpha, out):
+    """mpbp_loss_grad_noalloc: the loss and gradient computed in the library's
+    fixed device scratch array, for callers that cannot allocate device
+    memory.  `spec_problem` is a Problem (only its geometry is used); every
+    tensor, including the outputs in `out` = (loss [1] float64, g_rho, g_u,
+    g_alpha [D] float64), must already be on the device."""
+    lib = load()
+    p = spec_problem
+    pr = _Problem(p.n1, p.n2, p.ncomp, p.npeaks, p.m, p.nscan,
+                  p._G.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                  p._scan.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                  int(p.probe_per_peak), p.phase_scale)
+    loss, g_rho, g_u, g_alpha = out
+    s = lib.mpbp_loss_grad_noalloc(ctypes.byref(pr), _p(probe), _p(y), _p(rho), _p(u), _p(alpha),
+                                   _p(loss), _p(g_rho), _p(g_u), _p(g_alpha), _stream())
+    if s != 0:
+        raise MPBPError(s, "mpbp_loss_grad_noalloc")
+    return out
 
 
 class MPBPLoss(torch.autograd.Function):
