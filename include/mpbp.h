@@ -224,6 +224,35 @@ mpbp_status mpbp_frames_timing(mpbp_ctx *ctx, int32_t enable);
  * last read, and clears them.  Host pointers. */
 mpbp_status mpbp_frames_timing_read(mpbp_ctx *ctx, double *total_ms, int32_t *count);
 
+/* Schedule of mpbp_loss_grad_batched calls whose first context is ctx:
+ * mode 0 = one persistent launch for every frame side (work items of 1, 2 or
+ * 4 frames per 256-thread block); mode 1 = one persistent launch per frame
+ * side with that side's own block shape; mode 2 = as mode 1 for sides 32 and
+ * 64, one launch per problem for side 128; mode 3 = one launch per problem.
+ * Problems with M <= 16 always get their own launch.  order 0 = work items
+ * grouped by problem, 1 = problems interleaved.  Host-side only. */
+mpbp_status mpbp_set_batch_schedule(mpbp_ctx *ctx, int32_t mode, int32_t order);
+
+/* Autotuner for one context: times mpbp_loss_grad at rho, u, alpha (dev)
+ * with every schedule from 1 to the occupancy limit of resident frame-kernel
+ * blocks per SM and keeps the fastest (mpbp_set_schedule).  loss, g_rho and
+ * g_u (dev) receive the evaluations.  With cache_path != NULL (host string)
+ * the choice is first looked up in that JSON-lines file under a key made of
+ * the GPU name, M, D, n1 x n2 and the frame count, and appended to it after
+ * tuning.  Synchronous.  Needs probe and data. */
+mpbp_status mpbp_autotune(mpbp_ctx *ctx, const float *rho, const float *u, const float *alpha,
+                          double *loss, float *g_rho, float *g_u, const char *cache_path,
+                          void *stream);
+
+/* Autotuner for mpbp_loss_grad_batched calls on these contexts: times every
+ * batch mode and item order (mpbp_set_batch_schedule) on the given states and
+ * keeps the fastest in ctxs[0]; cache as for mpbp_autotune, keyed by the GPU
+ * and every problem's shape.  Synchronous. */
+mpbp_status mpbp_autotune_batched(int32_t n, mpbp_ctx *const *ctxs, const float *const *rho,
+                                  const float *const *u, const float *const *alpha,
+                                  double *const *loss, float *const *g_rho, float *const *g_u,
+                                  const char *cache_path, void *stream);
+
 /* Synchronises `stream`, then returns and clears the first error latched on
  * the device since the last call (MPBP_OK if none). */
 mpbp_status mpbp_sync_status(mpbp_ctx *ctx, void *stream);

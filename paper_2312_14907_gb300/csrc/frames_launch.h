@@ -11,6 +11,43 @@ struct FrameKernelInfo {
   int blocks_per_sm;    // occupancy limit on the current device
 };
 
+//
+// Several problems in one persistent launch.  A work item is one block's worth
+// of frames of one problem: 1 frame of M = 128, 2 of M = 64 or 4 of M = 32,
+// each on its own group of 2M threads.  Items are taken round-robin; when a
+// block's next item has the same frame side its inputs are prefetched during
+// the current item, as in the single-problem kernel.  Each warp writes its
+// loss partial per frame (fixed slots, so the per-problem sums are
+// deterministic).
+//
+constexpr int kBatchThreads = 256;
+constexpr int kBatchWarpSlots = kBatchThreads / 32;   // loss partials per frame
+constexpr int kBatchSmem = 128 * 129 * 8 + 128 * 128 * 4;   // the M = 128 frame buffers
+
+// Per-problem arguments travel in the launch's parameter space (constant
+// bank), like the single-problem kernel's, so reading them costs no
+// registers across a frame; larger batches are split into several launches.
+constexpr int kBatchMaxProbs = 48;
+
+struct BatchArgs {
+  FrameArgs probs[kBatchMaxProbs];       // per-problem arguments (frames == nullptr)
+  int prob_m[kBatchMaxProbs];            // frame side
+  long long frame_base[kBatchMaxProbs];  // first slot of the problem in frame_part
+  const int2* items;                     // [nitems] (problem, first frame)
+  double* frame_part;                    // [frames][kBatchWarpSlots] loss partials,
+                                         // zeroed before the launch
+  int nitems;
+  int nprob;
+};
+
+// Prepares the batched kernel on the current device; reports its occupancy.
+bool batched_prepare(int* blocks_per_sm);
+cudaError_t batched_launch(const BatchArgs& b, int grid, cudaStream_t s);
+
+// One launch per frame side: items are single frames of problems with side m.
+bool batched_m_prepare(int m, int* blocks_per_sm);
+cudaError_t batched_m_launch(int m, const BatchArgs& b, int grid, cudaStream_t s);
+
 // Prepares the kernels of frame side m on the current device (shared-memory
 // carve-out) and reports their launch shape.  Returns false for unsupported m.
 bool frames_prepare(int m, FrameKernelInfo* info);

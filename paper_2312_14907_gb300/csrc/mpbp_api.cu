@@ -1,9 +1,12 @@
 // mpbp_api.cu -- the C ABI declared in include/mpbp.h: context, workspace,
 // argument checks and the launch sequence of each entry point.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <fstream>
+#include <sstream>
 #include <new>
 #include <string>
 #include <vector>
@@ -14,6 +17,7 @@
 using namespace mpbp;
 
 struct mpbp_ctx {
+  unsigned long long serial = 0;   // unique per context created in this process
   int device = 0;
   int num_sms = 0;
   // problem
@@ -51,6 +55,24 @@ struct mpbp_ctx {
   double* g_alpha_base = nullptr;
   int* err = nullptr;
   unsigned* arrivals = nullptr;
+  // lazily allocated tables of a batched launch led by this context
+  void* batch_ws = nullptr;
+  size_t batch_ws_bytes = 0;
+  int batch_order = 0;    // 0: items grouped by frame side, 1: problems interleaved
+  int batch_mode = 1;     // 0: one launch for every frame side, 1: one launch per side,
+                          // 2: as 1 but M = 128 problems launched one by one,
+                          // 3: every problem launched on its own
+  std::vector<long long> batch_key;   // the batch whose plan is cached below
+  struct PlanLaunch {
+    int m;          // frame side, or 0 for the single launch over every side
+    int grid;
+    BatchArgs args;
+  };
+  std::vector<PlanLaunch> batch_plan;
+  std::vector<long long> batch_base;  // first loss slot of each fused problem
+  std::vector<int> batch_fused;       // batch positions of the fused problems
+  long long batch_frames = 0;
+  unsigned long long version = 0;     // bumped when probe or data change
   // lazily allocated for the host-buffer entry point
   float* io_x = nullptr;
   float* stage = nullptr;
@@ -96,6 +118,12 @@ struct Carver {
     return o;
   }
 };
+
+// whether problems of frame side m go through the batched kernel in `mode`
+bool batch_fused_side(int mode, int m) {
+  if (m < 32 || mode == 3) return false;
+  return mode != 2 || m < 128;
+}
 
 int frames_grid_for(const mpbp_ctx* c, long long nframes) {
   const long long need = (nframes + c->fk.frames_per_block - 1) / c->fk.frames_per_block;
@@ -185,10 +213,10 @@ mpbp_status enqueue_loss_grad(mpbp_ctx* c, const float* rho, const float* u, con
   fi.C = c->C;
   fi.pc = c->pc;
   fi.arrivals = c->arrivals;
+  fi.loss_part = c->loss_part;
+  fi.n_loss_part = grid;
 
   ReduceArgs ra{};
-  ra.loss_part = c->loss_part;
-  ra.n_loss_part = grid;
   ra.part = c->part;
   ra.n_part = c->finish_grid;
   ra.D = c->D;
@@ -231,6 +259,8 @@ mpbp_status mpbp_create(const mpbp_problem* pr, mpbp_ctx** out) {
 
   mpbp_ctx* c = new (std::nothrow) mpbp_ctx();
   if (!c) return MPBP_ERR_OOM;
+  static std::atomic<unsigned long long> next_serial{1};
+  c->serial = next_serial.fetch_add(1);
   auto bail = [&](mpbp_status s) {
     if (c->ws) cudaFree(c->ws);
     delete c;
@@ -270,7 +300,7 @@ mpbp_status mpbp_create(const mpbp_problem* pr, mpbp_ctx** out) {
   size_t oScan = cv.take<int2>(c->J);
   size_t oAT = cv.take<float>(c->nframes * mm);
   size_t oLP = cv.take<double>(max_frames_grid);
-  size_t oPart = cv.take<double>((size_t)c->finish_grid * (c->D + 2));
+  size_t oPart = cv.take<double>((size_t)c->finish_grid * (c->D + 3));
   size_t oLoss = cv.take<double>(1);
   size_t oGR = cv.take<float>(c->npix);
   size_t oGU = cv.take<float>(c->npix * c->C);
@@ -332,6 +362,7 @@ void mpbp_destroy(mpbp_ctx* c) {
   }
   if (c->ws) cudaFree(c->ws);
   if (c->io_x) cudaFree(c->io_x);
+  if (c->batch_ws) cudaFree(c->batch_ws);
   if (c->stage) cudaFree(c->stage);
   if (c->bgT) cudaFree(c->bgT);
   delete c;
@@ -358,12 +389,22 @@ mpbp_status mpbp_set_schedule(mpbp_ctx* c, int32_t blocks_per_sm) {
   return MPBP_OK;
 }
 
+mpbp_status mpbp_set_batch_schedule(mpbp_ctx* c, int32_t mode, int32_t order) {
+  if (!c || mode < 0 || mode > 3 || order < 0 || order > 1)
+    return fail(c, MPBP_ERR_INVALID_ARG, "batch schedule out of range");
+  c->batch_key.clear();
+  c->batch_mode = mode;
+  c->batch_order = order;
+  return MPBP_OK;
+}
+
 mpbp_status mpbp_set_probe(mpbp_ctx* c, const float* probe, void* stream) {
   if (!c || !probe) return fail(c, MPBP_ERR_INVALID_ARG, "null probe");
   const int Dp = c->probe_per_peak ? c->D : 1;
   MPBP_CUDA(c, cudaMemcpyAsync(c->probe, probe, sizeof(cf) * Dp * c->M * c->M,
                                cudaMemcpyDeviceToDevice, S(stream)));
   c->has_probe = true;
+  c->version++;
   return MPBP_OK;
 }
 
@@ -386,6 +427,7 @@ mpbp_status mpbp_set_data(mpbp_ctx* c, const float* y, const float* bg, void* st
     c->bgT = nullptr;
   }
   c->has_data = true;
+  c->version++;
   return MPBP_OK;
 }
 
@@ -533,11 +575,351 @@ mpbp_status mpbp_loss_grad_batched(int32_t n, mpbp_ctx* const* ctxs, const float
                                    double* const* g_alpha, void* stream) {
   if (n < 0 || (n > 0 && (!ctxs || !rho || !u || !alpha || !loss || !g_rho || !g_u)))
     return MPBP_ERR_INVALID_ARG;
+  if (n == 0) return MPBP_OK;
+  mpbp_ctx* lead = ctxs[0];
+  if (!lead) return MPBP_ERR_INVALID_ARG;
+  cudaStream_t s = S(stream);
   for (int i = 0; i < n; ++i) {
-    mpbp_status r = mpbp_loss_grad(ctxs[i], rho[i], u[i], alpha[i], nullptr, 0, loss[i], g_rho[i],
-                                   g_u[i], g_alpha ? g_alpha[i] : nullptr, stream);
+    mpbp_ctx* c = ctxs[i];
+    if (!c || !rho[i] || !u[i] || !alpha[i] || !loss[i] || !g_rho[i] || !g_u[i])
+      return fail(lead, MPBP_ERR_INVALID_ARG, "null argument in batch");
+    if (c->device != lead->device) return fail(lead, MPBP_ERR_INVALID_ARG, "batch spans devices");
+    if (!c->has_probe || !c->has_data) return fail(lead, MPBP_ERR_NO_DATA, "probe or data not set");
+    for (int k = 0; k < i; ++k)
+      if (ctxs[k] == c) return fail(lead, MPBP_ERR_INVALID_ARG, "a context appears twice in a batch");
+  }
+  // problems with M in {32, 64, 128} share the batched kernel: one launch for
+  // all sides (mode 0) or one per side (mode 1), at most kBatchMaxProbs
+  // problems per launch.  The plan (item table, launch arguments) is built
+  // once per batch composition and kept in the lead context.
+  std::vector<long long> key = {lead->batch_mode, lead->batch_order, n};
+  for (int i = 0; i < n; ++i) {
+    key.push_back((long long)ctxs[i]->serial);
+    key.push_back((long long)ctxs[i]->version);
+  }
+  if (key != lead->batch_key || !lead->batch_ws) {
+    lead->batch_key.clear();
+    lead->batch_plan.clear();
+    std::vector<int> fused;
+    for (int i = 0; i < n; ++i)
+      if (batch_fused_side(lead->batch_mode, ctxs[i]->M)) fused.push_back(i);
+    const int nf = (int)fused.size();
+    std::vector<long long> base(nf);
+    long long total_frames = 0;
+    for (int k = 0; k < nf; ++k) {
+      base[k] = total_frames;
+      total_frames += ctxs[fused[k]]->nframes;
+    }
+    // frames per work item: a 256-thread block's worth in the single launch
+    // over every side (mode 0), one frame in the per-side launches
+    auto per_item = [&](int m) {
+      if (lead->batch_mode != 0) return 1;
+      return m >= 128 ? 1 : (m == 64 ? 2 : 4);
+    };
+    struct Launch {
+      int m;
+      std::vector<int> probs;   // indices into `fused`
+      size_t first, count;      // item range
+    };
+    std::vector<Launch> launches;
+    std::vector<int2> items;    // (problem index within its launch, first frame)
+    auto add_launch = [&](int m, const std::vector<int>& probs) {
+      Launch L{m, probs, items.size(), 0};
+      const int np = (int)probs.size();
+      for (int side : {128, 64, 32}) {
+        if (lead->batch_order == 0) {
+          for (int k = 0; k < np; ++k) {
+            mpbp_ctx* c = ctxs[fused[probs[k]]];
+            if (c->M != side) continue;
+            for (long long f = 0; f < c->nframes; f += per_item(side)) items.push_back(make_int2(k, (int)f));
+          }
+        } else {
+          std::vector<long long> next(np, 0);
+          bool any = true;
+          while (any) {
+            any = false;
+            for (int k = 0; k < np; ++k) {
+              mpbp_ctx* c = ctxs[fused[probs[k]]];
+              if (c->M != side || next[k] >= c->nframes) continue;
+              items.push_back(make_int2(k, (int)next[k]));
+              next[k] += per_item(side);
+              any = true;
+            }
+          }
+        }
+      }
+      L.count = items.size() - L.first;
+      if (L.count) launches.push_back(L);
+    };
+    for (int side : {0, 128, 64, 32}) {
+      if ((lead->batch_mode == 0) != (side == 0)) continue;
+      std::vector<int> group;
+      for (int k = 0; k < nf; ++k) {
+        if (side != 0 && ctxs[fused[k]]->M != side) continue;
+        group.push_back(k);
+        if ((int)group.size() == kBatchMaxProbs) {
+          add_launch(side, group);
+          group.clear();
+        }
+      }
+      if (!group.empty()) add_launch(side, group);
+    }
+    // device tables in the lead context's batch buffer
+    Carver cv;
+    const size_t oI = cv.take<int2>(items.empty() ? 1 : items.size());
+    const size_t oFP = cv.take<double>((size_t)(total_frames > 0 ? total_frames : 1) * kBatchWarpSlots);
+    const size_t need = align_up(cv.off, 256);
+    if (need > lead->batch_ws_bytes) {
+      MPBP_CUDA(lead, cudaStreamSynchronize(s));
+      if (lead->batch_ws) cudaFree(lead->batch_ws);
+      lead->batch_ws = nullptr;
+      lead->batch_ws_bytes = 0;
+      cudaError_t e = cudaMalloc(&lead->batch_ws, need);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(lead, MPBP_ERR_OOM, "batch tables");
+      }
+      lead->batch_ws_bytes = need;
+    }
+    char* wb = static_cast<char*>(lead->batch_ws);
+    if (!items.empty())
+      MPBP_CUDA(lead, cudaMemcpyAsync(wb + oI, items.data(), sizeof(int2) * items.size(),
+                                      cudaMemcpyHostToDevice, s));
+    double* frame_part = reinterpret_cast<double*>(wb + oFP);
+    for (const Launch& L : launches) {
+      mpbp_ctx::PlanLaunch P{};
+      P.m = L.m;
+      for (size_t k = 0; k < L.probs.size(); ++k) {
+        mpbp_ctx* c = ctxs[fused[L.probs[k]]];
+        P.args.probs[k] = frame_args(c, nullptr, (int)c->nframes);
+        P.args.prob_m[k] = c->M;
+        P.args.frame_base[k] = base[L.probs[k]];
+      }
+      P.args.nprob = (int)L.probs.size();
+      P.args.items = reinterpret_cast<const int2*>(wb + oI) + L.first;
+      P.args.nitems = (int)L.count;
+      P.args.frame_part = frame_part;
+      int bps = 1;
+      const bool ok = L.m == 0 ? batched_prepare(&bps) : batched_m_prepare(L.m, &bps);
+      if (!ok) return fail(lead, MPBP_ERR_CUDA, "batched kernel setup");
+      P.grid = (int)std::min<long long>((long long)L.count, (long long)lead->num_sms * bps);
+      lead->batch_plan.push_back(P);
+    }
+    lead->batch_base = base;
+    lead->batch_fused = fused;
+    lead->batch_frames = total_frames;
+    lead->batch_key = key;
+  }
+  const std::vector<long long>& base = lead->batch_base;
+  const std::vector<int>& fused = lead->batch_fused;
+  const int nf = (int)fused.size();
+
+  // A1 for every problem
+  for (int i = 0; i < n; ++i) {
+    mpbp_ctx* c = ctxs[i];
+    if (c->acc_dirty) {
+      MPBP_CUDA(c, cudaMemsetAsync(c->acc, 0, sizeof(cf) * c->npix * c->D, s));
+      c->acc_dirty = false;
+    }
+    mpbp_status r = enqueue_object_build(c, rho[i], u[i], alpha[i], c->O, s);
     if (r != MPBP_OK) return r;
   }
+  // A2..A7: the batched launches, then the usual kernel for M <= 16
+  double* frame_part = nullptr;
+  if (!lead->batch_plan.empty()) {
+    frame_part = lead->batch_plan[0].args.frame_part;
+    MPBP_CUDA(lead, cudaMemsetAsync(frame_part, 0, sizeof(double) * lead->batch_frames * kBatchWarpSlots, s));
+  }
+  for (int k = 0; k < nf; ++k) ctxs[fused[k]]->acc_dirty = true;
+  for (const auto& P : lead->batch_plan) {
+    if (P.m == 0) MPBP_CUDA(lead, batched_launch(P.args, P.grid, s));
+    else MPBP_CUDA(lead, batched_m_launch(P.m, P.args, P.grid, s));
+  }
+  std::vector<int> grid_of(n, 0);
+  for (int i = 0; i < n; ++i) {
+    mpbp_ctx* c = ctxs[i];
+    if (batch_fused_side(lead->batch_mode, c->M)) continue;
+    FrameArgs fa = frame_args(c, nullptr, (int)c->nframes);
+    grid_of[i] = frames_grid_for(c, c->nframes);
+    c->acc_dirty = true;
+    MPBP_CUDA(c, frames_launch(c->M, fa, grid_of[i], false, s));
+  }
+  // A6/A7 tail and A8 reductions per problem
+  int k = 0;
+  for (int i = 0; i < n; ++i) {
+    mpbp_ctx* c = ctxs[i];
+    FinishArgs fi{};
+    fi.rho = rho[i];
+    fi.u = u[i];
+    fi.alpha = alpha[i];
+    fi.acc = c->acc;
+    fi.g_rho = g_rho[i];
+    fi.g_u = g_u[i];
+    fi.part = c->part;
+    fi.arrivals = c->arrivals;
+    fi.npix = c->npix;
+    fi.D = c->D;
+    fi.C = c->C;
+    fi.pc = c->pc;
+    ReduceArgs ra{};
+    if (batch_fused_side(lead->batch_mode, c->M)) {
+      fi.loss_part = frame_part + base[k] * kBatchWarpSlots;
+      fi.n_loss_part = c->nframes * kBatchWarpSlots;
+      ++k;
+    } else {
+      fi.loss_part = c->loss_part;
+      fi.n_loss_part = grid_of[i];
+    }
+    ra.part = c->part;
+    ra.n_part = c->finish_grid;
+    ra.D = c->D;
+    ra.loss_out = loss[i];
+    ra.g_alpha_out = g_alpha ? g_alpha[i] : nullptr;
+    ra.g_alpha_ws = c->g_alpha_ws;
+    ra.err = c->err;
+    ra.st = nullptr;
+    ra.alpha_from = 1;
+    MPBP_CUDA(c, launch_finish(fi, ra, c->finish_grid, s));
+    c->acc_dirty = false;
+  }
+  return MPBP_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// autotuning: time each candidate schedule on the caller's data, keep the
+// fastest, optionally remember it in a JSON-lines cache file
+// ---------------------------------------------------------------------------
+namespace {
+
+std::string gpu_name(int dev) {
+  cudaDeviceProp prop{};
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "unknown";
+  std::string n(prop.name);
+  for (char& ch : n)
+    if (ch == '"' || ch == '\\') ch = '_';
+  return n;
+}
+
+// value of "field": <number> in a cache line whose "key" is `key` (-1: none)
+double cache_lookup(const char* path, const std::string& key, const char* field) {
+  if (!path) return -1.0;
+  std::ifstream in(path);
+  std::string line, want = "\"key\": \"" + key + "\"";
+  double found = -1.0;
+  while (std::getline(in, line)) {
+    if (line.find(want) == std::string::npos) continue;
+    const std::string f = std::string("\"") + field + "\": ";
+    const size_t p = line.find(f);
+    if (p == std::string::npos) continue;
+    found = std::atof(line.c_str() + p + f.size());   // the last matching line wins
+  }
+  return found;
+}
+
+void cache_store(const char* path, const std::string& key, const std::string& fields) {
+  if (!path) return;
+  std::ofstream out(path, std::ios::app);
+  out << "{\"key\": \"" << key << "\", " << fields << "}\n";
+}
+
+template <typename F>
+double time_ms(cudaStream_t s, int reps, F&& run, mpbp_status* st) {
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    *st = MPBP_ERR_CUDA;
+    return 0.0;
+  }
+  *st = run();   // warm-up
+  if (*st == MPBP_OK) cudaEventRecord(a, s);
+  for (int r = 0; r < reps && *st == MPBP_OK; ++r) *st = run();
+  float ms = 0.f;
+  if (*st == MPBP_OK) {
+    cudaEventRecord(b, s);
+    if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess)
+      *st = MPBP_ERR_CUDA;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms / reps;
+}
+
+}  // namespace
+
+extern "C" {
+
+mpbp_status mpbp_autotune(mpbp_ctx* c, const float* rho, const float* u, const float* alpha,
+                          double* loss, float* g_rho, float* g_u, const char* cache_path,
+                          void* stream) {
+  if (!c || !rho || !u || !alpha || !loss || !g_rho || !g_u)
+    return fail(c, MPBP_ERR_INVALID_ARG, "null argument");
+  if (!c->has_probe || !c->has_data) return fail(c, MPBP_ERR_NO_DATA, "probe or data not set");
+  std::ostringstream k;
+  k << gpu_name(c->device) << "|single|m" << c->M << "|d" << c->D << "|n" << c->n1 << "x" << c->n2
+    << "|f" << c->nframes;
+  const double cached = cache_lookup(cache_path, k.str(), "blocks_per_sm");
+  if (cached >= 1.0) return mpbp_set_schedule(c, (int32_t)cached);
+  cudaStream_t s = S(stream);
+  int best = c->fk.blocks_per_sm;
+  double best_ms = 1e30;
+  for (int b = 1; b <= c->fk.blocks_per_sm; ++b) {
+    mpbp_set_schedule(c, b);
+    mpbp_status st = MPBP_OK;
+    const double ms = time_ms(s, 3, [&]() {
+      return mpbp_loss_grad(c, rho, u, alpha, nullptr, 0, loss, g_rho, g_u, nullptr, stream);
+    }, &st);
+    if (st != MPBP_OK) return st;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = b;
+    }
+  }
+  mpbp_set_schedule(c, best);
+  std::ostringstream f;
+  f << "\"blocks_per_sm\": " << best << ", \"ms\": " << best_ms;
+  cache_store(cache_path, k.str(), f.str());
+  return MPBP_OK;
+}
+
+mpbp_status mpbp_autotune_batched(int32_t n, mpbp_ctx* const* ctxs, const float* const* rho,
+                                  const float* const* u, const float* const* alpha,
+                                  double* const* loss, float* const* g_rho, float* const* g_u,
+                                  const char* cache_path, void* stream) {
+  if (n < 1 || !ctxs || !ctxs[0]) return MPBP_ERR_INVALID_ARG;
+  mpbp_ctx* lead = ctxs[0];
+  std::ostringstream k;
+  k << gpu_name(lead->device) << "|batch";
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return fail(lead, MPBP_ERR_INVALID_ARG, "null context");
+    k << "|m" << ctxs[i]->M << "d" << ctxs[i]->D << "n" << ctxs[i]->n1 << "x" << ctxs[i]->n2 << "f"
+      << ctxs[i]->nframes;
+  }
+  const double cm = cache_lookup(cache_path, k.str(), "mode");
+  const double co = cache_lookup(cache_path, k.str(), "order");
+  if (cm >= 0.0 && co >= 0.0) return mpbp_set_batch_schedule(lead, (int32_t)cm, (int32_t)co);
+  cudaStream_t s = S(stream);
+  int best_m = lead->batch_mode, best_o = lead->batch_order;
+  double best_ms = 1e30;
+  for (int mode = 0; mode <= 3; ++mode) {
+    for (int order = 0; order <= 1; ++order) {
+      mpbp_set_batch_schedule(lead, mode, order);
+      mpbp_status st = MPBP_OK;
+      const double ms = time_ms(s, 3, [&]() {
+        return mpbp_loss_grad_batched(n, ctxs, rho, u, alpha, loss, g_rho, g_u, nullptr, stream);
+      }, &st);
+      if (st != MPBP_OK) return st;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_m = mode;
+        best_o = order;
+      }
+    }
+  }
+  mpbp_set_batch_schedule(lead, best_m, best_o);
+  std::ostringstream f;
+  f << "\"mode\": " << best_m << ", \"order\": " << best_o << ", \"ms\": " << best_ms;
+  cache_store(cache_path, k.str(), f.str());
   return MPBP_OK;
 }
 

@@ -80,13 +80,10 @@ __device__ void final_reduce(const ReduceArgs& a) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nq = a.D + 3;   // loss, df/dalpha_m (D), |g_rho|^2, |g_u|^2
   for (int q = w; q < nq; q += T / 32) {
+    // per-block partials: column D + 2 is the loss, columns 0..D+1 as named
+    const int col = q == 0 ? a.D + 2 : q - 1;
     double v = 0.0;
-    if (q == 0) {
-      for (int i = lane; i < a.n_loss_part; i += 32) v += __ldcg(a.loss_part + i);
-    } else {
-      const int m = q - 1;
-      for (int i = lane; i < a.n_part; i += 32) v += __ldcg(a.part + (long long)i * (a.D + 2) + m);
-    }
+    for (int i = lane; i < a.n_part; i += 32) v += __ldcg(a.part + (long long)i * (a.D + 3) + col);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) vals[q] = v;
@@ -130,7 +127,7 @@ constexpr int kFinishPixelsPerThread = 4;
 
 __global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a, ReduceArgs ra) {
   constexpr int NW = kFinishThreads / 32;
-  constexpr int NQ = kMaxPeaks + 2;
+  constexpr int NQ = kMaxPeaks + 3;
   __shared__ double wsum[NW][NQ];
   __shared__ bool last;
   float ap[kMaxPeaks];   // df/dalpha_m partials of this thread
@@ -178,8 +175,12 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a, Re
     n_rho = fmaf(gr, gr, n_rho);
     n_u += su;
   }
+  // this block's slice of the frame kernel's loss partials (FP64)
+  double lp = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n_loss_part; i += stride)
+    lp += __ldcg(a.loss_part + i);
   // partial sums: FP32 within the warp (a few pixels per lane), FP64 across
-  // warps and blocks; one barrier for all D + 2 quantities
+  // warps and blocks; one barrier for all D + 3 quantities
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
@@ -190,9 +191,12 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a, Re
       if (lane == 0) wsum[w][q] = (double)v;
     }
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lp += __shfl_xor_sync(0xffffffffu, lp, o);
+  if (lane == 0) wsum[w][a.D + 2] = lp;
   __syncthreads();
-  double* out = a.part + (long long)blockIdx.x * (a.D + 2);
-  if (w == 0 && lane < a.D + 2) {
+  double* out = a.part + (long long)blockIdx.x * (a.D + 3);
+  if (w == 0 && lane < a.D + 3) {
     double t = 0.0;
 #pragma unroll
     for (int i = 0; i < NW; ++i) t += wsum[i][lane];

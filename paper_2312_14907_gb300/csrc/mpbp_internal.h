@@ -60,16 +60,16 @@ struct FinishArgs {
   cf* acc;              // read, then cleared for the next evaluation
   float* g_rho;
   float* g_u;
-  double* part;         // [gridDim.x][D + 2]: df/dalpha_m partials, |g_rho|^2, |g_u|^2
+  double* part;         // [gridDim.x][D + 3]: df/dalpha_m partials, |g_rho|^2, |g_u|^2, loss
   unsigned* arrivals;   // blocks done (the last one runs the final reduction)
+  const double* loss_part;  // the frame kernel's loss partials, summed by slices
+  long long n_loss_part;
   long long npix;
   int D, C;
   PhaseCoef pc;
 };
 
 struct ReduceArgs {
-  const double* loss_part;
-  int n_loss_part;
   const double* part;
   int n_part;
   int D;

@@ -94,7 +94,7 @@ extern "C" mpbp_status mpbp_loss_grad_noalloc(const mpbp_problem* pr, const floa
   const size_t oAcc = take(sizeof(cf) * npix * pr->npeaks);
   const size_t oA = take(sizeof(float) * nframes * mm);
   const size_t oLP = take(sizeof(double) * (fgrid > 0 ? fgrid : 1));
-  const size_t oPart = take(sizeof(double) * pgrid * (pr->npeaks + 2));
+  const size_t oPart = take(sizeof(double) * pgrid * (pr->npeaks + 3));
   const size_t oErr = take(sizeof(int));
   const size_t oArr = take(sizeof(unsigned));
   if (off > kScratchBytes) return MPBP_ERR_UNSUPPORTED;
@@ -169,9 +169,9 @@ extern "C" mpbp_status mpbp_loss_grad_noalloc(const mpbp_problem* pr, const floa
   fi.D = pr->npeaks;
   fi.C = pr->ncomp;
   fi.pc = pc;
+  fi.loss_part = loss_part;
+  fi.n_loss_part = fgrid > 0 ? fgrid : 1;
   ReduceArgs ra{};
-  ra.loss_part = loss_part;
-  ra.n_loss_part = fgrid > 0 ? fgrid : 1;
   ra.part = part;
   ra.n_part = pgrid;
   ra.D = pr->npeaks;

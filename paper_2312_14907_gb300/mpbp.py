@@ -60,7 +60,8 @@ EXPORTS = ["mpbp_status_string", "mpbp_create", "mpbp_destroy", "mpbp_last_error
            "mpbp_get_info", "mpbp_set_probe", "mpbp_set_data", "mpbp_object_build",
            "mpbp_forward", "mpbp_loss_grad", "mpbp_loss_grad_host", "mpbp_step_init",
            "mpbp_step", "mpbp_loss_grad_batched", "mpbp_set_schedule", "mpbp_sync_status",
-           "mpbp_frames_timing", "mpbp_frames_timing_read", "mpbp_loss_grad_noalloc"]
+           "mpbp_frames_timing", "mpbp_frames_timing_read", "mpbp_loss_grad_noalloc",
+           "mpbp_set_batch_schedule", "mpbp_autotune", "mpbp_autotune_batched"]
 
 
 def library_path():
@@ -110,6 +111,12 @@ def load(build_if_missing=True):
     lib.mpbp_loss_grad_batched.restype = st
     lib.mpbp_set_schedule.argtypes = [V, I32]
     lib.mpbp_set_schedule.restype = st
+    lib.mpbp_set_batch_schedule.argtypes = [V, I32, I32]
+    lib.mpbp_set_batch_schedule.restype = st
+    lib.mpbp_autotune.argtypes = [V, V, V, V, V, V, V, ctypes.c_char_p, V]
+    lib.mpbp_autotune.restype = st
+    lib.mpbp_autotune_batched.argtypes = [I32, V, V, V, V, V, V, V, ctypes.c_char_p, V]
+    lib.mpbp_autotune_batched.restype = st
     lib.mpbp_sync_status.argtypes = [V, V]
     lib.mpbp_sync_status.restype = st
     lib.mpbp_frames_timing.argtypes = [V, I32]
@@ -218,6 +225,20 @@ class Problem:
 
     def set_schedule(self, blocks_per_sm):
         self._check(self._lib.mpbp_set_schedule(self._h, int(blocks_per_sm)), "mpbp_set_schedule")
+
+    def autotune(self, rho, u, alpha, cache_path=None):
+        """Pick the fastest frame-kernel schedule on this data (mpbp_autotune)."""
+        self._state(rho, u, alpha)
+        loss, g_rho, g_u, _ = self.loss_grad(rho, u, alpha)
+        cp = None if cache_path is None else os.fsencode(cache_path)
+        self._check(self._lib.mpbp_autotune(self._h, _p(rho), _p(u), _p(alpha), _p(loss), _p(g_rho),
+                                            _p(g_u), cp, _stream()), "mpbp_autotune")
+        return self.info()["blocks_per_sm"]
+
+    def set_batch_schedule(self, mode, order=0):
+        """Schedule of batched calls led by this problem (see mpbp_set_batch_schedule)."""
+        self._check(self._lib.mpbp_set_batch_schedule(self._h, int(mode), int(order)),
+                    "mpbp_set_batch_schedule")
 
     def set_probe(self, probe):
         shape = (self.npeaks, self.m, self.m) if self.probe_per_peak else (self.m, self.m)
@@ -367,6 +388,21 @@ def loss_grad_noalloc(spec_problem, probe, y, rho, u, alpha, out):
     if s != 0:
         raise MPBPError(s, "mpbp_loss_grad_noalloc")
     return out
+
+
+def autotune_batched(problems, states, cache_path=None):
+    """Pick the fastest schedule for loss_grad_batched on these problems."""
+    lib = load()
+    n = len(problems)
+    outs = loss_grad_batched(problems, states)
+    arr = lambda xs: (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+    ctxs = (ctypes.c_void_p * n)(*[p._h.value for p in problems])
+    cp = None if cache_path is None else os.fsencode(cache_path)
+    s = lib.mpbp_autotune_batched(n, ctxs, arr([s[0] for s in states]), arr([s[1] for s in states]),
+                                  arr([s[2] for s in states]), arr([o[0] for o in outs]),
+                                  arr([o[1] for o in outs]), arr([o[2] for o in outs]), cp, _stream())
+    if s != 0:
+        raise MPBPError(s, "mpbp_autotune_batched")
 
 
 class MPBPLoss(torch.autograd.Function):

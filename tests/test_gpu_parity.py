@@ -223,6 +223,11 @@ def test_batched_matches_single_problems():
              Case(*custom_spec(160, 64, 4, 30, npeaks=4, offset=-5, seed=2), state="perturbed"),
              Case(*custom_spec(200, 128, 2, 60, npeaks=3, offset=-10, seed=3), state="perturbed")]
     probs, states = zip(*[_gpu(c) for c in cases])
-    outs = mpbp.loss_grad_batched(list(probs), list(states))
-    for c, o in zip(cases, outs):
-        _check_loss_grad(c, o)
+    for mode in (0, 1, 2, 3):
+        for order in (0, 1):
+            probs[0].set_batch_schedule(mode, order)
+            outs = mpbp.loss_grad_batched(list(probs), list(states))
+            for c, o in zip(cases, outs):
+                _check_loss_grad(c, o)
+    for p in probs:
+        p.sync_status()
