@@ -261,7 +261,7 @@ def run_gpu(args):
         "hbm_roofline": {"bytes_per_frame": bpf, "achieved_gbs": value * bpf / 1e9 / world,
                          "peak_gbs": pk["hbm_gbs"], "frac": value * bpf / 1e9 / world / pk["hbm_gbs"],
                          "peak_src": pk["src"]},
-        "roofline": {"bound": "alu", "kernel": "frames_t1<64> (fused per-frame kernel)",
+        "roofline": {"bound": "alu", "kernel": "frames_t2<64, false> (fused per-frame kernel)",
                      "achieved": achieved_tf, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
                      "frac": achieved_tf / pk["fp32_tflops"], "traffic": traffic,
                      "kernel_ms": kavg_ms, "kernel_share_of_step": kavg_ms / (tot_ms / args.steps),
@@ -353,6 +353,26 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_drive(args):
+    """Profiling driver: set up workload `--drive K` (1, 2, 3 or 5) with
+    synthetic data and run `--drive-evals` loss+gradient evaluations, without
+    timing (for `ncu` captures of the kernels)."""
+    import torch
+    from paper_2312_14907_gb300 import mpbp
+    spec = synth.config(args.drive)
+    scan = synth.scan_positions(spec)
+    prob = mpbp.Problem.from_spec(spec, scan)
+    probe, y = make_inputs(spec, scan, prob, torch)
+    prob.set_probe(torch.from_numpy(probe).cuda())
+    prob.set_data(torch.from_numpy(y).cuda())
+    x = [torch.from_numpy(a.astype(np.float32)).cuda() for a in synth.init_state(spec)]
+    for _ in range(args.drive_evals):
+        prob.loss_grad(*x)
+    torch.cuda.synchronize()
+    prob.sync_status()
+    print("drove %s: %d evaluations" % (spec.name, args.drive_evals))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -362,7 +382,13 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-frames", type=int, default=600)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--drive", type=int, default=0,
+                    help="profiling driver: run workload 1, 2, 3 or 5 untimed")
+    ap.add_argument("--drive-evals", type=int, default=4)
     args = ap.parse_args()
+    if args.drive:
+        run_drive(args)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

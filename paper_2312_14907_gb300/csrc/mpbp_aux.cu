@@ -123,7 +123,7 @@ __device__ void final_reduce(const ReduceArgs& a) {
 }
 
 constexpr int kFinishThreads = 256;
-constexpr int kFinishPixelsPerThread = 4;
+constexpr int kFinishPixelsPerThread = 1;   // latency-bound: many warps, few pixels each
 
 __global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a, ReduceArgs ra) {
   constexpr int NW = kFinishThreads / 32;
@@ -284,7 +284,7 @@ cudaError_t launch_frame_transpose(const float* in, float* out, long long nframe
 
 int finish_grid(long long npix, int num_sms) {
   return grid_for((npix + kFinishPixelsPerThread - 1) / kFinishPixelsPerThread, kFinishThreads,
-                  num_sms * 2);
+                  num_sms * 4);
 }
 
 cudaError_t launch_finish(const FinishArgs& a, const ReduceArgs& r, int grid, cudaStream_t s) {

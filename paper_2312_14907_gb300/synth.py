@@ -240,6 +240,28 @@ def poisson_counts(I, seed):
     return rng.poisson(np.maximum(I, 0.0)).astype(np.float32)
 
 
+def template_counts(spec, seed):
+    """Count-like data [D][J][M][M] without any forward model: per peak a fixed
+    speckle template (a few Gaussian spots on a weak floor, DC at [0][0]) times
+    a seeded per-frame level, rounded.  For tests that only need some data of
+    the right shape and range (the loss and gradient are compared for the same
+    y on both sides)."""
+    rng = np.random.default_rng(seed)
+    m = spec.m
+    q = np.fft.fftfreq(m) * m
+    q0, q1 = np.meshgrid(q, q, indexing="ij")
+    tmpl = np.empty((spec.npeaks, m, m), np.float32)
+    for d in range(spec.npeaks):
+        t = 0.05 + np.zeros((m, m))
+        for _ in range(6):
+            c0, c1 = rng.normal(0, m / 8, 2)
+            w = rng.uniform(1.0, m / 16)
+            t += rng.uniform(5, 60) * np.exp(-((q0 - c0) ** 2 + (q1 - c1) ** 2) / (2 * w * w))
+        tmpl[d] = t
+    level = rng.uniform(0.2, 1.5, (spec.npeaks, spec.nscan)).astype(np.float32)
+    return np.rint(level[:, :, None, None] * tmpl[:, None, :, :]).astype(np.float32)
+
+
 def perturbed_state(spec, rng, scale=0.05):
     """A generic state near the truth (for gradient checks away from the optimum)."""
     rho, u = truth(spec)

@@ -1,0 +1,73 @@
+"""The two 128x128-frame workloads at full size (512^2 object, 4 peaks, 61x61
+scan; 1024^2 object, 6 peaks, 121x121 scan with the scan overhanging the
+grid), in the launch configuration of a full evaluation.
+
+The oracle's direct DFT cannot evaluate every frame in seconds here, so:
+- seeded frame subsets go through the same full-size context and launch path
+  and are compared element by element with the oracle on the same subset;
+- on the full frame set, properties that hold at any size: a uniform shift of
+  u leaves the loss unchanged, sum_r df/du_c = 0, sum rho df/drho =
+  sum alpha df/dalpha, and the loss is additive over a partition of frames.
+"""
+import numpy as np
+import pytest
+
+from helpers import rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _setup(k):
+    import oracle
+    from paper_2312_14907_gb300 import mpbp, synth
+    spec = synth.config(k)
+    scan = synth.scan_positions(spec)
+    rng = np.random.default_rng(spec.seed + 77)
+    probe = (synth.probe(spec) * 3.0).astype(np.complex64)
+    y = synth.template_counts(spec, spec.seed + 78)
+    rho, u, alpha = synth.perturbed_state(spec, rng, 0.05)
+    x = [np.ascontiguousarray(a, np.float32) for a in (rho, u, alpha)]
+    p = mpbp.Problem.from_spec(spec, scan)
+    p.set_probe(torch.from_numpy(probe).cuda())
+    yd = torch.from_numpy(y).cuda()
+    p.set_data(yd)
+    del yd
+    xd = [torch.from_numpy(a).cuda() for a in x]
+    orc = oracle.OracleProblem.from_spec(spec, scan)
+    return spec, p, orc, probe, y, x, xd, rng
+
+
+@pytest.mark.parametrize("k", [3, 5])
+def test_fullsize_sampled_frames_and_invariants(k):
+    spec, p, orc, probe, y, x, xd, rng = _setup(k)
+    nf = spec.nframes
+    # sampled subsets through the full-size context, element-wise vs the oracle
+    for trial in range(2):
+        frames = np.sort(rng.choice(nf, 6, replace=False)).astype(np.int32)
+        got = [t.cpu().numpy() for t in p.loss_grad(*xd, frames=torch.from_numpy(frames).cuda())]
+        f, gr, gu, ga = orc.loss_grad(*x, probe, y, frames=frames, nthreads=4)
+        assert abs(got[0][0] - f) <= 1e-5 * abs(f), (got[0][0], f)
+        assert rel_l2(got[1], gr) <= 1e-4
+        for c in range(3):
+            if np.abs(gu[c]).max() > 0:
+                assert rel_l2(got[2][c], gu[c]) <= 1e-4
+        assert rel_l2(got[3], ga) <= 1e-4
+    # every frame
+    loss, g_rho, g_u, g_alpha = p.loss_grad(*xd)
+    f_all = loss.item()
+    assert np.isfinite(f_all) and f_all > 0
+    shifted = (xd[1] + torch.tensor([0.21, -0.4, 0.9], device="cuda")[:, None, None]).contiguous()
+    f_shift = p.loss_grad(xd[0], shifted, xd[2])[0].item()
+    assert abs(f_shift - f_all) <= 2e-5 * f_all
+    gu64 = g_u.double()
+    for c in range(3):
+        assert abs(gu64[c].sum().item()) <= 2e-4 * gu64[c].abs().sum().item()
+    lhs = (xd[0].double() * g_rho.double()).sum().item()
+    rhs = (xd[2].double() * g_alpha).sum().item()
+    assert abs(lhs - rhs) <= 1e-4 * max(abs(lhs), abs(rhs))
+    perm = torch.from_numpy(rng.permutation(nf).astype(np.int32)).cuda()
+    parts = [perm[: nf // 3].contiguous(), perm[nf // 3:].contiguous()]
+    f_parts = sum(p.loss_grad(*xd, frames=q)[0].item() for q in parts)
+    assert abs(f_parts - f_all) <= 1e-6 * f_all
+    p.sync_status()
