@@ -73,10 +73,15 @@ struct mpbp_ctx {
   std::vector<int> batch_fused;       // batch positions of the fused problems
   long long batch_frames = 0;
   unsigned long long version = 0;     // bumped when probe or data change
-  // lazily allocated for the host-buffer entry point
+  // lazily allocated for the host-buffer entry point: inputs, two staging
+  // buffers for chunks of y, a copy stream and events for the pipeline
   float* io_x = nullptr;
   float* stage = nullptr;
-  size_t stage_elems = 0;
+  size_t stage_elems = 0;   // per staging buffer
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_ready = nullptr;          // caller's stream reached this call
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+  cudaEvent_t ev_consumed[2] = {nullptr, nullptr};
   bool has_probe = false, has_data = false;
   bool acc_dirty = false;
   // optional event timing of the fused frame kernel
@@ -125,6 +130,10 @@ bool batch_fused_side(int mode, int m) {
   return mode != 2 || m < 128;
 }
 
+// frame-range launches of one host-path evaluation (each writes its own
+// slice of the loss partials)
+constexpr int kMaxHostChunks = 8;
+
 int frames_grid_for(const mpbp_ctx* c, long long nframes) {
   const long long need = (nframes + c->fk.frames_per_block - 1) / c->fk.frames_per_block;
   long long g = std::min<long long>(need, c->frames_grid_cap);
@@ -146,6 +155,7 @@ FrameArgs frame_args(mpbp_ctx* c, const int* frames, int nframes) {
   a.arrivals = c->arrivals;
   a.obj_stride = c->npix;
   a.nframes = nframes;
+  a.frame0 = 0;
   a.nframes_total = (int)c->nframes;
   a.n1 = c->n1;
   a.n2 = c->n2;
@@ -292,7 +302,7 @@ mpbp_status mpbp_create(const mpbp_problem* pr, mpbp_ctx** out) {
 
   const long long mm = (long long)c->M * c->M;
   const int Dp = c->probe_per_peak ? c->D : 1;
-  const int max_frames_grid = c->num_sms * 64;
+  const int max_frames_grid = c->num_sms * 64 * kMaxHostChunks;
   Carver cv;
   size_t oO = cv.take<cf>(c->npix * c->D);
   size_t oAcc = cv.take<cf>(c->npix * c->D);
@@ -362,6 +372,12 @@ void mpbp_destroy(mpbp_ctx* c) {
   }
   if (c->ws) cudaFree(c->ws);
   if (c->io_x) cudaFree(c->io_x);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  if (c->ev_ready) cudaEventDestroy(c->ev_ready);
+  for (int i = 0; i < 2; ++i) {
+    if (c->ev_copied[i]) cudaEventDestroy(c->ev_copied[i]);
+    if (c->ev_consumed[i]) cudaEventDestroy(c->ev_consumed[i]);
+  }
   if (c->batch_ws) cudaFree(c->batch_ws);
   if (c->stage) cudaFree(c->stage);
   if (c->bgT) cudaFree(c->bgT);
@@ -468,6 +484,7 @@ mpbp_status mpbp_loss_grad_host(mpbp_ctx* c, const float* y, const float* rho, c
   if (!y && !c->has_data) return fail(c, MPBP_ERR_NO_DATA, "data not set");
   cudaStream_t s = S(stream);
   const long long nx = c->npix * (1 + c->C) + c->D;
+  const long long mm = (long long)c->M * c->M;
   if (!c->io_x) {
     cudaError_t e = cudaMalloc(&c->io_x, sizeof(float) * nx + sizeof(double) * 2);
     if (e != cudaSuccess) {
@@ -476,27 +493,6 @@ mpbp_status mpbp_loss_grad_host(mpbp_ctx* c, const float* y, const float* rho, c
       return fail(c, MPBP_ERR_OOM, "host-path buffers");
     }
   }
-  if (y) {
-    const long long mm = (long long)c->M * c->M;
-    const long long chunk_frames = std::max<long long>(1, std::min<long long>(c->nframes, (256LL << 20) / (4 * mm)));
-    if (!c->stage) {
-      cudaError_t e = cudaMalloc(&c->stage, sizeof(float) * chunk_frames * mm);
-      if (e != cudaSuccess) {
-        cudaGetLastError();
-        c->stage = nullptr;
-        return fail(c, MPBP_ERR_OOM, "host-path staging buffer");
-      }
-      c->stage_elems = chunk_frames * mm;
-    }
-    const long long cf_ = (long long)c->stage_elems / mm;
-    for (long long f0 = 0; f0 < c->nframes; f0 += cf_) {
-      const long long nf = std::min(cf_, c->nframes - f0);
-      MPBP_CUDA(c, cudaMemcpyAsync(c->stage, y + f0 * mm, sizeof(float) * nf * mm,
-                                   cudaMemcpyHostToDevice, s));
-      MPBP_CUDA(c, launch_frame_transpose(c->stage, c->aT + f0 * mm, nf, c->M, true, s));
-    }
-    c->has_data = true;
-  }
   float* drho = c->io_x;
   float* du = drho + c->npix;
   float* dalpha = du + c->npix * c->C;
@@ -504,9 +500,100 @@ mpbp_status mpbp_loss_grad_host(mpbp_ctx* c, const float* y, const float* rho, c
   MPBP_CUDA(c, cudaMemcpyAsync(drho, rho, sizeof(float) * c->npix, cudaMemcpyHostToDevice, s));
   MPBP_CUDA(c, cudaMemcpyAsync(du, u, sizeof(float) * c->npix * c->C, cudaMemcpyHostToDevice, s));
   MPBP_CUDA(c, cudaMemcpyAsync(dalpha, alpha, sizeof(float) * c->D, cudaMemcpyHostToDevice, s));
-  mpbp_status r = enqueue_loss_grad(c, drho, du, dalpha, nullptr, 0, dloss, c->g_rho_ws,
-                                    c->g_u_ws, nullptr, nullptr, s);
+  if (c->acc_dirty) {
+    MPBP_CUDA(c, cudaMemsetAsync(c->acc, 0, sizeof(cf) * c->npix * c->D, s));
+    c->acc_dirty = false;
+  }
+  mpbp_status r = enqueue_object_build(c, drho, du, dalpha, c->O, s);
   if (r != MPBP_OK) return r;
+
+  // frames in chunks: chunk k's data is copied on the copy stream while the
+  // caller's stream transposes and evaluates chunk k - 1 (the gradient
+  // accumulator sums over the chunk launches, each with its own loss slice)
+  int nchunks = 1;
+  if (y) nchunks = (int)std::min<long long>(kMaxHostChunks, std::max<long long>(1, c->nframes / 512));
+  const long long per = (c->nframes + nchunks - 1) / nchunks;
+  if (y) {
+    if (!c->copy_stream) {
+      if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c->ev_copied[0], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c->ev_copied[1], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c->ev_consumed[0], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c->ev_consumed[1], cudaEventDisableTiming) != cudaSuccess)
+        return fail(c, MPBP_ERR_CUDA, "copy stream");
+    }
+    if ((size_t)(per * mm) > c->stage_elems) {
+      MPBP_CUDA(c, cudaStreamSynchronize(s));
+      MPBP_CUDA(c, cudaStreamSynchronize(c->copy_stream));
+      if (c->stage) cudaFree(c->stage);
+      c->stage = nullptr;
+      c->stage_elems = 0;
+      cudaError_t e = cudaMalloc(&c->stage, sizeof(float) * 2 * per * mm);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, MPBP_ERR_OOM, "host-path staging buffers");
+      }
+      c->stage_elems = per * mm;
+    }
+    // the copies must not overtake earlier work of this call's stream
+    MPBP_CUDA(c, cudaEventRecord(c->ev_ready, s));
+    MPBP_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->ev_ready, 0));
+  }
+  c->acc_dirty = true;
+  int nparts = 0;
+  for (int k = 0; k < nchunks; ++k) {
+    const long long f0 = k * per;
+    const long long nf = std::min(per, c->nframes - f0);
+    if (nf <= 0) break;
+    if (y) {
+      float* st = c->stage + (k & 1) * c->stage_elems;
+      if (k >= 2) MPBP_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->ev_consumed[k & 1], 0));
+      MPBP_CUDA(c, cudaMemcpyAsync(st, y + f0 * mm, sizeof(float) * nf * mm, cudaMemcpyHostToDevice,
+                                   c->copy_stream));
+      MPBP_CUDA(c, cudaEventRecord(c->ev_copied[k & 1], c->copy_stream));
+      MPBP_CUDA(c, cudaStreamWaitEvent(s, c->ev_copied[k & 1], 0));
+      MPBP_CUDA(c, launch_frame_transpose(st, c->aT + f0 * mm, nf, c->M, true, s));
+      MPBP_CUDA(c, cudaEventRecord(c->ev_consumed[k & 1], s));
+    }
+    FrameArgs fa = frame_args(c, nullptr, (int)nf);
+    fa.frame0 = (int)f0;
+    fa.loss_part = c->loss_part + nparts;
+    fa.arrivals = k == 0 ? c->arrivals : nullptr;
+    const int grid = frames_grid_for(c, nf);
+    MPBP_CUDA(c, frames_launch(c->M, fa, grid, false, s));
+    nparts += grid;
+  }
+  if (y) c->has_data = true;
+
+  FinishArgs fi{};
+  fi.rho = drho;
+  fi.u = du;
+  fi.alpha = dalpha;
+  fi.acc = c->acc;
+  fi.g_rho = c->g_rho_ws;
+  fi.g_u = c->g_u_ws;
+  fi.part = c->part;
+  fi.npix = c->npix;
+  fi.D = c->D;
+  fi.C = c->C;
+  fi.pc = c->pc;
+  fi.arrivals = c->arrivals;
+  fi.loss_part = c->loss_part;
+  fi.n_loss_part = nparts;
+  ReduceArgs ra{};
+  ra.part = c->part;
+  ra.n_part = c->finish_grid;
+  ra.D = c->D;
+  ra.loss_out = dloss;
+  ra.g_alpha_out = nullptr;
+  ra.g_alpha_ws = c->g_alpha_ws;
+  ra.err = c->err;
+  ra.st = nullptr;
+  ra.alpha_from = 1;
+  MPBP_CUDA(c, launch_finish(fi, ra, c->finish_grid, s));
+  c->acc_dirty = false;
+
   MPBP_CUDA(c, cudaMemcpyAsync(loss, dloss, sizeof(double), cudaMemcpyDeviceToHost, s));
   if (g_rho)
     MPBP_CUDA(c, cudaMemcpyAsync(g_rho, c->g_rho_ws, sizeof(float) * c->npix, cudaMemcpyDeviceToHost, s));

@@ -31,6 +31,7 @@ struct FrameArgs {
                         // cleared here, before that kernel can start
   long long obj_stride; // n1*n2
   int nframes;          // frames to process
+  int frame0;           // without a frame list: frames frame0 .. frame0 + nframes - 1
   int nframes_total;    // D*J (bound for frame indices)
   int n1, n2, J;
   int probe_stride;     // M*M when one probe per peak, else 0

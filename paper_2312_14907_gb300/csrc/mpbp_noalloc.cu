@@ -149,6 +149,7 @@ extern "C" mpbp_status mpbp_loss_grad_noalloc(const mpbp_problem* pr, const floa
   fa.arrivals = arrivals;
   fa.obj_stride = npix;
   fa.nframes = (int)nframes;
+  fa.frame0 = 0;
   fa.nframes_total = (int)nframes;
   fa.n1 = pr->n1;
   fa.n2 = pr->n2;
