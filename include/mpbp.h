@@ -49,7 +49,7 @@ typedef enum {
   MPBP_ERR_UNSUPPORTED = 2,  /* valid problem the kernels do not cover (M)   */
   MPBP_ERR_CUDA = 3,         /* a CUDA runtime call failed                   */
   MPBP_ERR_NONFINITE = 4,    /* the loss came out NaN or infinite            */
-  MPBP_ERR_TIMEOUT = 5,      /* reserved: no kernel of this library waits   */
+  MPBP_ERR_TIMEOUT = 5,      /* a bounded wait of the tensor-core kernel ran out */
   MPBP_ERR_BOUNDS = 6,       /* a frame index outside [0, npeaks*nscan)      */
   MPBP_ERR_OOM = 7,          /* device allocation failed                     */
   MPBP_ERR_NO_DATA = 8       /* probe or measured data not set yet           */
@@ -102,7 +102,14 @@ typedef struct {
   int32_t num_sms;
   int32_t launches_loss_grad; /* kernels + memsets enqueued by mpbp_loss_grad  */
   int32_t launches_step;      /* kernels + memsets enqueued by mpbp_step       */
+  int32_t precision;          /* MPBP_PRECISION_* of the gradient evaluations */
 } mpbp_info;
+
+/* Arithmetic of the 2-D DFTs (F of Eq. 2 and its adjoint in the gradient). */
+enum {
+  MPBP_PRECISION_FP32 = 0,      /* FP32 radix-2 FFTs on the CUDA cores (default) */
+  MPBP_PRECISION_TC_SPLIT16 = 1 /* dense DFT matrices on the tensor cores        */
+};
 
 /* Name of a status code (static string). */
 const char *mpbp_status_string(mpbp_status s);
@@ -213,6 +220,25 @@ mpbp_status mpbp_loss_grad_noalloc(const mpbp_problem *problem, const float *pro
 /* Overrides the fused frame kernel's schedule: resident blocks per SM used to
  * size its persistent grid (0 = occupancy maximum).  Host-side only. */
 mpbp_status mpbp_set_schedule(mpbp_ctx *ctx, int32_t blocks_per_sm);
+
+/* Selects the arithmetic of the DFT passes (Eq. 2: Psi = F psi, and the
+ * adjoint F^H chi of the gradient) in this context's gradient evaluations.
+ *   MPBP_PRECISION_FP32: FP32 radix-2 FFTs in registers (default).
+ *   MPBP_PRECISION_TC_SPLIT16: each 1-D pass is a product with the dense DFT
+ *     matrix on the tensor cores (tcgen05.mma): operands split into an FP16
+ *     high and low part after a per-frame power-of-two scaling, products
+ *     hi*hi + hi*lo + lo*hi accumulated in FP32 (about 2^-21 relative error
+ *     per transform, against about 2^-22 log2(M) for the FFTs).  Frame side
+ *     M = 64 only: MPBP_ERR_UNSUPPORTED for other M, and the context keeps
+ *     its previous mode.
+ * Applies to mpbp_loss_grad, mpbp_loss_grad_host, mpbp_step and to problems
+ * that mpbp_loss_grad_batched launches on their own (batch mode 3, or a side
+ * the mode does not fuse); mpbp_forward and the fused batched kernels always
+ * use the FFTs.  Resets the schedule to the selected kernel's occupancy
+ * maximum.  The first switch to TC_SPLIT16 allocates and uploads a 64 KB
+ * table and synchronises the device.  A device error word bit from a bounded
+ * wait of that kernel is reported by mpbp_sync_status as MPBP_ERR_TIMEOUT. */
+mpbp_status mpbp_set_precision(mpbp_ctx *ctx, int32_t mode);
 
 /* Turns on (enable != 0) or off the recording of CUDA events around every
  * launch of the fused frame kernel, on the stream it is launched on.  Off by

@@ -56,4 +56,18 @@ bool frames_prepare(int m, FrameKernelInfo* info);
 // otherwise loss partials and the gradient accumulator.
 cudaError_t frames_launch(int m, const FrameArgs& a, int grid, bool forward, cudaStream_t s);
 
+// Tensor-core variant of the gradient kernel for m = 64 (frames_tc.cu): the
+// DFT passes as split-FP16 GEMMs on tcgen05.  Two frames in flight per
+// 256-thread block.
+constexpr int kTcThreads = 256;
+constexpr int kTcFramesPerBlock = 2;
+constexpr size_t kTcSplitBytes = 2 * 128 * 128 * 2;   // W hi + lo, FP16
+
+// W hi and lo in the kernel's tensor-memory layout (kTcSplitBytes / 4 words, host)
+void tc_split_dft64(uint32_t* out);
+// Prepares the kernel on the current device: shared memory, occupancy.
+bool tc_prepare(int* blocks_per_sm, int* smem_bytes);
+// wsplit: device copy of tc_split_dft64's table (16-byte aligned)
+cudaError_t tc_launch(const FrameArgs& a, const void* wsplit, int grid, cudaStream_t s);
+
 }  // namespace mpbp

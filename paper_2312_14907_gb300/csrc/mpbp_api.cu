@@ -28,7 +28,10 @@ struct mpbp_ctx {
   long long nframes = 0;  // D * J
   PhaseCoef pc{};
   // kernel schedule
-  FrameKernelInfo fk{};
+  FrameKernelInfo fk{};       // the gradient kernel in use
+  FrameKernelInfo fk_fft{};   // the FFT kernels (forward mode always uses them)
+  int precision = MPBP_PRECISION_FP32;
+  void* tc_w = nullptr;       // split DFT matrix of the tensor-core kernel
   int blocks_per_sm = 0;  // schedule in use
   int frames_grid_cap = 0;
   int finish_grid = 0;
@@ -140,6 +143,19 @@ int frames_grid_for(const mpbp_ctx* c, long long nframes) {
   return (int)std::max<long long>(g, 1);
 }
 
+// grid of the forward-mode FFT kernel: occupancy maximum
+int frames_grid_fft(const mpbp_ctx* c, long long nframes) {
+  const long long need = (nframes + c->fk_fft.frames_per_block - 1) / c->fk_fft.frames_per_block;
+  long long g = std::min<long long>(need, (long long)c->num_sms * c->fk_fft.blocks_per_sm);
+  return (int)std::max<long long>(g, 1);
+}
+
+// the gradient-mode frame kernel of the context's precision
+cudaError_t launch_frames(const mpbp_ctx* c, const FrameArgs& fa, int grid, cudaStream_t s) {
+  if (c->precision == MPBP_PRECISION_TC_SPLIT16) return tc_launch(fa, c->tc_w, grid, s);
+  return frames_launch(c->M, fa, grid, false, s);
+}
+
 FrameArgs frame_args(mpbp_ctx* c, const int* frames, int nframes) {
   FrameArgs a{};
   a.O = c->O;
@@ -207,7 +223,7 @@ mpbp_status enqueue_loss_grad(mpbp_ctx* c, const float* rho, const float* u, con
     ev1 = c->ev_pool[c->ev_used].second;
     c->ev_used++;
   }
-  MPBP_CUDA(c, frames_launch(c->M, fa, grid, false, s));
+  MPBP_CUDA(c, launch_frames(c, fa, grid, s));
   if (ev1) MPBP_CUDA(c, cudaEventRecord(ev1, s));
 
   FinishArgs fi{};
@@ -296,6 +312,7 @@ mpbp_status mpbp_create(const mpbp_problem* pr, mpbp_ctx** out) {
       c->pc.kps[m][k] = (float)(pr->phase_scale * g);
     }
   if (!frames_prepare(c->M, &c->fk)) return bail(MPBP_ERR_CUDA);
+  c->fk_fft = c->fk;
   c->blocks_per_sm = c->fk.blocks_per_sm;
   c->frames_grid_cap = c->num_sms * c->blocks_per_sm;
   c->finish_grid = finish_grid(c->npix, c->num_sms);
@@ -381,6 +398,7 @@ void mpbp_destroy(mpbp_ctx* c) {
   if (c->batch_ws) cudaFree(c->batch_ws);
   if (c->stage) cudaFree(c->stage);
   if (c->bgT) cudaFree(c->bgT);
+  if (c->tc_w) cudaFree(c->tc_w);
   delete c;
 }
 
@@ -394,7 +412,37 @@ mpbp_status mpbp_get_info(const mpbp_ctx* c, mpbp_info* info) {
   info->num_sms = c->num_sms;
   info->launches_loss_grad = 3;  // object build, frames, gradient assembly + reductions
   info->launches_step = 4;       // + update
+  info->precision = c->precision;
   return MPBP_OK;
+}
+
+mpbp_status mpbp_set_precision(mpbp_ctx* c, int32_t mode) {
+  if (!c) return MPBP_ERR_INVALID_ARG;
+  if (mode != MPBP_PRECISION_FP32 && mode != MPBP_PRECISION_TC_SPLIT16)
+    return fail(c, MPBP_ERR_INVALID_ARG, "unknown precision mode");
+  if (mode == MPBP_PRECISION_FP32) {
+    c->fk = c->fk_fft;
+  } else {
+    if (c->M != 64) return fail(c, MPBP_ERR_UNSUPPORTED, "tensor-core DFTs need frame side 64");
+    int bps = 0, smem = 0;
+    if (!tc_prepare(&bps, &smem)) return fail(c, MPBP_ERR_CUDA, "tensor-core kernel cannot run here");
+    if (!c->tc_w) {
+      std::vector<uint32_t> w(kTcSplitBytes / 4);
+      tc_split_dft64(w.data());
+      MPBP_CUDA(c, cudaDeviceSynchronize());
+      void* d = nullptr;
+      if (cudaMalloc(&d, kTcSplitBytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, MPBP_ERR_OOM, "cudaMalloc of the DFT table failed");
+      }
+      c->tc_w = d;
+      MPBP_CUDA(c, cudaMemcpy(d, w.data(), kTcSplitBytes, cudaMemcpyHostToDevice));
+    }
+    c->fk = FrameKernelInfo{kTcThreads, smem, kTcFramesPerBlock, bps};
+  }
+  c->precision = mode;
+  c->batch_key.clear();
+  return mpbp_set_schedule(c, 0);
 }
 
 mpbp_status mpbp_set_schedule(mpbp_ctx* c, int32_t blocks_per_sm) {
@@ -462,7 +510,7 @@ mpbp_status mpbp_forward(mpbp_ctx* c, const float* rho, const float* u, const fl
   FrameArgs fa = frame_args(c, nullptr, (int)c->nframes);
   fa.I_out = I_out;
   fa.arrivals = nullptr;
-  MPBP_CUDA(c, frames_launch(c->M, fa, frames_grid_for(c, c->nframes), true, S(stream)));
+  MPBP_CUDA(c, frames_launch(c->M, fa, frames_grid_fft(c, c->nframes), true, S(stream)));
   return MPBP_OK;
 }
 
@@ -561,7 +609,7 @@ mpbp_status mpbp_loss_grad_host(mpbp_ctx* c, const float* y, const float* rho, c
     fa.loss_part = c->loss_part + nparts;
     fa.arrivals = k == 0 ? c->arrivals : nullptr;
     const int grid = frames_grid_for(c, nf);
-    MPBP_CUDA(c, frames_launch(c->M, fa, grid, false, s));
+    MPBP_CUDA(c, launch_frames(c, fa, grid, s));
     nparts += grid;
   }
   if (y) c->has_data = true;
@@ -829,7 +877,7 @@ mpbp_status mpbp_loss_grad_batched(int32_t n, mpbp_ctx* const* ctxs, const float
     FrameArgs fa = frame_args(c, nullptr, (int)c->nframes);
     grid_of[i] = frames_grid_for(c, c->nframes);
     c->acc_dirty = true;
-    MPBP_CUDA(c, frames_launch(c->M, fa, grid_of[i], false, s));
+    MPBP_CUDA(c, launch_frames(c, fa, grid_of[i], s));
   }
   // A6/A7 tail and A8 reductions per problem
   int k = 0;
@@ -943,7 +991,7 @@ mpbp_status mpbp_autotune(mpbp_ctx* c, const float* rho, const float* u, const f
     return fail(c, MPBP_ERR_INVALID_ARG, "null argument");
   if (!c->has_probe || !c->has_data) return fail(c, MPBP_ERR_NO_DATA, "probe or data not set");
   std::ostringstream k;
-  k << gpu_name(c->device) << "|single|m" << c->M << "|d" << c->D << "|n" << c->n1 << "x" << c->n2
+  k << gpu_name(c->device) << "|single|m" << c->M << "|p" << c->precision << "|d" << c->D << "|n" << c->n1 << "x" << c->n2
     << "|f" << c->nframes;
   const double cached = cache_lookup(cache_path, k.str(), "blocks_per_sm");
   if (cached >= 1.0) return mpbp_set_schedule(c, (int32_t)cached);
@@ -1039,6 +1087,7 @@ mpbp_status mpbp_sync_status(mpbp_ctx* c, void* stream) {
   if (h) MPBP_CUDA(c, cudaMemset(c->err, 0, sizeof(int)));
   if (h & kErrBounds) return fail(c, MPBP_ERR_BOUNDS, "frame index out of range");
   if (h & kErrNonfinite) return fail(c, MPBP_ERR_NONFINITE, "non-finite loss");
+  if (h & kErrTimeout) return fail(c, MPBP_ERR_TIMEOUT, "a tensor-core wait ran out");
   return MPBP_OK;
 }
 

@@ -53,7 +53,8 @@ class Info(ctypes.Structure):
     _fields_ = [("workspace_bytes", ctypes.c_int64), ("frames_grid", ctypes.c_int32),
                 ("frames_block", ctypes.c_int32), ("frames_smem", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("num_sms", ctypes.c_int32),
-                ("launches_loss_grad", ctypes.c_int32), ("launches_step", ctypes.c_int32)]
+                ("launches_loss_grad", ctypes.c_int32), ("launches_step", ctypes.c_int32),
+                ("precision", ctypes.c_int32)]
 
 
 EXPORTS = ["mpbp_status_string", "mpbp_create", "mpbp_destroy", "mpbp_last_error",
@@ -61,7 +62,11 @@ EXPORTS = ["mpbp_status_string", "mpbp_create", "mpbp_destroy", "mpbp_last_error
            "mpbp_forward", "mpbp_loss_grad", "mpbp_loss_grad_host", "mpbp_step_init",
            "mpbp_step", "mpbp_loss_grad_batched", "mpbp_set_schedule", "mpbp_sync_status",
            "mpbp_frames_timing", "mpbp_frames_timing_read", "mpbp_loss_grad_noalloc",
-           "mpbp_set_batch_schedule", "mpbp_autotune", "mpbp_autotune_batched"]
+           "mpbp_set_batch_schedule", "mpbp_autotune", "mpbp_autotune_batched",
+           "mpbp_set_precision"]
+
+PRECISION_FP32 = 0        # FFTs on the CUDA cores
+PRECISION_TC_SPLIT16 = 1  # dense DFT matrices on the tensor cores, split FP16
 
 
 def library_path():
@@ -111,6 +116,8 @@ def load(build_if_missing=True):
     lib.mpbp_loss_grad_batched.restype = st
     lib.mpbp_set_schedule.argtypes = [V, I32]
     lib.mpbp_set_schedule.restype = st
+    lib.mpbp_set_precision.argtypes = [V, I32]
+    lib.mpbp_set_precision.restype = st
     lib.mpbp_set_batch_schedule.argtypes = [V, I32, I32]
     lib.mpbp_set_batch_schedule.restype = st
     lib.mpbp_autotune.argtypes = [V, V, V, V, V, V, V, ctypes.c_char_p, V]
@@ -222,6 +229,11 @@ class Problem:
         inf = Info()
         self._check(self._lib.mpbp_get_info(self._h, ctypes.byref(inf)), "mpbp_get_info")
         return {k: getattr(inf, k) for k, _ in Info._fields_}
+
+    def set_precision(self, mode):
+        """DFT arithmetic of the gradient evaluations: PRECISION_FP32 (FFTs) or
+        PRECISION_TC_SPLIT16 (tensor cores, frame side 64 only)."""
+        self._check(self._lib.mpbp_set_precision(self._h, int(mode)), "mpbp_set_precision")
 
     def set_schedule(self, blocks_per_sm):
         self._check(self._lib.mpbp_set_schedule(self._h, int(blocks_per_sm)), "mpbp_set_schedule")
