@@ -2,10 +2,10 @@
 // Eq. 2 computed on the tensor cores (tcgen05.mma, accumulators in TMEM).
 //
 // Each 1-D pass of the 2-D transform is one real GEMM
-//   D[r][n] = sum_K W[r][K] X[n][K],    r = 2q + po,  K = 64 pi + k,
-//   W[2q + 0][k] = cos,  W[2q + 0][64 + k] = sin,
-//   W[2q + 1][k] = -sin, W[2q + 1][64 + k] = cos     (theta = 2 pi q k / 64),
-// with M = 128 (64 complex outputs, real and imaginary rows interleaved),
+//   D[r][n] = sum_K W[r][K] X[n][K],    r = row (q, po),  K = 64 pi + k,
+//   W[(q, 0)][k] = cos,  W[(q, 0)][64 + k] = sin,
+//   W[(q, 1)][k] = -sin, W[(q, 1)][64 + k] = cos     (theta = 2 pi q k / 64),
+// with M = 128 (64 complex outputs, a real and an imaginary row each),
 // N = 64 (the other index of the frame) and K = 128 (the real parts of the 64
 // inputs, then their imaginary parts).  W is a constant held in tensor memory
 // as the A operand; the data X is the B operand in shared memory.  Both are
@@ -14,16 +14,20 @@
 // D = Wh Xh + Wh Xl + Wl Xh is accumulated in FP32, which keeps about 22
 // significant bits of each operand.
 //
-// Because the accumulator row 2q + po of one pass is the operand row q (part
+// Because an accumulator row (q, po) of one pass is the operand row q (part
 // po) of the next, each thread writes the next operand straight from its own
 // accumulator row (thread t reads TMEM lane t); only the residual and the
-// scatter, which need both parts of one value, trade halves with the
-// neighbouring lane.  Passes:
-//   forward   X[k1][k0]  = psi(k0, k1)            -> D = F_0 psi     [2q0+po][k1]
-//             X[q0][k1]  = D                      -> D = Psi         [2q1+po][q0]
+// scatter, which need both parts of one value, trade halves with the partner
+// lane.  The rows of W, and so the TMEM lanes, are ordered so that lane t
+// holds transform row q(t) = (t mod 16) + 16 (t div 32), part po(t) =
+// (t div 16) mod 2: the partner is lane t ^ 16 of the same warp, and eight
+// neighbouring lanes write eight different operand rows (no bank conflicts).
+// Passes:
+//   forward   X[k1][k0]  = psi(k0, k1)            -> D = F_0 psi     [(q0,po)][k1]
+//             X[q0][k1]  = D                      -> D = Psi         [(q1,po)][q0]
 //   residual  (A4) on Psi; its conj(chi) becomes the next operand
-//   adjoint   X[q1][q0]  = conj(chi)(q0, q1)      -> D = F_0 conj(chi) [2k0+po][q1]
-//             X[k0][q1]  = D                      -> D = Z           [2k1+po][k0]
+//   adjoint   X[q1][q0]  = conj(chi)(q0, q1)      -> D = F_0 conj(chi) [(k0,po)][q1]
+//             X[k0][q1]  = D                      -> D = Z           [(k1,po)][k0]
 //   scatter   acc_m(s_j + (k0, k1)) += P(k0, k1) Z(k0, k1)      (A6 + A7)
 // with Z = F conj(chi) = conj(F^H chi), exactly as in the FFT kernels.
 //
@@ -129,16 +133,17 @@ MPBP_DI void tmem_row64(uint32_t taddr, float (&d)[64]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Neighbouring lanes (accumulator rows 2i + 0 and 2i + 1: real and imaginary
-// part of transform row i) trade halves.  Afterwards the lane of part po
-// holds both parts of columns 32 po .. 32 po + 31: re[j], im[j] of 32 po + j.
+// Partner lanes t and t ^ 16 (accumulator rows (i, 0) and (i, 1): real and
+// imaginary part of transform row i) trade halves.  Afterwards the lane of
+// part po holds both parts of columns 32 po .. 32 po + 31: re[j], im[j] of
+// column 32 po + j.
 MPBP_DI void pair_columns(const float (&d)[64], int po, float (&re)[32], float (&im)[32]) {
   const bool hi = po != 0;
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
     const float keep = hi ? d[32 + j] : d[j];
     const float send = hi ? d[j] : d[32 + j];
-    const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
+    const float recv = __shfl_xor_sync(0xffffffffu, send, 16);
     re[j] = hi ? recv : keep;
     im[j] = hi ? keep : recv;
   }
@@ -261,11 +266,15 @@ MPBP_DI void tc_pass(TcGroup& G, int* err) {
   }
 }
 
+// one warp polls the completion barrier; the others sleep in the group barrier
 MPBP_DI void tc_wait(TcGroup& G, int* err) {
-  uint32_t done = G.ok ? try_wait(G.mbar, G.phase) : 1u;
-  if (!done) {
-    const unsigned long long t0 = global_ns();
-    while (!(done = try_wait(G.mbar, G.phase)) && global_ns() - t0 < kWaitNs) {
+  uint32_t done = 1u;
+  if (G.t < 32 && G.ok) {
+    done = try_wait(G.mbar, G.phase);
+    if (!done) {
+      const unsigned long long t0 = global_ns();
+      while (!(done = try_wait(G.mbar, G.phase)) && global_ns() - t0 < kWaitNs) {
+      }
     }
   }
   G.phase ^= 1u;
@@ -340,8 +349,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) frames_tc64(const FrameArgs p, 
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
   const int t = G.t;
-  const int rq = t >> 1;    // transform row of this thread's accumulator row
-  const int po = t & 1;     // its part
+  const int rq = (t & 15) | ((t >> 5) << 4);   // transform row of this thread's TMEM lane
+  const int po = (t >> 4) & 1;                  // its part
   const uint32_t dlane = G.dcol + G.lane;
   double lsum = 0.0;
   float d[64], cre[32], cim[32];
@@ -381,7 +390,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) frames_tc64(const FrameArgs p, 
         split_store8(G.bh, G.bl, rq, 64 + 32 * po + 8 * c, cim + 8 * c, s);
       }
     }
-    tc_pass(G, p.err);   // [2q0 + po][k1] = 2^e1 F_0 psi
+    tc_pass(G, p.err);   // [(q0, po)][k1] = 2^e1 F_0 psi
     if (has_next) fetch_patch(p, G, nxt);   // every thread is past its patch reads
     tc_wait(G, p.err);
 
@@ -389,7 +398,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) frames_tc64(const FrameArgs p, 
     if (G.ok) tmem_row64(dlane, d);
 #pragma unroll
     for (int c = 0; c < 8; ++c) split_store8(G.bh, G.bl, rq, 64 * po + 8 * c, d + 8 * c, pow2f(-6));
-    tc_pass(G, p.err);   // [2q1 + po][q0] = 2^(e1 - 6) Psi
+    tc_pass(G, p.err);   // [(q1, po)][q0] = 2^(e1 - 6) Psi
     tc_wait(G, p.err);
 
     // A4: row q1 = rq of Psi; after the pairing this thread has q0 = 32 po + j
@@ -399,13 +408,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) frames_tc64(const FrameArgs p, 
       pair_columns(d, po, cre, cim);
       const float un = pow2f(6 - e1);
       const float* bg = p.bgT ? p.bgT + (long long)cur.f * TM * TM + rq * TM + 32 * po : nullptr;
+      float av[32];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {   // q0 = 32 po + 4i .. + 3
+        const float4 v = *reinterpret_cast<const float4*>(G.at + at_idx(rq, 32 * po + 4 * i));
+        av[4 * i] = v.x;
+        av[4 * i + 1] = v.y;
+        av[4 * i + 2] = v.z;
+        av[4 * i + 3] = v.w;
+      }
       float fl = 0.0f, mx = 0.0f;
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
-        const int q0 = 32 * po + j;
-        const float av = G.at[at_idx(rq, q0)];
         const float bv = bg ? __ldg(bg + j) : 0.0f;
-        const cf z = residual(cf{cre[j] * un, cim[j] * un}, av, bv, fl);
+        const cf z = residual(cf{cre[j] * un, cim[j] * un}, av[j], bv, fl);
         cre[j] = z.x;
         cim[j] = z.y;
         mx = abs_max(abs_max(mx, z.x), z.y);
@@ -419,14 +435,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) frames_tc64(const FrameArgs p, 
         split_store8(G.bh, G.bl, rq, 64 + 32 * po + 8 * c, cim + 8 * c, s);
       }
     }
-    tc_pass(G, p.err);   // [2k0 + po][q1] = 2^e3 F_0 conj(chi)
+    tc_pass(G, p.err);   // [(k0, po)][q1] = 2^e3 F_0 conj(chi)
     if (has_next) fetch_at(p, G, nxt);   // every thread is past its sqrt(y) reads
     tc_wait(G, p.err);
 
     if (G.ok) tmem_row64(dlane, d);
 #pragma unroll
     for (int c = 0; c < 8; ++c) split_store8(G.bh, G.bl, rq, 64 * po + 8 * c, d + 8 * c, pow2f(-6));
-    tc_pass(G, p.err);   // [2k1 + po][k0] = 2^(e3 - 6) Z
+    tc_pass(G, p.err);   // [(k1, po)][k0] = 2^(e3 - 6) Z
     // the probe values of the scatter load while the pass runs
     cf pv[32];
 #pragma unroll
@@ -461,11 +477,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) frames_tc64(const FrameArgs p, 
 }
 
 // W hi and lo as the A operand in tensor memory: [2][128 rows][64 columns],
-// column c of a row holding elements 2c (low half) and 2c + 1 (high half)
+// column c of a row holding elements 2c (low half) and 2c + 1 (high half);
+// row r is transform row (r mod 16) + 16 (r div 32), part (r div 16) mod 2
 void tc_split_dft64(uint32_t* out) {
   const double two_pi = 6.283185307179586476925286766559;
   for (int r = 0; r < TK; ++r) {
-    const int q = r >> 1, po = r & 1;
+    const int q = (r & 15) | ((r >> 5) << 4), po = (r >> 4) & 1;
     for (int c = 0; c < W_COLS; ++c) {
       uint16_t hv[2], lv[2];
       for (int e = 0; e < 2; ++e) {
