@@ -53,11 +53,12 @@ def hbm_bytes_per_frame(spec):
 
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    out = {"hbm_gbs": 6800.0, "src": "fallback", "sm_max_mhz": 2070.0}
+    out = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "src": "fallback", "sm_max_mhz": 2070.0}
     try:
         with open(path) as f:
             d = json.load(f)
         out.update({"hbm_gbs": float(d["hbm_gbs"]), "src": "measured",
+                    "bf16_tflops": float(d.get("bf16_tflops", 1900.0)),
                     "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0))})
     except Exception:
         pass
@@ -276,8 +277,50 @@ def run_gpu(args):
         "clocks": clk.summary(),
         "wall_s": wall,
     }
+    # the tensor-core precision mode on the same steps (not the headline):
+    # per-step time and its frame kernel's duration, CUDA events as above
+    if spec.m == 64:
+        prob.set_precision(mpbp.PRECISION_TC_SPLIT16)
+        xs = [t.clone() for t in x]
+        st2 = prob.step_init(t0, w_rho=1.0, w_u=1e-3, w_alpha=1e-3)
+        for _ in range(args.warmup):
+            prob.step(*xs, st2)
+        n_tc = max(3, min(args.steps, 20))
+        evt = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_tc)]
+        prob.frames_timing(True)
+        torch.cuda.synchronize()
+        for k in range(n_tc):
+            flush.zero_()
+            evt[k][0].record(stream)
+            prob.step(*xs, st2)
+            evt[k][1].record(stream)
+        torch.cuda.synchronize()
+        prob.frames_timing(False)
+        tk_ms, tk_n = prob.frames_timing_read()
+        prob.sync_status()
+        tc_step = sum(a.elapsed_time(b) for a, b in evt) / n_tc
+        tk_avg = tk_ms / max(tk_n, 1)
+        tc_flops = 4 * 3 * 2 * 128 * 64 * 128   # 4 passes x 3 split products, M=128 N=64 K=128
+        line["alt_precision"] = {
+            "mode": "tc_split16 (DFT matrices on tcgen05 tensor cores, split-FP16 operands, FP32 accumulation)",
+            "ms_per_step": tc_step, "value": spec.nframes / (tc_step / 1e3), "unit": UNIT,
+            "kernel": "frames_tc64", "kernel_ms": tk_avg,
+            "tensor_tflops": tc_flops * spec.nframes / (tk_avg / 1e3) / 1e12,
+            "tensor_flops_per_frame": tc_flops,
+            "tensor_peak_tflops": pk["bf16_tflops"], "peak_src": pk["src"] + " (dense bf16 = fp16 rate)"}
+        prob.set_precision(mpbp.PRECISION_FP32)
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(spec, scan, probe, y, budget_s=args.cpu_budget)
+        def gpu_eval(rho, u, alpha, precision):
+            prob.set_precision(precision)
+            got = prob.loss_grad(*[torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+                                   for a in (rho, u, alpha)])
+            prob.set_precision(mpbp.PRECISION_FP32)
+            return [t.cpu().numpy() for t in got]
+        modes = {"fp32_fft": mpbp.PRECISION_FP32}
+        if spec.m == 64:
+            modes["tc_split16"] = mpbp.PRECISION_TC_SPLIT16
+        line["cpu_baseline"] = cpu_baseline(spec, scan, probe, y, budget_s=args.cpu_budget,
+                                            gpu_eval=gpu_eval, modes=modes)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -295,21 +338,38 @@ def kernel_revision():
     return h.hexdigest()[:12]
 
 
-def cpu_baseline(spec, scan, probe, y, budget_s=20.0):
+def cpu_baseline(spec, scan, probe, y, budget_s=20.0, gpu_eval=None, modes=None):
     """The FP64 oracle, as it stands, on the host cores: whole evaluations of
-    all frames of the problem, repeated until about `budget_s` seconds."""
+    all frames of the problem at a seeded perturbed state, repeated until about
+    `budget_s` seconds.  With gpu_eval, the GPU result at the same state in
+    each precision mode is compared with the oracle's (loss relative error,
+    relative L2 error of each gradient block)."""
     import oracle
     p = oracle.OracleProblem.from_spec(spec, scan)
-    rho0, u0, a0 = synth.init_state(spec)
+    rho, u, alpha = synth.perturbed_state(spec, np.random.default_rng(spec.seed + 5), 0.05)
     n, t = 0, 0.0
+    ref = None
     while t < budget_s and n < 50:
         t1 = time.perf_counter()
-        p.loss_grad(rho0, u0, a0, probe, y)
+        ref = p.loss_grad(rho, u, alpha, probe, y)
         t += time.perf_counter() - t1
         n += 1
-    return {"value": n * spec.nframes / t, "unit": UNIT, "cores": oracle.max_threads(),
-            "kind": "oracle",
-            "sample": "%d full loss+gradient evaluation(s) of all %d frames (%.1f s)" % (n, spec.nframes, t)}
+    out = {"value": n * spec.nframes / t, "unit": UNIT, "cores": oracle.max_threads(),
+           "kind": "oracle",
+           "sample": "%d full loss+gradient evaluation(s) of all %d frames (%.1f s)" % (n, spec.nframes, t)}
+    if gpu_eval is not None:
+        def rel(a, b):
+            a, b = np.asarray(a, np.float64).ravel(), np.asarray(b, np.float64).ravel()
+            return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+        par = {}
+        for name, mode in (modes or {}).items():
+            loss, g_rho, g_u, g_alpha = gpu_eval(rho, u, alpha, mode)
+            par[name] = {"loss_rel_err": abs(float(loss[0]) - ref[0]) / abs(ref[0]),
+                         "g_rho_rel_l2": rel(g_rho, ref[1]), "g_u_rel_l2": rel(g_u, ref[2]),
+                         "g_alpha_rel_l2": rel(g_alpha, ref[3])}
+        out["gpu_vs_oracle"] = {"state": "seeded 5% perturbation of the true object, all frames",
+                                "tolerance": {"loss": 1e-5, "gradients": 1e-4}, **par}
+    return out
 
 
 def run_reference(args):

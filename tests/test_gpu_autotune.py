@@ -34,7 +34,7 @@ def test_single_problem_autotune_and_cache(tmp_path):
     b = p.autotune(*x, cache_path=str(cache))
     assert 1 <= b <= p.info()["blocks_per_sm"] or b >= 1
     lines = [json.loads(l) for l in cache.read_text().splitlines()]
-    assert len(lines) == 1 and lines[0]["blocks_per_sm"] == b and "|single|m64|d3|" in lines[0]["key"]
+    assert len(lines) == 1 and lines[0]["blocks_per_sm"] == b and "|single|m64|p0|d3|" in lines[0]["key"]
     _check(case, p.loss_grad(*x))
     # a second problem of the same shape reads the cache instead of tuning
     p2, x2 = _gpu(case)
