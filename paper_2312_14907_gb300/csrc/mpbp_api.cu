@@ -82,9 +82,12 @@ struct mpbp_ctx {
   float* stage = nullptr;
   size_t stage_elems = 0;   // per staging buffer
   cudaStream_t copy_stream = nullptr;
-  cudaEvent_t ev_ready = nullptr;          // caller's stream reached this call
-  cudaEvent_t ev_copied[2] = {nullptr, nullptr};
-  cudaEvent_t ev_consumed[2] = {nullptr, nullptr};
+  cudaStream_t chunk_stream[2] = {nullptr, nullptr};   // alternating chunk launches
+  cudaEvent_t ev_ready = nullptr;          // caller's stream reached the frame launches
+  cudaEvent_t ev_x = nullptr;              // rho, u, alpha are on the device
+  cudaEvent_t ev_copied[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_consumed[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_done[2] = {nullptr, nullptr};
   bool has_probe = false, has_data = false;
   bool acc_dirty = false;
   // optional event timing of the fused frame kernel
@@ -136,6 +139,7 @@ bool batch_fused_side(int mode, int m) {
 // frame-range launches of one host-path evaluation (each writes its own
 // slice of the loss partials)
 constexpr int kMaxHostChunks = 8;
+constexpr int kStageSlots = 3;   // staging buffers of the host-buffer entry point
 
 int frames_grid_for(const mpbp_ctx* c, long long nframes) {
   const long long need = (nframes + c->fk.frames_per_block - 1) / c->fk.frames_per_block;
@@ -391,9 +395,14 @@ void mpbp_destroy(mpbp_ctx* c) {
   if (c->io_x) cudaFree(c->io_x);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   if (c->ev_ready) cudaEventDestroy(c->ev_ready);
-  for (int i = 0; i < 2; ++i) {
+  if (c->ev_x) cudaEventDestroy(c->ev_x);
+  for (int i = 0; i < kStageSlots; ++i) {
     if (c->ev_copied[i]) cudaEventDestroy(c->ev_copied[i]);
     if (c->ev_consumed[i]) cudaEventDestroy(c->ev_consumed[i]);
+  }
+  for (int i = 0; i < 2; ++i) {
+    if (c->chunk_stream[i]) cudaStreamDestroy(c->chunk_stream[i]);
+    if (c->ev_done[i]) cudaEventDestroy(c->ev_done[i]);
   }
   if (c->batch_ws) cudaFree(c->batch_ws);
   if (c->stage) cudaFree(c->stage);
@@ -545,31 +554,31 @@ mpbp_status mpbp_loss_grad_host(mpbp_ctx* c, const float* y, const float* rho, c
   float* du = drho + c->npix;
   float* dalpha = du + c->npix * c->C;
   double* dloss = reinterpret_cast<double*>(c->io_x + align_up(nx, 2));
-  MPBP_CUDA(c, cudaMemcpyAsync(drho, rho, sizeof(float) * c->npix, cudaMemcpyHostToDevice, s));
-  MPBP_CUDA(c, cudaMemcpyAsync(du, u, sizeof(float) * c->npix * c->C, cudaMemcpyHostToDevice, s));
-  MPBP_CUDA(c, cudaMemcpyAsync(dalpha, alpha, sizeof(float) * c->D, cudaMemcpyHostToDevice, s));
-  if (c->acc_dirty) {
-    MPBP_CUDA(c, cudaMemsetAsync(c->acc, 0, sizeof(cf) * c->npix * c->D, s));
-    c->acc_dirty = false;
-  }
-  mpbp_status r = enqueue_object_build(c, drho, du, dalpha, c->O, s);
-  if (r != MPBP_OK) return r;
-
-  // frames in chunks: chunk k's data is copied on the copy stream while the
-  // caller's stream transposes and evaluates chunk k - 1 (the gradient
-  // accumulator sums over the chunk launches, each with its own loss slice)
+  // Frames in chunks.  Chunk k of y is copied by the copy engine into one of
+  // kStageSlots staging buffers while earlier chunks are evaluated.  On the
+  // thread-pair frame sides (FP32 precision) the frame kernel reads the
+  // staged counts in their natural layout and writes sqrt(y) into the
+  // context's layout itself, and the chunk launches alternate between two
+  // streams so that one chunk's last frames overlap the next chunk's first;
+  // otherwise each chunk is transposed into the context's layout and
+  // evaluated on the caller's stream.  The gradient accumulator sums over the
+  // chunk launches, each with its own slice of loss partials.
+  const bool raw = y && c->precision == MPBP_PRECISION_FP32 && frames_raw_supported(c->M);
   int nchunks = 1;
-  if (y) nchunks = (int)std::min<long long>(kMaxHostChunks, std::max<long long>(1, c->nframes / 512));
+  if (y) nchunks = (int)std::min<long long>(kMaxHostChunks, std::max<long long>(1, c->nframes / (raw ? 256 : 512)));
   const long long per = (c->nframes + nchunks - 1) / nchunks;
   if (y) {
     if (!c->copy_stream) {
-      if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
-          cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming) != cudaSuccess ||
-          cudaEventCreateWithFlags(&c->ev_copied[0], cudaEventDisableTiming) != cudaSuccess ||
-          cudaEventCreateWithFlags(&c->ev_copied[1], cudaEventDisableTiming) != cudaSuccess ||
-          cudaEventCreateWithFlags(&c->ev_consumed[0], cudaEventDisableTiming) != cudaSuccess ||
-          cudaEventCreateWithFlags(&c->ev_consumed[1], cudaEventDisableTiming) != cudaSuccess)
-        return fail(c, MPBP_ERR_CUDA, "copy stream");
+      bool ok = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) == cudaSuccess &&
+                cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming) == cudaSuccess &&
+                cudaEventCreateWithFlags(&c->ev_x, cudaEventDisableTiming) == cudaSuccess;
+      for (int i = 0; i < 2 && ok; ++i)
+        ok = cudaStreamCreateWithFlags(&c->chunk_stream[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&c->ev_done[i], cudaEventDisableTiming) == cudaSuccess;
+      for (int i = 0; i < kStageSlots && ok; ++i)
+        ok = cudaEventCreateWithFlags(&c->ev_copied[i], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&c->ev_consumed[i], cudaEventDisableTiming) == cudaSuccess;
+      if (!ok) return fail(c, MPBP_ERR_CUDA, "host-path streams");
     }
     if ((size_t)(per * mm) > c->stage_elems) {
       MPBP_CUDA(c, cudaStreamSynchronize(s));
@@ -577,40 +586,92 @@ mpbp_status mpbp_loss_grad_host(mpbp_ctx* c, const float* y, const float* rho, c
       if (c->stage) cudaFree(c->stage);
       c->stage = nullptr;
       c->stage_elems = 0;
-      cudaError_t e = cudaMalloc(&c->stage, sizeof(float) * 2 * per * mm);
+      cudaError_t e = cudaMalloc(&c->stage, sizeof(float) * kStageSlots * per * mm);
       if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(c, MPBP_ERR_OOM, "host-path staging buffers");
       }
       c->stage_elems = per * mm;
     }
-    // the copies must not overtake earlier work of this call's stream
-    MPBP_CUDA(c, cudaEventRecord(c->ev_ready, s));
-    MPBP_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->ev_ready, 0));
   }
+  auto copy_chunk = [&](int k) -> mpbp_status {
+    const int slot = k % kStageSlots;
+    const long long f0 = k * per;
+    const long long nf = std::min(per, c->nframes - f0);
+    if (k >= kStageSlots) MPBP_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->ev_consumed[slot], 0));
+    MPBP_CUDA(c, cudaMemcpyAsync(c->stage + slot * c->stage_elems, y + f0 * mm, sizeof(float) * nf * mm,
+                                 cudaMemcpyHostToDevice, c->copy_stream));
+    MPBP_CUDA(c, cudaEventRecord(c->ev_copied[slot], c->copy_stream));
+    return MPBP_OK;
+  };
+
+  // The host link carries rho, u, alpha first, then the first chunks of y.
+  // io_x and the staging buffers are used by this function alone, and its
+  // last call released them before it returned, so these copies need not
+  // wait for anything.
+  cudaStream_t xs = y ? c->copy_stream : s;
+  MPBP_CUDA(c, cudaMemcpyAsync(drho, rho, sizeof(float) * c->npix, cudaMemcpyHostToDevice, xs));
+  MPBP_CUDA(c, cudaMemcpyAsync(du, u, sizeof(float) * c->npix * c->C, cudaMemcpyHostToDevice, xs));
+  MPBP_CUDA(c, cudaMemcpyAsync(dalpha, alpha, sizeof(float) * c->D, cudaMemcpyHostToDevice, xs));
+  if (y) {
+    MPBP_CUDA(c, cudaEventRecord(c->ev_x, c->copy_stream));
+    for (int k = 0; k < nchunks && k < kStageSlots; ++k) {
+      mpbp_status rc = copy_chunk(k);
+      if (rc != MPBP_OK) return rc;
+    }
+    MPBP_CUDA(c, cudaStreamWaitEvent(s, c->ev_x, 0));
+  }
+  if (c->acc_dirty) {
+    MPBP_CUDA(c, cudaMemsetAsync(c->acc, 0, sizeof(cf) * c->npix * c->D, s));
+    c->acc_dirty = false;
+  }
+  mpbp_status r = enqueue_object_build(c, drho, du, dalpha, c->O, s);
+  if (r != MPBP_OK) return r;
+  // the frame launches follow the object build and any earlier work of the
+  // caller's stream (which may still read the data being replaced)
+  if (y) MPBP_CUDA(c, cudaEventRecord(c->ev_ready, s));
   c->acc_dirty = true;
   int nparts = 0;
   for (int k = 0; k < nchunks; ++k) {
     const long long f0 = k * per;
     const long long nf = std::min(per, c->nframes - f0);
     if (nf <= 0) break;
-    if (y) {
-      float* st = c->stage + (k & 1) * c->stage_elems;
-      if (k >= 2) MPBP_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->ev_consumed[k & 1], 0));
-      MPBP_CUDA(c, cudaMemcpyAsync(st, y + f0 * mm, sizeof(float) * nf * mm, cudaMemcpyHostToDevice,
-                                   c->copy_stream));
-      MPBP_CUDA(c, cudaEventRecord(c->ev_copied[k & 1], c->copy_stream));
-      MPBP_CUDA(c, cudaStreamWaitEvent(s, c->ev_copied[k & 1], 0));
-      MPBP_CUDA(c, launch_frame_transpose(st, c->aT + f0 * mm, nf, c->M, true, s));
-      MPBP_CUDA(c, cudaEventRecord(c->ev_consumed[k & 1], s));
-    }
     FrameArgs fa = frame_args(c, nullptr, (int)nf);
     fa.frame0 = (int)f0;
     fa.loss_part = c->loss_part + nparts;
     fa.arrivals = k == 0 ? c->arrivals : nullptr;
     const int grid = frames_grid_for(c, nf);
-    MPBP_CUDA(c, launch_frames(c, fa, grid, s));
+    if (y) {
+      const int slot = k % kStageSlots;
+      float* st = c->stage + slot * c->stage_elems;
+      if (k >= kStageSlots) {
+        mpbp_status rc = copy_chunk(k);
+        if (rc != MPBP_OK) return rc;
+      }
+      if (raw) {
+        cudaStream_t cs = c->chunk_stream[k & 1];
+        if (k < 2) MPBP_CUDA(c, cudaStreamWaitEvent(cs, c->ev_ready, 0));
+        MPBP_CUDA(c, cudaStreamWaitEvent(cs, c->ev_copied[slot], 0));
+        fa.yraw = st - f0 * mm;   // indexed by absolute frame number
+        fa.aT_w = c->aT;
+        MPBP_CUDA(c, frames_launch_raw(c->M, fa, grid, cs));
+        MPBP_CUDA(c, cudaEventRecord(c->ev_consumed[slot], cs));
+      } else {
+        MPBP_CUDA(c, cudaStreamWaitEvent(s, c->ev_copied[slot], 0));
+        MPBP_CUDA(c, launch_frame_transpose(st, c->aT + f0 * mm, nf, c->M, true, s));
+        MPBP_CUDA(c, cudaEventRecord(c->ev_consumed[slot], s));
+        MPBP_CUDA(c, launch_frames(c, fa, grid, s));
+      }
+    } else {
+      MPBP_CUDA(c, launch_frames(c, fa, grid, s));
+    }
     nparts += grid;
+  }
+  if (raw) {
+    for (int i = 0; i < 2 && i < nchunks; ++i) {
+      MPBP_CUDA(c, cudaEventRecord(c->ev_done[i], c->chunk_stream[i]));
+      MPBP_CUDA(c, cudaStreamWaitEvent(s, c->ev_done[i], 0));
+    }
   }
   if (y) c->has_data = true;
 

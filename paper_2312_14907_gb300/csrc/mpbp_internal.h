@@ -36,6 +36,12 @@ struct FrameArgs {
   int nframes_total;    // D*J (bound for frame indices)
   int n1, n2, J;
   int probe_stride;     // M*M when one probe per peak, else 0
+  // raw-data variant of the gradient kernel (M >= 32): the measured counts
+  // y (natural layout [q0][q1], frame f at yraw + f*M*M) are read instead of
+  // the context's sqrt(y), and sqrt(y) is written to aT_w in the context's
+  // transposed layout on the way
+  const float* yraw;
+  float* aT_w;
 };
 
 // Per-pixel coefficients of phi_m = phase_scale * G_m . u.

@@ -201,6 +201,36 @@ def test_host_buffer_entry_point_matches_device_path():
     _check_loss_grad(case, [torch.from_numpy(h) for h in host])
 
 
+@pytest.mark.parametrize("m,pinned", [(32, True), (64, False), (128, True), (16, True)])
+def test_host_entry_point_paths(m, pinned):
+    """Chunks of y copied into staging buffers are read in their natural
+    layout by the frame kernel on thread-pair sides (M >= 32), and transposed
+    by a separate kernel for M = 16; from page-locked or pageable host memory.
+    Either way the result matches the device path, and y becomes the
+    context's data for later device calls."""
+    from paper_2312_14907_gb300 import mpbp
+    n = max(3 * m, 48)
+    spec, scan = custom_spec(n, m, 5, m // 2, npeaks=2, offset=-m // 8, seed=m)
+    case = Case(spec, scan=scan, state="perturbed")
+    p, x = _gpu(case)
+    dev = [t.cpu().numpy() for t in p.loss_grad(*x)]
+    # a second context without data: the host call supplies it
+    q = mpbp.Problem.from_spec(case.spec, case.scan)
+    q.set_probe(torch.from_numpy(case.probe).cuda())
+    host_t = lambda a: torch.from_numpy(np.ascontiguousarray(a))
+    wrap = (lambda a: host_t(a).pin_memory()) if pinned else host_t
+    host = [t.numpy() for t in q.loss_grad_host(wrap(case.rho), wrap(case.u), wrap(case.alpha),
+                                                 y=wrap(case.y))]
+    assert abs(host[0][0] - dev[0][0]) <= 1e-6 * abs(dev[0][0])
+    for a, b in zip(host[1:], dev[1:]):
+        assert rel_l2(a, b) <= 1e-5
+    again = [t.cpu().numpy() for t in q.loss_grad(*x)]   # device call on the data y left behind
+    assert abs(again[0][0] - dev[0][0]) <= 1e-6 * abs(dev[0][0])
+    for a, b in zip(again[1:], dev[1:]):
+        assert rel_l2(a, b) <= 1e-5
+    q.sync_status()
+
+
 def test_autograd_function():
     from paper_2312_14907_gb300 import mpbp
     spec, scan = custom_spec(40, 16, 4, 6, npeaks=2, offset=0)
