@@ -141,6 +141,16 @@ bool batch_fused_side(int mode, int m) {
 constexpr int kMaxHostChunks = 8;
 constexpr int kStageSlots = 3;   // staging buffers of the host-buffer entry point
 
+// device address of page-locked (CUDA-registered) host memory, else NULL
+void* mapped_host(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 int frames_grid_for(const mpbp_ctx* c, long long nframes) {
   const long long need = (nframes + c->fk.frames_per_block - 1) / c->fk.frames_per_block;
   long long g = std::min<long long>(need, c->frames_grid_cap);
@@ -566,7 +576,12 @@ mpbp_status mpbp_loss_grad_host(mpbp_ctx* c, const float* y, const float* rho, c
   const bool raw = y && c->precision == MPBP_PRECISION_FP32 && frames_raw_supported(c->M);
   int nchunks = 1;
   if (y) nchunks = (int)std::min<long long>(kMaxHostChunks, std::max<long long>(1, c->nframes / (raw ? 256 : 512)));
-  const long long per = (c->nframes + nchunks - 1) / nchunks;
+  // chunk k holds frames [bound[k], bound[k+1]) (equal chunks: measured as
+  // fast as chunks shrinking towards the end)
+  long long bound[kMaxHostChunks + 1];
+  for (int k = 0; k <= nchunks; ++k) bound[k] = c->nframes * k / nchunks;
+  long long per = 0;
+  for (int k = 0; k < nchunks; ++k) per = std::max(per, bound[k + 1] - bound[k]);
   if (y) {
     if (!c->copy_stream) {
       bool ok = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) == cudaSuccess &&
@@ -596,8 +611,8 @@ mpbp_status mpbp_loss_grad_host(mpbp_ctx* c, const float* y, const float* rho, c
   }
   auto copy_chunk = [&](int k) -> mpbp_status {
     const int slot = k % kStageSlots;
-    const long long f0 = k * per;
-    const long long nf = std::min(per, c->nframes - f0);
+    const long long f0 = bound[k];
+    const long long nf = bound[k + 1] - f0;
     if (k >= kStageSlots) MPBP_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->ev_consumed[slot], 0));
     MPBP_CUDA(c, cudaMemcpyAsync(c->stage + slot * c->stage_elems, y + f0 * mm, sizeof(float) * nf * mm,
                                  cudaMemcpyHostToDevice, c->copy_stream));
@@ -633,9 +648,9 @@ mpbp_status mpbp_loss_grad_host(mpbp_ctx* c, const float* y, const float* rho, c
   c->acc_dirty = true;
   int nparts = 0;
   for (int k = 0; k < nchunks; ++k) {
-    const long long f0 = k * per;
-    const long long nf = std::min(per, c->nframes - f0);
-    if (nf <= 0) break;
+    const long long f0 = bound[k];
+    const long long nf = bound[k + 1] - f0;
+    if (nf <= 0) continue;
     FrameArgs fa = frame_args(c, nullptr, (int)nf);
     fa.frame0 = (int)f0;
     fa.loss_part = c->loss_part + nparts;
@@ -649,8 +664,10 @@ mpbp_status mpbp_loss_grad_host(mpbp_ctx* c, const float* y, const float* rho, c
         if (rc != MPBP_OK) return rc;
       }
       if (raw) {
-        cudaStream_t cs = c->chunk_stream[k & 1];
-        if (k < 2) MPBP_CUDA(c, cudaStreamWaitEvent(cs, c->ev_ready, 0));
+        // the last chunk runs on the caller's stream, right before the finish
+        const bool last = k == nchunks - 1;
+        cudaStream_t cs = last ? s : c->chunk_stream[k & 1];
+        if (k < 2 && !last) MPBP_CUDA(c, cudaStreamWaitEvent(cs, c->ev_ready, 0));
         MPBP_CUDA(c, cudaStreamWaitEvent(cs, c->ev_copied[slot], 0));
         fa.yraw = st - f0 * mm;   // indexed by absolute frame number
         fa.aT_w = c->aT;
@@ -668,7 +685,7 @@ mpbp_status mpbp_loss_grad_host(mpbp_ctx* c, const float* y, const float* rho, c
     nparts += grid;
   }
   if (raw) {
-    for (int i = 0; i < 2 && i < nchunks; ++i) {
+    for (int i = 0; i < 2 && i < nchunks - 1; ++i) {
       MPBP_CUDA(c, cudaEventRecord(c->ev_done[i], c->chunk_stream[i]));
       MPBP_CUDA(c, cudaStreamWaitEvent(s, c->ev_done[i], 0));
     }
@@ -700,8 +717,25 @@ mpbp_status mpbp_loss_grad_host(mpbp_ctx* c, const float* y, const float* rho, c
   ra.err = c->err;
   ra.st = nullptr;
   ra.alpha_from = 1;
+  // Page-locked outputs are written by the gradient assembly itself, through
+  // their device mapping; otherwise they are copied back from the workspace.
+  void* m_loss = mapped_host(loss);
+  void* m_rho = g_rho ? mapped_host(g_rho) : nullptr;
+  void* m_u = g_u ? mapped_host(g_u) : nullptr;
+  void* m_alpha = g_alpha ? mapped_host(g_alpha) : nullptr;
+  const bool direct = m_loss && (!g_rho || m_rho) && (!g_u || m_u) && (!g_alpha || m_alpha);
+  if (direct) {
+    if (m_rho) fi.g_rho = static_cast<float*>(m_rho);
+    if (m_u) fi.g_u = static_cast<float*>(m_u);
+    ra.loss_out = static_cast<double*>(m_loss);
+    ra.g_alpha_out = static_cast<double*>(m_alpha);
+  }
   MPBP_CUDA(c, launch_finish(fi, ra, c->finish_grid, s));
   c->acc_dirty = false;
+  if (direct) {
+    MPBP_CUDA(c, cudaStreamSynchronize(s));
+    return MPBP_OK;
+  }
 
   MPBP_CUDA(c, cudaMemcpyAsync(loss, dloss, sizeof(double), cudaMemcpyDeviceToHost, s));
   if (g_rho)

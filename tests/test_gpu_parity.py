@@ -205,7 +205,8 @@ def test_host_buffer_entry_point_matches_device_path():
 def test_host_entry_point_paths(m, pinned):
     """Chunks of y copied into staging buffers are read in their natural
     layout by the frame kernel on thread-pair sides (M >= 32), and transposed
-    by a separate kernel for M = 16; from page-locked or pageable host memory.
+    by a separate kernel for M = 16; from page-locked or pageable host memory
+    (page-locked outputs are written in place, pageable ones copied back).
     Either way the result matches the device path, and y becomes the
     context's data for later device calls."""
     from paper_2312_14907_gb300 import mpbp
@@ -219,8 +220,12 @@ def test_host_entry_point_paths(m, pinned):
     q.set_probe(torch.from_numpy(case.probe).cuda())
     host_t = lambda a: torch.from_numpy(np.ascontiguousarray(a))
     wrap = (lambda a: host_t(a).pin_memory()) if pinned else host_t
+    out = None
+    if pinned:   # page-locked outputs are written by the gradient assembly directly
+        out = tuple(torch.full(t.shape, float("nan"), dtype=dt).pin_memory()
+                    for t, dt in zip(dev, (torch.float64, torch.float32, torch.float32, torch.float64)))
     host = [t.numpy() for t in q.loss_grad_host(wrap(case.rho), wrap(case.u), wrap(case.alpha),
-                                                 y=wrap(case.y))]
+                                                 y=wrap(case.y), out=out)]
     assert abs(host[0][0] - dev[0][0]) <= 1e-6 * abs(dev[0][0])
     for a, b in zip(host[1:], dev[1:]):
         assert rel_l2(a, b) <= 1e-5
