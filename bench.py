@@ -426,6 +426,7 @@ def run_drive(args):
     prob.set_probe(torch.from_numpy(probe).cuda())
     prob.set_data(torch.from_numpy(y).cuda())
     x = [torch.from_numpy(a.astype(np.float32)).cuda() for a in synth.init_state(spec)]
+    prob.set_precision(args.drive_precision)
     for _ in range(args.drive_evals):
         prob.loss_grad(*x)
     torch.cuda.synchronize()
@@ -445,6 +446,8 @@ def main():
     ap.add_argument("--drive", type=int, default=0,
                     help="profiling driver: run workload 1, 2, 3 or 5 untimed")
     ap.add_argument("--drive-evals", type=int, default=4)
+    ap.add_argument("--drive-precision", type=int, default=0,
+                    help="profiling driver: 0 = FP32 FFT kernels, 1 = tensor-core DFTs (M = 64)")
     args = ap.parse_args()
     if args.drive:
         run_drive(args)
