@@ -160,10 +160,14 @@ mpbp_status mpbp_loss_grad(mpbp_ctx *ctx, const float *rho, const float *u,
                            void *stream);
 
 /* End-to-end variant of mpbp_loss_grad on HOST buffers: copies y (host
- * [D][J][M][M], or NULL to keep the data already set), rho, u, alpha to the
- * device, evaluates all frames, copies loss (1 double), g_rho, g_u and
- * g_alpha (host, NULL to skip) back, and synchronises the stream.  Page-locked
- * host memory makes the copies asynchronous and fast. */
+ * [D][J][M][M], or NULL to keep the data already set; when given it also
+ * becomes the context's data for later calls), rho, u, alpha to the device,
+ * evaluates all frames, returns loss (1 double), g_rho, g_u and g_alpha (host,
+ * NULL to skip), and synchronises the stream.  y is copied in chunks that are
+ * evaluated while later chunks are still in flight.  Page-locked host memory
+ * makes the copies asynchronous and fast; when every requested output is
+ * page-locked the device writes the outputs in place (no separate read-back),
+ * otherwise they are copied back from the workspace. */
 mpbp_status mpbp_loss_grad_host(mpbp_ctx *ctx, const float *y, const float *rho,
                                 const float *u, const float *alpha, double *loss,
                                 float *g_rho, float *g_u, double *g_alpha, void *stream);
