@@ -189,6 +189,22 @@ mpbp_status mpbp_step_init(mpbp_ctx *ctx, const mpbp_step_params *prm,
 mpbp_status mpbp_step(mpbp_ctx *ctx, float *rho, float *u, float *alpha,
                       mpbp_step_state *st, void *stream);
 
+/* Records one mpbp_step(ctx, rho, u, alpha, st) -- object synthesis, fused
+ * frame kernel, gradient assembly with the line-search decision, update --
+ * as a CUDA graph owned by the context (replacing an earlier one), on a
+ * stream of the context's own; nothing runs.  The pointers (dev) are baked
+ * into the graph, and so are the kernels and schedule chosen at capture
+ * (later mpbp_set_precision / mpbp_set_schedule calls need a new capture).
+ * Frame-kernel timing (mpbp_frames_timing) must be off.  Synchronous.
+ * MPBP_ERR_CUDA if capture or instantiation fails. */
+mpbp_status mpbp_step_capture(mpbp_ctx *ctx, float *rho, float *u, float *alpha,
+                              mpbp_step_state *st);
+
+/* Launches the captured step on `stream`: the same work as mpbp_step with
+ * the captured arguments, with one launch from the host instead of four.
+ * MPBP_ERR_INVALID_ARG if no step has been captured. */
+mpbp_status mpbp_step_replay(mpbp_ctx *ctx, void *stream);
+
 /* Loss and gradient of n independent problems (frame sides may differ) in
  * one persistent launch of the fused frame kernel.  Each argument is a host
  * array of n per-problem pointers with the meaning of mpbp_loss_grad

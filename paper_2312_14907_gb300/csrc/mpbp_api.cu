@@ -92,6 +92,9 @@ struct mpbp_ctx {
   bool acc_dirty = false;
   // optional event timing of the fused frame kernel
   bool timing = false;
+  // one optimizer step captured as a CUDA graph (mpbp_step_capture)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t step_exec = nullptr;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
   size_t ev_used = 0;
   std::string last_error;
@@ -418,6 +421,8 @@ void mpbp_destroy(mpbp_ctx* c) {
   if (c->stage) cudaFree(c->stage);
   if (c->bgT) cudaFree(c->bgT);
   if (c->tc_w) cudaFree(c->tc_w);
+  if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
 }
 
@@ -796,6 +801,55 @@ mpbp_status mpbp_step(mpbp_ctx* c, float* rho, float* u, float* alpha, mpbp_step
   sa.D = c->D;
   sa.alpha_from = 1;
   MPBP_CUDA(c, launch_step_update(sa, c->num_sms, s));
+  return MPBP_OK;
+}
+
+mpbp_status mpbp_step_capture(mpbp_ctx* c, float* rho, float* u, float* alpha, mpbp_step_state* st) {
+  if (!c || !rho || !u || !alpha || !st) return fail(c, MPBP_ERR_INVALID_ARG, "null argument");
+  if (!c->has_probe || !c->has_data) return fail(c, MPBP_ERR_NO_DATA, "probe or data not set");
+  if (c->timing) return fail(c, MPBP_ERR_INVALID_ARG, "frame-kernel timing must be off while capturing");
+  if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    c->cap_stream = nullptr;
+    return fail(c, MPBP_ERR_CUDA, "capture stream");
+  }
+  // the graph starts from a clear gradient accumulator, as every step leaves it
+  if (c->acc_dirty) {
+    MPBP_CUDA(c, cudaMemsetAsync(c->acc, 0, sizeof(cf) * c->npix * c->D, c->cap_stream));
+    MPBP_CUDA(c, cudaStreamSynchronize(c->cap_stream));
+    c->acc_dirty = false;
+  }
+  MPBP_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  const mpbp_status r = mpbp_step(c, rho, u, alpha, st, c->cap_stream);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+  c->acc_dirty = false;   // the captured step ends by clearing the accumulator
+  if (r != MPBP_OK || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return r != MPBP_OK ? r : fail(c, MPBP_ERR_CUDA, "stream capture of the step failed");
+  }
+  cudaGraphExec_t x = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&x, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, MPBP_ERR_CUDA, "graph instantiation failed");
+  }
+  if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+  c->step_exec = x;
+  return MPBP_OK;
+}
+
+mpbp_status mpbp_step_replay(mpbp_ctx* c, void* stream) {
+  if (!c) return MPBP_ERR_INVALID_ARG;
+  if (!c->step_exec) return fail(c, MPBP_ERR_INVALID_ARG, "no step captured");
+  cudaStream_t s = S(stream);
+  if (c->acc_dirty) {
+    MPBP_CUDA(c, cudaMemsetAsync(c->acc, 0, sizeof(cf) * c->npix * c->D, s));
+    c->acc_dirty = false;
+  }
+  MPBP_CUDA(c, cudaGraphLaunch(c->step_exec, s));
   return MPBP_OK;
 }
 

@@ -63,7 +63,7 @@ EXPORTS = ["mpbp_status_string", "mpbp_create", "mpbp_destroy", "mpbp_last_error
            "mpbp_step", "mpbp_loss_grad_batched", "mpbp_set_schedule", "mpbp_sync_status",
            "mpbp_frames_timing", "mpbp_frames_timing_read", "mpbp_loss_grad_noalloc",
            "mpbp_set_batch_schedule", "mpbp_autotune", "mpbp_autotune_batched",
-           "mpbp_set_precision"]
+           "mpbp_set_precision", "mpbp_step_capture", "mpbp_step_replay"]
 
 PRECISION_FP32 = 0        # FFTs on the CUDA cores
 PRECISION_TC_SPLIT16 = 1  # dense DFT matrices on the tensor cores, split FP16
@@ -118,6 +118,10 @@ def load(build_if_missing=True):
     lib.mpbp_set_schedule.restype = st
     lib.mpbp_set_precision.argtypes = [V, I32]
     lib.mpbp_set_precision.restype = st
+    lib.mpbp_step_capture.argtypes = [V, V, V, V, V]
+    lib.mpbp_step_capture.restype = st
+    lib.mpbp_step_replay.argtypes = [V, V]
+    lib.mpbp_step_replay.restype = st
     lib.mpbp_set_batch_schedule.argtypes = [V, I32, I32]
     lib.mpbp_set_batch_schedule.restype = st
     lib.mpbp_autotune.argtypes = [V, V, V, V, V, V, V, ctypes.c_char_p, V]
@@ -334,6 +338,17 @@ class Problem:
         self._state(rho, u, alpha)
         self._check(self._lib.mpbp_step(self._h, _p(rho), _p(u), _p(alpha), _p(state), _stream()),
                     "mpbp_step")
+
+    def step_capture(self, rho, u, alpha, state):
+        """Records one step on these tensors as a CUDA graph (mpbp_step_capture)."""
+        self._state(rho, u, alpha)
+        self._check(self._lib.mpbp_step_capture(self._h, _p(rho), _p(u), _p(alpha), _p(state)),
+                    "mpbp_step_capture")
+        self._captured = (rho, u, alpha, state)   # keep the baked-in buffers alive
+
+    def step_replay(self):
+        """Launches the captured step on the current stream (mpbp_step_replay)."""
+        self._check(self._lib.mpbp_step_replay(self._h, _stream()), "mpbp_step_replay")
 
     @staticmethod
     def read_state(state):

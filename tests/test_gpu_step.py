@@ -114,3 +114,38 @@ def test_step_graph_capture_matches_eager():
     for u, v in zip(xe, xg):
         assert rel_l2(v.cpu().numpy(), u.cpu().numpy()) <= 1e-5
     pg.sync_status()
+
+
+def test_native_step_capture_and_replay_match_eager():
+    """mpbp_step_capture / mpbp_step_replay: the context's own graph of one
+    step replays the eager iterations exactly (same decisions, same iterate)."""
+    from paper_2312_14907_gb300 import mpbp
+    spec, scan = custom_spec(128, 64, 5, 16, npeaks=3, offset=-4)
+    case = Case(spec, scan=scan, state="perturbed")
+    pe, xe = _setup(case)
+    ste = pe.step_init(_t0(case), w_rho=1.0, w_u=0.05, w_alpha=0.01)
+    pg, xg = _setup(case)
+    stg = pg.step_init(_t0(case), w_rho=1.0, w_u=0.05, w_alpha=0.01)
+    with pytest.raises(mpbp.MPBPError):
+        pg.step_replay()                      # nothing captured yet
+    pg.frames_timing(True)
+    with pytest.raises(mpbp.MPBPError):
+        pg.step_capture(*xg, stg)             # timing events cannot be captured
+    pg.frames_timing(False)
+    pg.step_capture(*xg, stg)                 # records, runs nothing
+    for _ in range(8):
+        pe.step(*xe, ste)
+        pg.step_replay()
+    torch.cuda.synchronize()
+    a, b = pe.read_state(ste), pg.read_state(stg)
+    assert (a.k, a.n_accept, a.n_reject) == (b.k, b.n_accept, b.n_reject) and a.k == 8
+    assert abs(a.f_last - b.f_last) <= 1e-6 * abs(a.f_last)
+    for u, v in zip(xe, xg):
+        assert rel_l2(v.cpu().numpy(), u.cpu().numpy()) <= 1e-5
+    # an eager evaluation in between leaves the graph usable
+    pg.loss_grad(*xg)
+    pg.step_replay()
+    pe.step(*xe, ste)
+    torch.cuda.synchronize()
+    assert pg.read_state(stg).k == pe.read_state(ste).k == 9
+    pg.sync_status()
