@@ -45,6 +45,12 @@ class StepParams(ctypes.Structure):
                 ("w_alpha", ctypes.c_double)]
 
 
+class AdamParams(ctypes.Structure):
+    _fields_ = [("lr_u", ctypes.c_double), ("lr_chi", ctypes.c_double),
+                ("lr_alpha", ctypes.c_double), ("beta1", ctypes.c_double),
+                ("beta2", ctypes.c_double), ("eps", ctypes.c_double)]
+
+
 class StepState(ctypes.Structure):
     _fields_ = [("f_prev", ctypes.c_double), ("gn2_prev", ctypes.c_double),
                 ("t", ctypes.c_double), ("f_last", ctypes.c_double),
@@ -73,6 +79,20 @@ def _load():
                                     ctypes.POINTER(StepState), dp, dp, dp, dp, dp, dp,
                                     dp, dp, dp, ctypes.c_int]
         lib.oracle_step.restype = None
+        lib.oracle_loss_grad_phases.argtypes = [pp, dp, dp, dp, dp, dp, dp, ip, ctypes.c_int,
+                                                dp, dp, dp, ctypes.c_int]
+        lib.oracle_loss_grad_phases.restype = ctypes.c_double
+        lib.oracle_loss_grad_log.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp, ip, ctypes.c_int,
+                                             dp, dp, dp, ctypes.c_int]
+        lib.oracle_loss_grad_log.restype = ctypes.c_double
+        lib.oracle_adam_update.argtypes = [ctypes.c_long, dp, dp, dp, dp, ctypes.c_long,
+                                           ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double]
+        lib.oracle_adam_update.restype = None
+        lib.oracle_adam_step.argtypes = [pp, dp, dp, dp, ip, ctypes.c_int, dp,
+                                         ctypes.POINTER(AdamParams), ctypes.POINTER(ctypes.c_long),
+                                         dp, dp, dp, dp, dp, dp, dp, dp, dp, ctypes.c_int]
+        lib.oracle_adam_step.restype = ctypes.c_double
         lib.oracle_max_threads.argtypes = []
         lib.oracle_max_threads.restype = ctypes.c_int
         _lib = lib
@@ -100,6 +120,28 @@ def _ptr(a):
 
 def max_threads():
     return _load().oracle_max_threads()
+
+
+def _frames(frames):
+    if frames is None:
+        return None, 0
+    fr = np.ascontiguousarray(frames, dtype=np.int32)
+    return fr, fr.size
+
+
+def _iptr(fr):
+    return None if fr is None else fr.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def adam_update(x, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update of x (float64, in place) with gradient g at step t >= 1;
+    m and v (float64, in place) are the moments (see oracle_adam_update)."""
+    lib = _load()
+    for a in (x, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    g = _d(g)
+    lib.oracle_adam_update(x.size, _ptr(x), _ptr(g), _ptr(m), _ptr(v), int(t), float(lr),
+                           float(beta1), float(beta2), float(eps))
 
 
 def dft2(x, sign=-1):
@@ -182,6 +224,67 @@ class OracleProblem:
 
     def loss(self, rho, u, alpha, probe, y, bg=None, nthreads=0):
         return self.loss_grad(rho, u, alpha, probe, y, bg=bg, nthreads=nthreads)[0]
+
+    def loss_grad_phases(self, rho, phi, alpha, probe, y, bg=None, frames=None, nthreads=0):
+        """Per-peak-phase form: phi [D][n1][n2]; returns (loss, g_rho, g_phi, g_alpha)."""
+        lib = _load()
+        n1, n2 = self.shape
+        rho, phi, alpha, probe, y = _d(rho), _d(phi), _d(alpha), _c(probe), _d(y)
+        bg = None if bg is None else _d(bg)
+        g_rho, g_phi, g_alpha = np.empty((n1, n2)), np.empty((self.npeaks, n1, n2)), np.empty(self.npeaks)
+        fr, nfr = _frames(frames)
+        loss = lib.oracle_loss_grad_phases(ctypes.byref(self.c), _ptr(rho), _ptr(phi), _ptr(alpha),
+                                           _ptr(probe), _ptr(bg), _ptr(y), _iptr(fr), nfr,
+                                           _ptr(g_rho), _ptr(g_phi), _ptr(g_alpha), int(nthreads))
+        return loss, g_rho, g_phi, g_alpha
+
+    def loss_grad_log(self, chi, u, alpha_t, probe, y, mask=None, bg=None, frames=None, nthreads=0):
+        """Eq. 8 variables: rho = mask e^chi, alpha = (1, e^alpha_t[1:]); returns
+        (loss, g_chi, g_u, g_alpha_t)."""
+        lib = _load()
+        n1, n2 = self.shape
+        chi, u, alpha_t, probe, y = _d(chi), _d(u), _d(alpha_t), _c(probe), _d(y)
+        mask = None if mask is None else _d(mask)
+        bg = None if bg is None else _d(bg)
+        g_chi, g_u, g_a = np.empty((n1, n2)), np.empty((self.ncomp, n1, n2)), np.empty(self.npeaks)
+        fr, nfr = _frames(frames)
+        loss = lib.oracle_loss_grad_log(ctypes.byref(self.c), _ptr(chi), _ptr(u), _ptr(alpha_t),
+                                        _ptr(mask), _ptr(probe), _ptr(bg), _ptr(y), _iptr(fr), nfr,
+                                        _ptr(g_chi), _ptr(g_u), _ptr(g_a), int(nthreads))
+        return loss, g_chi, g_u, g_a
+
+
+class OracleAdam:
+    """Alg. 1 without the projector: minibatch Adam in the Eq. 8 variables
+    (see oracle_adam_step).  Holds the moments and the step count."""
+
+    def __init__(self, problem, probe, y, mask=None, bg=None, lr_u=0.01, lr_chi=0.1,
+                 lr_alpha=0.1, beta1=0.9, beta2=0.999, eps=1e-8, nthreads=0):
+        self.p = problem
+        self.probe, self.y = _c(probe), _d(y)
+        self.mask = None if mask is None else _d(mask)
+        self.bg = None if bg is None else _d(bg)
+        self.params = AdamParams(lr_u, lr_chi, lr_alpha, beta1, beta2, eps)
+        n1, n2 = problem.shape
+        self.m_chi, self.v_chi = np.zeros((n1, n2)), np.zeros((n1, n2))
+        self.m_u, self.v_u = np.zeros((problem.ncomp, n1, n2)), np.zeros((problem.ncomp, n1, n2))
+        self.m_a, self.v_a = np.zeros(problem.npeaks), np.zeros(problem.npeaks)
+        self.t = ctypes.c_long(0)
+        self.nthreads = nthreads
+
+    def step(self, frames, chi, u, alpha_t):
+        """Updates chi, u, alpha_t (float64, in place) from the listed frames;
+        returns the minibatch loss before the update."""
+        lib = _load()
+        for a in (chi, u, alpha_t):
+            assert a.dtype == np.float64 and a.flags.c_contiguous
+        fr, nfr = _frames(frames)
+        return lib.oracle_adam_step(ctypes.byref(self.p.c), _ptr(self.probe), _ptr(self.bg),
+                                    _ptr(self.y), _iptr(fr), nfr, _ptr(self.mask),
+                                    ctypes.byref(self.params), ctypes.byref(self.t),
+                                    _ptr(chi), _ptr(u), _ptr(alpha_t), _ptr(self.m_chi),
+                                    _ptr(self.v_chi), _ptr(self.m_u), _ptr(self.v_u),
+                                    _ptr(self.m_a), _ptr(self.v_a), int(self.nthreads))
 
 
 class OracleStepper:

@@ -26,6 +26,12 @@
  *     df/dalpha_m  += Re( conj(g) rho(r) e^{i phi_m(r)} )
  *     df/du_c(r)    = phase_scale * sum_m G_{m,c} df/dphi_m(r)
  *
+ * Also: the per-peak-phase form (O_m = alpha_m rho e^{i phi_m} with D
+ * independent phase maps, the paper's "TS" variables, Sec. 5); the auxiliary
+ * variables of Eq. 8 (rho = mask e^{chi}, alpha_m = e^{alpha_t_m}, alpha_0 = 1)
+ * with the chain rule to them; and the minibatch Adam iteration of Alg. 1
+ * without its projector line (Adam as in Kingma and Ba, arXiv 1412.6980).
+ *
  * Complex arrays are interleaved (re, im) doubles.  Layouts (row-major):
  *   rho [n1][n2], u [C][n1][n2], alpha [D], G [D][C], scan [J][2] (row, col of
  *   the frame's top-left pixel), probe [Dp][M][M] (Dp = D or 1), y / bg / I
@@ -218,27 +224,25 @@ void oracle_forward(const oracle_problem *p, const double *rho, const double *u,
 /* ------------------------------------------------------------------------ */
 
 /* Loss and gradient over the frames listed in `frames` (all D*J frames when
- * frames == NULL), i.e. the minibatch sum of Eq. 11 with the minibatch given.
- * Gradient outputs are overwritten.  frame_loss (nullable) receives each
- * listed frame's own term.  nthreads <= 0 uses the OpenMP default.
- * Returns the loss. */
-double oracle_loss_grad(const oracle_problem *p, const double *rho, const double *u,
-                        const double *alpha, const double *probe, const double *bg,
-                        const double *y, const int *frames, int nframes,
-                        double *g_rho, double *g_u, double *g_alpha,
-                        double *frame_loss, int nthreads)
+ * frames == NULL), i.e. the minibatch sum of Eq. 11 with the minibatch given,
+ * for objects O_m = alpha_m rho E_m with the phase factors E_m = e^{i phi_m}
+ * given ([D][npix] complex).  Outputs (overwritten): g_rho, g_phi [D][npix]
+ * (df/dphi_m), g_alpha.  frame_loss (nullable) receives each listed frame's
+ * own term.  nthreads <= 0 uses the OpenMP default.  Returns the loss. */
+static double loss_grad_core(const oracle_problem *p, const double *rho, const double *E,
+                             const double *alpha, const double *probe, const double *bg,
+                             const double *y, const int *frames, int nframes,
+                             double *g_rho, double *g_phi_out, double *g_alpha,
+                             double *frame_loss, int nthreads)
 {
-    int m = p->m, D = p->npeaks, C = p->ncomp;
+    int m = p->m, D = p->npeaks;
     long npix = (long)p->n1 * p->n2, mm = (long)m * m;
     long nlist = frames ? nframes : (long)D * p->nscan;
     double *O = malloc(sizeof(double) * 2 * D * npix);
-    double *E = malloc(sizeof(double) * 2 * D * npix);   /* e^{i phi_m(r)} */
-    oracle_object_build(p, rho, u, alpha, O);
     for (int mpk = 0; mpk < D; ++mpk)
         for (long r = 0; r < npix; ++r) {
-            double ph = phase_at(p, u, mpk, r);
-            E[2 * (mpk * npix + r)] = cos(ph);
-            E[2 * (mpk * npix + r) + 1] = sin(ph);
+            O[2 * (mpk * npix + r)] = alpha[mpk] * rho[r] * E[2 * (mpk * npix + r)];
+            O[2 * (mpk * npix + r) + 1] = alpha[mpk] * rho[r] * E[2 * (mpk * npix + r) + 1];
         }
 
     int nt = 1;
@@ -319,15 +323,48 @@ double oracle_loss_grad(const oracle_problem *p, const double *rho, const double
 
     double loss = 0.0;
     for (long r = 0; r < npix; ++r) g_rho[r] = 0.0;
-    for (long r = 0; r < (long)C * npix; ++r) g_u[r] = 0.0;
+    for (long r = 0; r < (long)D * npix; ++r) g_phi_out[r] = 0.0;
     for (int mpk = 0; mpk < D; ++mpk) g_alpha[mpk] = 0.0;
-    double *gphi = calloc((size_t)D * npix, sizeof(double));
     for (int t = 0; t < nt; ++t) {
         loss += t_loss[t];
         for (long r = 0; r < npix; ++r) g_rho[r] += t_grho[(size_t)t * npix + r];
-        for (long r = 0; r < (long)D * npix; ++r) gphi[r] += t_gphi[(size_t)t * D * npix + r];
+        for (long r = 0; r < (long)D * npix; ++r) g_phi_out[r] += t_gphi[(size_t)t * D * npix + r];
         for (int mpk = 0; mpk < D; ++mpk) g_alpha[mpk] += t_galpha[(size_t)t * D + mpk];
     }
+    free(t_loss); free(t_grho); free(t_gphi); free(t_galpha);
+    free(O);
+    return loss;
+}
+
+/* e^{i phi} of per-peak phase maps phi [D][npix] */
+static double *phase_factors(long n, const double *phi)
+{
+    double *E = malloc(sizeof(double) * 2 * n);
+    for (long i = 0; i < n; ++i) {
+        E[2 * i] = cos(phi[i]);
+        E[2 * i + 1] = sin(phi[i]);
+    }
+    return E;
+}
+
+/* Eq. 4 and its gradient in the displacement form of Eq. 3: phi_m =
+ * phase_scale * G_m . u, and df/du_c = phase_scale * sum_m G_{m,c} df/dphi_m.
+ * Arguments as loss_grad_core, with u [C][n1][n2] and g_u [C][n1][n2]. */
+double oracle_loss_grad(const oracle_problem *p, const double *rho, const double *u,
+                        const double *alpha, const double *probe, const double *bg,
+                        const double *y, const int *frames, int nframes,
+                        double *g_rho, double *g_u, double *g_alpha,
+                        double *frame_loss, int nthreads)
+{
+    int D = p->npeaks, C = p->ncomp;
+    long npix = (long)p->n1 * p->n2;
+    double *phi = malloc(sizeof(double) * D * npix);
+    for (int mpk = 0; mpk < D; ++mpk)
+        for (long r = 0; r < npix; ++r) phi[mpk * npix + r] = phase_at(p, u, mpk, r);
+    double *E = phase_factors((long)D * npix, phi);
+    double *gphi = malloc(sizeof(double) * D * npix);
+    double loss = loss_grad_core(p, rho, E, alpha, probe, bg, y, frames, nframes, g_rho, gphi,
+                                 g_alpha, frame_loss, nthreads);
     /* d phi_m / d u_c = phase_scale * G_{m,c} */
     for (int c = 0; c < C; ++c)
         for (long r = 0; r < npix; ++r) {
@@ -336,9 +373,104 @@ double oracle_loss_grad(const oracle_problem *p, const double *rho, const double
                 s += p->G[mpk * C + c] * gphi[mpk * npix + r];
             g_u[c * npix + r] = p->phase_scale * s;
         }
-    free(gphi); free(t_loss); free(t_grho); free(t_gphi); free(t_galpha);
-    free(O); free(E);
+    free(phi); free(E); free(gphi);
     return loss;
+}
+
+/* The per-peak-phase form (the paper's two-step "TS" reconstruction, Sec. 5):
+ * O_m = alpha_m rho e^{i phi_m} with D independent phase maps phi [D][n1][n2]
+ * in place of the displacement field; g_phi [D][n1][n2] = df/dphi_m. */
+double oracle_loss_grad_phases(const oracle_problem *p, const double *rho, const double *phi,
+                               const double *alpha, const double *probe, const double *bg,
+                               const double *y, const int *frames, int nframes,
+                               double *g_rho, double *g_phi, double *g_alpha, int nthreads)
+{
+    long n = (long)p->npeaks * p->n1 * p->n2;
+    double *E = phase_factors(n, phi);
+    double loss = loss_grad_core(p, rho, E, alpha, probe, bg, y, frames, nframes, g_rho, g_phi,
+                                 g_alpha, NULL, nthreads);
+    free(E);
+    return loss;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Alg. 1: the auxiliary variables of Eq. 8 and the Adam update             */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. 4 and its gradient in the auxiliary variables of Eq. 8: rho = mask *
+ * e^{chi} (mask [n1][n2] nullable = all ones: the support constraint),
+ * alpha_0 = 1 (the reference peak) and alpha_m = e^{alpha_t[m]} for m >= 1.
+ * g_chi = rho df/drho, g_alpha_t[m] = alpha_m df/dalpha_m (0 for m = 0),
+ * g_u = df/du.  Returns the loss over the listed frames. */
+double oracle_loss_grad_log(const oracle_problem *p, const double *chi, const double *u,
+                            const double *alpha_t, const double *mask, const double *probe,
+                            const double *bg, const double *y, const int *frames, int nframes,
+                            double *g_chi, double *g_u, double *g_alpha_t, int nthreads)
+{
+    int D = p->npeaks;
+    long npix = (long)p->n1 * p->n2;
+    double *rho = malloc(sizeof(double) * npix);
+    double *alpha = malloc(sizeof(double) * D);
+    double *grho = malloc(sizeof(double) * npix);
+    double *galpha = malloc(sizeof(double) * D);
+    for (long r = 0; r < npix; ++r) rho[r] = (mask ? mask[r] : 1.0) * exp(chi[r]);
+    alpha[0] = 1.0;
+    for (int mpk = 1; mpk < D; ++mpk) alpha[mpk] = exp(alpha_t[mpk]);
+    double loss = oracle_loss_grad(p, rho, u, alpha, probe, bg, y, frames, nframes, grho, g_u,
+                                   galpha, NULL, nthreads);
+    for (long r = 0; r < npix; ++r) g_chi[r] = rho[r] * grho[r];
+    g_alpha_t[0] = 0.0;
+    for (int mpk = 1; mpk < D; ++mpk) g_alpha_t[mpk] = alpha[mpk] * galpha[mpk];
+    free(rho); free(alpha); free(grho); free(galpha);
+    return loss;
+}
+
+/* Adam (Kingma and Ba, arXiv 1412.6980, Algorithm 1) on n variables x with
+ * gradient g at step t >= 1 (the step count including this one):
+ *   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
+ *   x -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). */
+void oracle_adam_update(long n, double *x, const double *g, double *mo, double *ve, long t,
+                        double lr, double b1, double b2, double eps)
+{
+    double c1 = 1.0 - pow(b1, (double)t), c2 = 1.0 - pow(b2, (double)t);
+    for (long i = 0; i < n; ++i) {
+        mo[i] = b1 * mo[i] + (1.0 - b1) * g[i];
+        ve[i] = b2 * ve[i] + (1.0 - b2) * g[i] * g[i];
+        x[i] -= lr * (mo[i] / c1) / (sqrt(ve[i] / c2) + eps);
+    }
+}
+
+typedef struct {
+    double lr_u, lr_chi, lr_alpha;   /* Adam step sizes of u, chi, alpha_t */
+    double beta1, beta2, eps;
+} oracle_adam_params;
+
+/* One minibatch iteration of Alg. 1 without the projector (its line 5): the
+ * gradient of Eq. 4 over the listed frames in the variables of Eq. 8, then
+ * Adam on u, chi and alpha_t (alpha_t[0] is not a variable: its gradient is 0,
+ * so it never moves).  *t counts the iterations (incremented here); the
+ * moments [m, v] of each block are caller-owned and start at 0.  Returns the
+ * minibatch loss at the iterate before the update. */
+double oracle_adam_step(const oracle_problem *p, const double *probe, const double *bg,
+                        const double *y, const int *frames, int nframes, const double *mask,
+                        const oracle_adam_params *prm, long *t,
+                        double *chi, double *u, double *alpha_t,
+                        double *m_chi, double *v_chi, double *m_u, double *v_u,
+                        double *m_a, double *v_a, int nthreads)
+{
+    int D = p->npeaks, C = p->ncomp;
+    long npix = (long)p->n1 * p->n2;
+    double *gchi = malloc(sizeof(double) * npix);
+    double *gu = malloc(sizeof(double) * C * npix);
+    double *ga = malloc(sizeof(double) * D);
+    double f = oracle_loss_grad_log(p, chi, u, alpha_t, mask, probe, bg, y, frames, nframes,
+                                    gchi, gu, ga, nthreads);
+    *t += 1;
+    oracle_adam_update(npix, chi, gchi, m_chi, v_chi, *t, prm->lr_chi, prm->beta1, prm->beta2, prm->eps);
+    oracle_adam_update((long)C * npix, u, gu, m_u, v_u, *t, prm->lr_u, prm->beta1, prm->beta2, prm->eps);
+    oracle_adam_update(D, alpha_t, ga, m_a, v_a, *t, prm->lr_alpha, prm->beta1, prm->beta2, prm->eps);
+    free(gchi); free(gu); free(ga);
+    return f;
 }
 
 /* ------------------------------------------------------------------------ */

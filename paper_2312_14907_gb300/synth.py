@@ -270,3 +270,20 @@ def perturbed_state(spec, rng, scale=0.05):
     alpha = alpha_truth(spec) * (1.0 + scale * rng.standard_normal(spec.npeaks))
     alpha[0] = 1.0
     return rho, u, alpha
+
+
+def epoch_order(nframes, seed):
+    """A seeded shuffle of all D*J frame numbers (Alg. 1, line 1): the random
+    order of one epoch of minibatches, drawn here and passed to both the
+    GPU path and the oracle as an input."""
+    return np.random.default_rng(seed).permutation(nframes).astype(np.int32)
+
+
+def support_mask(spec, margin=5):
+    """The support constraint of the reconstruction: 1 on the object's
+    square support grown by `margin` pixels on every side (the paper grows the
+    film support by 5 pixels), 0 elsewhere (float32)."""
+    _, (a0, a1, side) = _support_mask(spec)
+    mask = np.zeros((spec.n1, spec.n2), np.float32)
+    mask[max(a0 - margin, 0):a0 + side + margin, max(a1 - margin, 0):a1 + side + margin] = 1.0
+    return mask
