@@ -205,6 +205,65 @@ mpbp_status mpbp_step_capture(mpbp_ctx *ctx, float *rho, float *u, float *alpha,
  * MPBP_ERR_INVALID_ARG if no step has been captured. */
 mpbp_status mpbp_step_replay(mpbp_ctx *ctx, void *stream);
 
+/* ------------------------------------------------------------------------
+ * The paper's own optimizer, Alg. 1 without its projector line (the
+ * "concurrent-wrapped" reconstruction): minibatches of frames from a shuffled
+ * epoch, the auxiliary variables of Eq. 8 -- rho = mask * e^{chi} (mask: the
+ * support constraint), alpha_0 = 1, alpha_m = e^{alpha_t[m]} -- and Adam
+ * (Kingma and Ba) with step sizes per block (the paper: 0.01 for u, 0.1 for
+ * chi and alpha_t).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  double lr_u, lr_chi, lr_alpha;   /* Adam step sizes of u, chi, alpha_t     */
+  double beta1, beta2, eps;        /* moment decay rates and denominator term */
+} mpbp_adam_params;
+
+typedef struct {
+  double lr_u, lr_chi, lr_alpha, beta1, beta2, eps;   /* copied from the params */
+  double f_last;         /* minibatch loss of the last step, before its update */
+  double bc1, bc2;       /* 1 - beta1^t, 1 - beta2^t of the last step           */
+  int64_t t;             /* steps taken                                         */
+} mpbp_adam_state;
+
+/* Initialises Adam: st (dev) from prm (host), t = 0, and the context's moment
+ * buffers (allocated on the first call, 4 * (2 (1 + C) n1 n2) + 16 D bytes)
+ * to zero.  Synchronous on the first call. */
+mpbp_status mpbp_adam_init(mpbp_ctx *ctx, const mpbp_adam_params *prm, mpbp_adam_state *st,
+                           void *stream);
+
+/* One minibatch iteration: the loss of Eq. 4 and its gradient over `frames`
+ * (dev int32 [nframes]; NULL = all frames) at rho = mask * e^{chi}, u,
+ * alpha = (1, e^{alpha_t[1..]}); the chain rule to chi (rho df/drho) and
+ * alpha_t (alpha df/dalpha); Adam on chi [n1][n2], u [C][n1][n2] and
+ * alpha_t[1..D-1] (dev, updated in place; alpha_t[0] is never read or
+ * moved).  mask (dev [n1][n2], or NULL for none) must stay fixed between
+ * steps.  st->f_last receives the minibatch loss.  Needs probe, data and
+ * mpbp_adam_init; the frame order is the caller's (e.g. a seeded shuffle per
+ * epoch, Alg. 1 line 1). */
+mpbp_status mpbp_adam_step(mpbp_ctx *ctx, const int32_t *frames, int32_t nframes, float *chi,
+                           float *u, float *alpha_t, const float *mask, mpbp_adam_state *st,
+                           void *stream);
+
+/* Copies the Adam moments out of (get) or into (set) the context, for
+ * checkpoint and resume: m_chi, v_chi [n1][n2], m_u, v_u [C][n1][n2] floats,
+ * m_alpha, v_alpha [D] doubles (dev).  Together with st and the variables they
+ * are the whole optimizer state.  Needs mpbp_adam_init. */
+mpbp_status mpbp_adam_get_state(mpbp_ctx *ctx, float *m_chi, float *v_chi, float *m_u,
+                                float *v_u, double *m_alpha, double *v_alpha, void *stream);
+mpbp_status mpbp_adam_set_state(mpbp_ctx *ctx, const float *m_chi, const float *v_chi,
+                                const float *m_u, const float *v_u, const double *m_alpha,
+                                const double *v_alpha, void *stream);
+
+/* The per-peak-phase form of Eq. 3 (the variables of the paper's two-step
+ * reconstruction, Sec. 5): objects O_m = alpha_m rho e^{i phi_m} from D
+ * independent phase maps phi (dev [D][n1][n2]) instead of the displacement
+ * field.  Loss and gradient as mpbp_loss_grad, with g_phi (dev [D][n1][n2]) =
+ * df/dphi_m in place of g_u. */
+mpbp_status mpbp_loss_grad_phases(mpbp_ctx *ctx, const float *rho, const float *phi,
+                                  const float *alpha, const int32_t *frames, int32_t nframes,
+                                  double *loss, float *g_rho, float *g_phi, double *g_alpha,
+                                  void *stream);
+
 /* Loss and gradient of n independent problems (frame sides may differ) in
  * one persistent launch of the fused frame kernel.  Each argument is a host
  * array of n per-problem pointers with the meaning of mpbp_loss_grad

@@ -23,6 +23,30 @@ struct StepArgs {
   int alpha_from;
 };
 
+// Alg. 1 (Adam in the auxiliary variables of Eq. 8), mpbp_alg1.cu
+struct AdamArgs {
+  float* chi;           // [npix] log density (updated)
+  float* u;             // [C][npix] (updated)
+  float* alpha_t;       // [D] log peak scalings, entry 0 unused (updated)
+  const float* mask;    // [npix] support, or nullptr
+  float* rho_x;         // [npix] mask * e^chi (written by prep)
+  float* alpha_x;       // [D] (1, e^alpha_t[1..]) (written by prep)
+  const float* g_rho;   // df/drho, df/du, df/dalpha of the minibatch
+  const float* g_u;
+  const double* g_alpha;
+  float* m_chi;         // Adam moments
+  float* v_chi;
+  float* m_u;
+  float* v_u;
+  double* m_a;
+  double* v_a;
+  mpbp_adam_state* st;  // parameters, step count, bias corrections
+  long long npix;
+  int C, D;
+};
+cudaError_t launch_adam_prep(const AdamArgs& a, int num_sms, cudaStream_t s);
+cudaError_t launch_adam_update(const AdamArgs& a, int num_sms, cudaStream_t s);
+
 cudaError_t launch_object_build(const ObjectArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_frame_transpose(const float* in, float* out, long long nframes, int m,
                                    bool take_sqrt, cudaStream_t s);

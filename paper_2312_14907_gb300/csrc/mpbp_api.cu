@@ -92,6 +92,11 @@ struct mpbp_ctx {
   bool acc_dirty = false;
   // optional event timing of the fused frame kernel
   bool timing = false;
+  // Alg. 1: Adam moments and the materialised rho, alpha (mpbp_adam_init)
+  void* adam_buf = nullptr;
+  float *m_chi = nullptr, *v_chi = nullptr, *m_u = nullptr, *v_u = nullptr;
+  double *m_a = nullptr, *v_a = nullptr;
+  float *rho_x = nullptr, *alpha_x = nullptr;
   // one optimizer step captured as a CUDA graph (mpbp_step_capture)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t step_exec = nullptr;
@@ -198,10 +203,12 @@ FrameArgs frame_args(mpbp_ctx* c, const int* frames, int nframes) {
 }
 
 mpbp_status enqueue_object_build(mpbp_ctx* c, const float* rho, const float* u,
-                                 const float* alpha, cf* out, cudaStream_t s) {
+                                 const float* alpha, cf* out, cudaStream_t s,
+                                 const float* phi = nullptr) {
   ObjectArgs oa{};
   oa.rho = rho;
   oa.u = u;
+  oa.phi = phi;
   oa.alpha = alpha;
   oa.O = out;
   oa.npix = c->npix;
@@ -217,12 +224,13 @@ mpbp_status enqueue_object_build(mpbp_ctx* c, const float* rho, const float* u,
 mpbp_status enqueue_loss_grad(mpbp_ctx* c, const float* rho, const float* u, const float* alpha,
                               const int32_t* frames, int32_t nframes, double* loss,
                               float* g_rho, float* g_u, double* g_alpha,
-                              mpbp_step_state* st, cudaStream_t s) {
+                              mpbp_step_state* st, cudaStream_t s,
+                              const float* phi = nullptr, float* g_phi = nullptr) {
   if (c->acc_dirty) {
     MPBP_CUDA(c, cudaMemsetAsync(c->acc, 0, sizeof(cf) * c->npix * c->D, s));
     c->acc_dirty = false;
   }
-  mpbp_status r = enqueue_object_build(c, rho, u, alpha, c->O, s);
+  mpbp_status r = enqueue_object_build(c, rho, u, alpha, c->O, s, phi);
   if (r != MPBP_OK) return r;
   const int nf = frames ? nframes : (int)c->nframes;
   FrameArgs fa = frame_args(c, frames, nf);
@@ -250,6 +258,8 @@ mpbp_status enqueue_loss_grad(mpbp_ctx* c, const float* rho, const float* u, con
   fi.acc = c->acc;
   fi.g_rho = g_rho;
   fi.g_u = g_u;
+  fi.phi = phi;
+  fi.g_phi = g_phi;
   fi.part = c->part;
   fi.npix = c->npix;
   fi.D = c->D;
@@ -423,6 +433,7 @@ void mpbp_destroy(mpbp_ctx* c) {
   if (c->tc_w) cudaFree(c->tc_w);
   if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->adam_buf) cudaFree(c->adam_buf);
   delete c;
 }
 
@@ -802,6 +813,134 @@ mpbp_status mpbp_step(mpbp_ctx* c, float* rho, float* u, float* alpha, mpbp_step
   sa.alpha_from = 1;
   MPBP_CUDA(c, launch_step_update(sa, c->num_sms, s));
   return MPBP_OK;
+}
+
+mpbp_status mpbp_adam_init(mpbp_ctx* c, const mpbp_adam_params* prm, mpbp_adam_state* st,
+                           void* stream) {
+  if (!c || !prm || !st) return fail(c, MPBP_ERR_INVALID_ARG, "null argument");
+  if (!(prm->lr_u >= 0) || !(prm->lr_chi >= 0) || !(prm->lr_alpha >= 0) || !(prm->beta1 >= 0 && prm->beta1 < 1) ||
+      !(prm->beta2 >= 0 && prm->beta2 < 1) || !(prm->eps >= 0))
+    return fail(c, MPBP_ERR_INVALID_ARG, "Adam parameters out of range");
+  cudaStream_t s = S(stream);
+  const long long np = c->npix, nu = c->npix * c->C;
+  if (!c->adam_buf) {
+    Carver cv;
+    const size_t o_mc = cv.take<float>(np), o_vc = cv.take<float>(np), o_mu = cv.take<float>(nu),
+                 o_vu = cv.take<float>(nu), o_ma = cv.take<double>(c->D), o_va = cv.take<double>(c->D),
+                 o_rx = cv.take<float>(np), o_ax = cv.take<float>(c->D);
+    void* b = nullptr;
+    MPBP_CUDA(c, cudaStreamSynchronize(s));
+    if (cudaMalloc(&b, align_up(cv.off, 256)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, MPBP_ERR_OOM, "Adam moment buffers");
+    }
+    c->adam_buf = b;
+    char* p = static_cast<char*>(b);
+    c->m_chi = reinterpret_cast<float*>(p + o_mc);
+    c->v_chi = reinterpret_cast<float*>(p + o_vc);
+    c->m_u = reinterpret_cast<float*>(p + o_mu);
+    c->v_u = reinterpret_cast<float*>(p + o_vu);
+    c->m_a = reinterpret_cast<double*>(p + o_ma);
+    c->v_a = reinterpret_cast<double*>(p + o_va);
+    c->rho_x = reinterpret_cast<float*>(p + o_rx);
+    c->alpha_x = reinterpret_cast<float*>(p + o_ax);
+  }
+  MPBP_CUDA(c, cudaMemsetAsync(c->m_chi, 0, sizeof(float) * np, s));
+  MPBP_CUDA(c, cudaMemsetAsync(c->v_chi, 0, sizeof(float) * np, s));
+  MPBP_CUDA(c, cudaMemsetAsync(c->m_u, 0, sizeof(float) * nu, s));
+  MPBP_CUDA(c, cudaMemsetAsync(c->v_u, 0, sizeof(float) * nu, s));
+  MPBP_CUDA(c, cudaMemsetAsync(c->m_a, 0, sizeof(double) * c->D, s));
+  MPBP_CUDA(c, cudaMemsetAsync(c->v_a, 0, sizeof(double) * c->D, s));
+  mpbp_adam_state h{};
+  h.lr_u = prm->lr_u;
+  h.lr_chi = prm->lr_chi;
+  h.lr_alpha = prm->lr_alpha;
+  h.beta1 = prm->beta1;
+  h.beta2 = prm->beta2;
+  h.eps = prm->eps;
+  h.bc1 = h.bc2 = 1.0;
+  MPBP_CUDA(c, cudaMemcpyAsync(st, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+  MPBP_CUDA(c, cudaStreamSynchronize(s));
+  return MPBP_OK;
+}
+
+mpbp_status mpbp_adam_step(mpbp_ctx* c, const int32_t* frames, int32_t nframes, float* chi, float* u,
+                           float* alpha_t, const float* mask, mpbp_adam_state* st, void* stream) {
+  if (!c || !chi || !u || !alpha_t || !st) return fail(c, MPBP_ERR_INVALID_ARG, "null argument");
+  if (frames && nframes < 0) return fail(c, MPBP_ERR_INVALID_ARG, "nframes < 0");
+  if (!c->has_probe || !c->has_data) return fail(c, MPBP_ERR_NO_DATA, "probe or data not set");
+  if (!c->adam_buf) return fail(c, MPBP_ERR_NO_DATA, "mpbp_adam_init first");
+  cudaStream_t s = S(stream);
+  AdamArgs a{};
+  a.chi = chi;
+  a.u = u;
+  a.alpha_t = alpha_t;
+  a.mask = mask;
+  a.rho_x = c->rho_x;
+  a.alpha_x = c->alpha_x;
+  a.g_rho = c->g_rho_ws;
+  a.g_u = c->g_u_ws;
+  a.g_alpha = c->g_alpha_ws;
+  a.m_chi = c->m_chi;
+  a.v_chi = c->v_chi;
+  a.m_u = c->m_u;
+  a.v_u = c->v_u;
+  a.m_a = c->m_a;
+  a.v_a = c->v_a;
+  a.st = st;
+  a.npix = c->npix;
+  a.C = c->C;
+  a.D = c->D;
+  MPBP_CUDA(c, launch_adam_prep(a, c->num_sms, s));
+  mpbp_status r = enqueue_loss_grad(c, c->rho_x, u, c->alpha_x, frames, frames ? nframes : 0, &st->f_last,
+                                    c->g_rho_ws, c->g_u_ws, nullptr, nullptr, s);
+  if (r != MPBP_OK) return r;
+  MPBP_CUDA(c, launch_adam_update(a, c->num_sms, s));
+  return MPBP_OK;
+}
+
+mpbp_status mpbp_adam_get_state(mpbp_ctx* c, float* m_chi, float* v_chi, float* m_u, float* v_u,
+                                double* m_alpha, double* v_alpha, void* stream) {
+  if (!c || !m_chi || !v_chi || !m_u || !v_u || !m_alpha || !v_alpha)
+    return fail(c, MPBP_ERR_INVALID_ARG, "null argument");
+  if (!c->adam_buf) return fail(c, MPBP_ERR_NO_DATA, "mpbp_adam_init first");
+  cudaStream_t s = S(stream);
+  const long long np = c->npix, nu = c->npix * c->C;
+  MPBP_CUDA(c, cudaMemcpyAsync(m_chi, c->m_chi, sizeof(float) * np, cudaMemcpyDeviceToDevice, s));
+  MPBP_CUDA(c, cudaMemcpyAsync(v_chi, c->v_chi, sizeof(float) * np, cudaMemcpyDeviceToDevice, s));
+  MPBP_CUDA(c, cudaMemcpyAsync(m_u, c->m_u, sizeof(float) * nu, cudaMemcpyDeviceToDevice, s));
+  MPBP_CUDA(c, cudaMemcpyAsync(v_u, c->v_u, sizeof(float) * nu, cudaMemcpyDeviceToDevice, s));
+  MPBP_CUDA(c, cudaMemcpyAsync(m_alpha, c->m_a, sizeof(double) * c->D, cudaMemcpyDeviceToDevice, s));
+  MPBP_CUDA(c, cudaMemcpyAsync(v_alpha, c->v_a, sizeof(double) * c->D, cudaMemcpyDeviceToDevice, s));
+  return MPBP_OK;
+}
+
+mpbp_status mpbp_adam_set_state(mpbp_ctx* c, const float* m_chi, const float* v_chi, const float* m_u,
+                                const float* v_u, const double* m_alpha, const double* v_alpha,
+                                void* stream) {
+  if (!c || !m_chi || !v_chi || !m_u || !v_u || !m_alpha || !v_alpha)
+    return fail(c, MPBP_ERR_INVALID_ARG, "null argument");
+  if (!c->adam_buf) return fail(c, MPBP_ERR_NO_DATA, "mpbp_adam_init first");
+  cudaStream_t s = S(stream);
+  const long long np = c->npix, nu = c->npix * c->C;
+  MPBP_CUDA(c, cudaMemcpyAsync(c->m_chi, m_chi, sizeof(float) * np, cudaMemcpyDeviceToDevice, s));
+  MPBP_CUDA(c, cudaMemcpyAsync(c->v_chi, v_chi, sizeof(float) * np, cudaMemcpyDeviceToDevice, s));
+  MPBP_CUDA(c, cudaMemcpyAsync(c->m_u, m_u, sizeof(float) * nu, cudaMemcpyDeviceToDevice, s));
+  MPBP_CUDA(c, cudaMemcpyAsync(c->v_u, v_u, sizeof(float) * nu, cudaMemcpyDeviceToDevice, s));
+  MPBP_CUDA(c, cudaMemcpyAsync(c->m_a, m_alpha, sizeof(double) * c->D, cudaMemcpyDeviceToDevice, s));
+  MPBP_CUDA(c, cudaMemcpyAsync(c->v_a, v_alpha, sizeof(double) * c->D, cudaMemcpyDeviceToDevice, s));
+  return MPBP_OK;
+}
+
+mpbp_status mpbp_loss_grad_phases(mpbp_ctx* c, const float* rho, const float* phi, const float* alpha,
+                                  const int32_t* frames, int32_t nframes, double* loss, float* g_rho,
+                                  float* g_phi, double* g_alpha, void* stream) {
+  if (!c || !rho || !phi || !alpha || !loss || !g_rho || !g_phi)
+    return fail(c, MPBP_ERR_INVALID_ARG, "null argument");
+  if (frames && nframes < 0) return fail(c, MPBP_ERR_INVALID_ARG, "nframes < 0");
+  if (!c->has_probe || !c->has_data) return fail(c, MPBP_ERR_NO_DATA, "probe or data not set");
+  return enqueue_loss_grad(c, rho, nullptr, alpha, frames, frames ? nframes : 0, loss, g_rho, nullptr,
+                           g_alpha, nullptr, S(stream), phi, g_phi);
 }
 
 mpbp_status mpbp_step_capture(mpbp_ctx* c, float* rho, float* u, float* alpha, mpbp_step_state* st) {

@@ -10,21 +10,28 @@ namespace mpbp {
 // ----------------------------------------------------------------------------
 // A1: objects
 // ----------------------------------------------------------------------------
+// PHI: the phases phi_m are given per peak (the per-peak-phase variables of
+// the paper's two-step reconstruction) instead of derived from u
+template <bool PHI>
 __global__ void object_build_kernel(ObjectArgs a) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < a.npix; p += stride) {
     const float r = a.rho[p];
     float uc[kMaxComp];
 #pragma unroll
-    for (int c = 0; c < kMaxComp; ++c) uc[c] = c < a.C ? a.u[c * a.npix + p] : 0.f;
+    for (int c = 0; c < kMaxComp; ++c) uc[c] = !PHI && c < a.C ? a.u[c * a.npix + p] : 0.f;
 #pragma unroll
     for (int m = 0; m < kMaxPeaks; ++m) {
       if (m < a.D) {
-        float arg = 0.f;
-#pragma unroll
-        for (int c = 0; c < kMaxComp; ++c) arg = fmaf(a.pc.kpi[m][c], uc[c], arg);
         float sn, cs;
-        sincospif(arg, &sn, &cs);   // exp(i phi), phi = pi * arg
+        if constexpr (PHI) {
+          sincosf(a.phi[m * a.npix + p], &sn, &cs);
+        } else {
+          float arg = 0.f;
+#pragma unroll
+          for (int c = 0; c < kMaxComp; ++c) arg = fmaf(a.pc.kpi[m][c], uc[c], arg);
+          sincospif(arg, &sn, &cs);   // exp(i phi), phi = pi * arg
+        }
         const float amp = a.alpha[m] * r;
         reinterpret_cast<float2*>(a.O)[m * a.npix + p] = make_float2(amp * cs, amp * sn);
       }
@@ -125,6 +132,7 @@ __device__ void final_reduce(const ReduceArgs& a) {
 constexpr int kFinishThreads = 256;
 constexpr int kFinishPixelsPerThread = 1;   // latency-bound: many warps, few pixels each
 
+template <bool PHI>
 __global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a, ReduceArgs ra) {
   constexpr int NW = kFinishThreads / 32;
   constexpr int NQ = kMaxPeaks + 3;
@@ -140,17 +148,21 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a, Re
     const float r = a.rho[p];
     float uc[kMaxComp];
 #pragma unroll
-    for (int c = 0; c < kMaxComp; ++c) uc[c] = c < a.C ? a.u[c * a.npix + p] : 0.f;
-    float gr = 0.f;
+    for (int c = 0; c < kMaxComp; ++c) uc[c] = !PHI && c < a.C ? a.u[c * a.npix + p] : 0.f;
+    float gr = 0.f, gphi2 = 0.f;
     float gu[kMaxComp] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int m = 0; m < kMaxPeaks; ++m) {
       if (m < a.D) {
-        float arg = 0.f;
-#pragma unroll
-        for (int c = 0; c < kMaxComp; ++c) arg = fmaf(a.pc.kpi[m][c], uc[c], arg);
         float sn, cs;
-        sincospif(arg, &sn, &cs);
+        if constexpr (PHI) {
+          sincosf(a.phi[m * a.npix + p], &sn, &cs);
+        } else {
+          float arg = 0.f;
+#pragma unroll
+          for (int c = 0; c < kMaxComp; ++c) arg = fmaf(a.pc.kpi[m][c], uc[c], arg);
+          sincospif(arg, &sn, &cs);
+        }
         const float2 A = acc[m * a.npix + p];
         acc[m * a.npix + p] = make_float2(0.f, 0.f);
         const float Tr = fmaf(cs, A.x, -sn * A.y);
@@ -158,18 +170,25 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a, Re
         const float am = a.alpha[m];
         gr = fmaf(am, Tr, gr);
         const float dphi = -am * r * Ti;
+        if constexpr (PHI) {
+          a.g_phi[m * a.npix + p] = dphi;
+          gphi2 = fmaf(dphi, dphi, gphi2);
+        } else {
 #pragma unroll
-        for (int c = 0; c < kMaxComp; ++c) gu[c] = fmaf(a.pc.kps[m][c], dphi, gu[c]);
+          for (int c = 0; c < kMaxComp; ++c) gu[c] = fmaf(a.pc.kps[m][c], dphi, gu[c]);
+        }
         ap[m] = fmaf(r, Tr, ap[m]);
       }
     }
     a.g_rho[p] = gr;
-    float su = 0.f;
+    float su = gphi2;   // |g_phi|^2 in the phase form, |g_u|^2 otherwise
+    if constexpr (!PHI) {
 #pragma unroll
-    for (int c = 0; c < kMaxComp; ++c) {
-      if (c < a.C) {
-        a.g_u[c * a.npix + p] = gu[c];
-        su = fmaf(gu[c], gu[c], su);
+      for (int c = 0; c < kMaxComp; ++c) {
+        if (c < a.C) {
+          a.g_u[c * a.npix + p] = gu[c];
+          su = fmaf(gu[c], gu[c], su);
+        }
       }
     }
     n_rho = fmaf(gr, gr, n_rho);
@@ -266,7 +285,8 @@ static int grid_for(long long n, int threads, int cap) {
 }
 
 cudaError_t launch_object_build(const ObjectArgs& a, int num_sms, cudaStream_t s) {
-  object_build_kernel<<<grid_for(a.npix, 256, num_sms * 8), 256, 0, s>>>(a);
+  if (a.phi) object_build_kernel<true><<<grid_for(a.npix, 256, num_sms * 8), 256, 0, s>>>(a);
+  else object_build_kernel<false><<<grid_for(a.npix, 256, num_sms * 8), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -288,7 +308,8 @@ int finish_grid(long long npix, int num_sms) {
 }
 
 cudaError_t launch_finish(const FinishArgs& a, const ReduceArgs& r, int grid, cudaStream_t s) {
-  finish_kernel<<<grid, kFinishThreads, 0, s>>>(a, r);
+  if (a.phi) finish_kernel<true><<<grid, kFinishThreads, 0, s>>>(a, r);
+  else finish_kernel<false><<<grid, kFinishThreads, 0, s>>>(a, r);
   return cudaGetLastError();
 }
 

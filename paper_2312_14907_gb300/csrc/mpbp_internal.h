@@ -53,6 +53,7 @@ struct PhaseCoef {
 struct ObjectArgs {
   const float* rho;
   const float* u;
+  const float* phi;     // per-peak phases [D][npix] in place of u (or nullptr)
   const float* alpha;
   cf* O;
   long long npix;
@@ -64,6 +65,8 @@ struct ObjectArgs {
 struct FinishArgs {
   const float* rho;
   const float* u;
+  const float* phi;     // per-peak phases [D][npix] in place of u (or nullptr):
+  float* g_phi;         // then df/dphi_m [D][npix] is written in place of g_u
   const float* alpha;
   cf* acc;              // read, then cleared for the next evaluation
   float* g_rho;

@@ -40,6 +40,20 @@ class StepParams(ctypes.Structure):
                 ("w_u", ctypes.c_double), ("w_alpha", ctypes.c_double)]
 
 
+class AdamParams(ctypes.Structure):
+    _fields_ = [("lr_u", ctypes.c_double), ("lr_chi", ctypes.c_double),
+                ("lr_alpha", ctypes.c_double), ("beta1", ctypes.c_double),
+                ("beta2", ctypes.c_double), ("eps", ctypes.c_double)]
+
+
+class AdamState(ctypes.Structure):
+    _fields_ = [("lr_u", ctypes.c_double), ("lr_chi", ctypes.c_double),
+                ("lr_alpha", ctypes.c_double), ("beta1", ctypes.c_double),
+                ("beta2", ctypes.c_double), ("eps", ctypes.c_double),
+                ("f_last", ctypes.c_double), ("bc1", ctypes.c_double),
+                ("bc2", ctypes.c_double), ("t", ctypes.c_int64)]
+
+
 class StepState(ctypes.Structure):
     _fields_ = [("f_prev", ctypes.c_double), ("gn2_prev", ctypes.c_double),
                 ("t", ctypes.c_double), ("f_last", ctypes.c_double), ("k", ctypes.c_int32),
@@ -63,7 +77,9 @@ EXPORTS = ["mpbp_status_string", "mpbp_create", "mpbp_destroy", "mpbp_last_error
            "mpbp_step", "mpbp_loss_grad_batched", "mpbp_set_schedule", "mpbp_sync_status",
            "mpbp_frames_timing", "mpbp_frames_timing_read", "mpbp_loss_grad_noalloc",
            "mpbp_set_batch_schedule", "mpbp_autotune", "mpbp_autotune_batched",
-           "mpbp_set_precision", "mpbp_step_capture", "mpbp_step_replay"]
+           "mpbp_set_precision", "mpbp_step_capture", "mpbp_step_replay",
+           "mpbp_adam_init", "mpbp_adam_step", "mpbp_adam_get_state", "mpbp_adam_set_state",
+           "mpbp_loss_grad_phases"]
 
 PRECISION_FP32 = 0        # FFTs on the CUDA cores
 PRECISION_TC_SPLIT16 = 1  # dense DFT matrices on the tensor cores, split FP16
@@ -118,6 +134,16 @@ def load(build_if_missing=True):
     lib.mpbp_set_schedule.restype = st
     lib.mpbp_set_precision.argtypes = [V, I32]
     lib.mpbp_set_precision.restype = st
+    lib.mpbp_adam_init.argtypes = [V, P(AdamParams), V, V]
+    lib.mpbp_adam_init.restype = st
+    lib.mpbp_adam_step.argtypes = [V, V, I32, V, V, V, V, V, V]
+    lib.mpbp_adam_step.restype = st
+    lib.mpbp_adam_get_state.argtypes = [V, V, V, V, V, V, V, V]
+    lib.mpbp_adam_get_state.restype = st
+    lib.mpbp_adam_set_state.argtypes = [V, V, V, V, V, V, V, V]
+    lib.mpbp_adam_set_state.restype = st
+    lib.mpbp_loss_grad_phases.argtypes = [V, V, V, V, V, I32, V, V, V, V, V]
+    lib.mpbp_loss_grad_phases.restype = st
     lib.mpbp_step_capture.argtypes = [V, V, V, V, V]
     lib.mpbp_step_capture.restype = st
     lib.mpbp_step_replay.argtypes = [V, V]
@@ -307,6 +333,78 @@ class Problem:
                                              _p(loss), _p(g_rho), _p(g_u), _p(g_alpha), _stream()),
                     "mpbp_loss_grad")
         return loss, g_rho, g_u, g_alpha
+
+    def _frames_arg(self, frames, dev):
+        nfr = 0
+        if frames is not None:
+            if not (frames.is_cuda and frames.dtype == torch.int32 and frames.dim() == 1
+                    and frames.is_contiguous()):
+                raise TypeError("frames must be a contiguous int32 CUDA vector")
+            nfr = frames.numel()
+            if nfr == 0:
+                frames = torch.zeros(1, dtype=torch.int32, device=dev)
+        return frames, nfr
+
+    def loss_grad_phases(self, rho, phi, alpha, frames=None):
+        """Per-peak-phase form: phi [D][n1][n2] in place of u; returns
+        (loss [1] float64, g_rho, g_phi [D][n1][n2], g_alpha [D] float64)."""
+        sh = self.shapes
+        _dev(rho, torch.float32, sh["rho"], "rho")
+        _dev(phi, torch.float32, (self.npeaks,) + tuple(sh["rho"]), "phi")
+        _dev(alpha, torch.float32, sh["alpha"], "alpha")
+        dev = rho.device
+        loss = torch.empty(1, dtype=torch.float64, device=dev)
+        g_rho = torch.empty(sh["rho"], dtype=torch.float32, device=dev)
+        g_phi = torch.empty_like(phi)
+        g_alpha = torch.empty(self.npeaks, dtype=torch.float64, device=dev)
+        frames, nfr = self._frames_arg(frames, dev)
+        self._check(self._lib.mpbp_loss_grad_phases(self._h, _p(rho), _p(phi), _p(alpha), _p(frames),
+                                                    nfr, _p(loss), _p(g_rho), _p(g_phi), _p(g_alpha),
+                                                    _stream()), "mpbp_loss_grad_phases")
+        return loss, g_rho, g_phi, g_alpha
+
+    def adam_init(self, lr_u=0.01, lr_chi=0.1, lr_alpha=0.1, beta1=0.9, beta2=0.999, eps=1e-8,
+                  state=None):
+        """Alg. 1's Adam (mpbp_adam_init); returns the device state buffer."""
+        prm = AdamParams(lr_u, lr_chi, lr_alpha, beta1, beta2, eps)
+        if state is None:
+            state = torch.zeros(ctypes.sizeof(AdamState), dtype=torch.uint8, device="cuda")
+        self._check(self._lib.mpbp_adam_init(self._h, ctypes.byref(prm), _p(state), _stream()),
+                    "mpbp_adam_init")
+        return state
+
+    def adam_step(self, frames, chi, u, alpha_t, state, mask=None):
+        """One minibatch iteration of Alg. 1 on chi, u, alpha_t (updated in place)."""
+        sh = self.shapes
+        _dev(chi, torch.float32, sh["rho"], "chi")
+        _dev(u, torch.float32, sh["u"], "u")
+        _dev(alpha_t, torch.float32, sh["alpha"], "alpha_t")
+        if mask is not None:
+            _dev(mask, torch.float32, sh["rho"], "mask")
+        frames, nfr = self._frames_arg(frames, chi.device)
+        self._check(self._lib.mpbp_adam_step(self._h, _p(frames), nfr, _p(chi), _p(u), _p(alpha_t),
+                                              _p(mask), _p(state), _stream()), "mpbp_adam_step")
+
+    def adam_get_state(self):
+        """(m_chi, v_chi, m_u, v_u, m_alpha, v_alpha) device copies of the moments."""
+        sh, dev = self.shapes, "cuda"
+        out = (torch.empty(sh["rho"], device=dev), torch.empty(sh["rho"], device=dev),
+               torch.empty(sh["u"], device=dev), torch.empty(sh["u"], device=dev),
+               torch.empty(self.npeaks, dtype=torch.float64, device=dev),
+               torch.empty(self.npeaks, dtype=torch.float64, device=dev))
+        self._check(self._lib.mpbp_adam_get_state(self._h, *[_p(t) for t in out], _stream()),
+                    "mpbp_adam_get_state")
+        return out
+
+    def adam_set_state(self, moments):
+        """Loads moments shaped as adam_get_state's (device tensors)."""
+        ms = [t.contiguous() for t in moments]
+        self._check(self._lib.mpbp_adam_set_state(self._h, *[_p(t) for t in ms], _stream()),
+                    "mpbp_adam_set_state")
+
+    @staticmethod
+    def read_adam_state(state):
+        return AdamState.from_buffer_copy(state.cpu().numpy().tobytes())
 
     def loss_grad_host(self, rho, u, alpha, y=None, out=None):
         """Host-buffer variant (copies in, evaluates, copies out, synchronises)."""
