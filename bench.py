@@ -330,6 +330,35 @@ def run_gpu(args):
             "tensor_flops_per_frame": tc_flops,
             "tensor_peak_tflops": pk["bf16_tflops"], "peak_src": pk["src"] + " (dense bf16 = fp16 rate)"}
         prob.set_precision(mpbp.PRECISION_FP32)
+    # the paper's own iteration (Alg. 1 without its projector): minibatches
+    # of 50 frames from a seeded shuffle per epoch, Adam in the Eq. 8
+    # variables with the paper's step sizes, inside the support mask
+    mask = torch.from_numpy(synth.support_mask(spec)).cuda()
+    chi = torch.log(torch.clamp(x[0], min=0.2)).contiguous()
+    ua = x[1].clone()
+    at = torch.log(x[2]).contiguous()
+    ast = prob.adam_init(lr_u=0.01, lr_chi=0.1, lr_alpha=0.1)
+    bsz = 50
+    epochs = [torch.from_numpy(synth.epoch_order(spec.nframes, spec.seed + 100 + e)).cuda() for e in range(3)]
+    batches = [[ep[k:k + bsz].contiguous() for k in range(0, spec.nframes, bsz)] for ep in epochs]
+    for fr in batches[0]:                    # warm-up epoch
+        prob.adam_step(fr, chi, ua, at, ast, mask=mask)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.zero_()
+    e0.record(stream)
+    for ep in batches[1:]:
+        for fr in ep:
+            prob.adam_step(fr, chi, ua, at, ast, mask=mask)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prob.sync_status()
+    ep_ms = e0.elapsed_time(e1) / (len(batches) - 1)
+    line["alg1"] = {
+        "iteration": "Alg. 1 minus the projector: minibatch of %d frames, Adam (0.01 u, 0.1 chi, 0.1 alpha)" % bsz,
+        "ms_per_epoch": ep_ms, "minibatches_per_epoch": len(batches[0]),
+        "ms_per_minibatch": ep_ms / len(batches[0]), "value": spec.nframes / (ep_ms / 1e3), "unit": UNIT,
+        "launches_per_minibatch": 5}
     if rank == 0 and not args.no_cpu_baseline:
         def gpu_eval(rho, u, alpha, precision):
             prob.set_precision(precision)
