@@ -93,6 +93,10 @@ def _load():
                                          ctypes.POINTER(AdamParams), ctypes.POINTER(ctypes.c_long),
                                          dp, dp, dp, dp, dp, dp, dp, dp, dp, ctypes.c_int]
         lib.oracle_adam_step.restype = ctypes.c_double
+        lib.oracle_unwrap2d.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp]
+        lib.oracle_unwrap2d.restype = None
+        lib.oracle_project_u.argtypes = [pp, dp, dp, dp]
+        lib.oracle_project_u.restype = None
         lib.oracle_max_threads.argtypes = []
         lib.oracle_max_threads.restype = ctypes.c_int
         _lib = lib
@@ -142,6 +146,16 @@ def adam_update(x, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     g = _d(g)
     lib.oracle_adam_update(x.size, _ptr(x), _ptr(g), _ptr(m), _ptr(v), int(t), float(lr),
                            float(beta1), float(beta2), float(eps))
+
+
+def unwrap2d(wrapped, mask=None):
+    """Reliability-sorted 2-D phase unwrapping of wrapped [n1][n2] (see
+    oracle_unwrap2d); mask nonzero = inside."""
+    lib = _load()
+    w = _d(wrapped)
+    out = np.empty_like(w)
+    lib.oracle_unwrap2d(w.shape[0], w.shape[1], _ptr(w), _ptr(None if mask is None else _d(mask)), _ptr(out))
+    return out
 
 
 def dft2(x, sign=-1):
@@ -224,6 +238,14 @@ class OracleProblem:
 
     def loss(self, rho, u, alpha, probe, y, bg=None, nthreads=0):
         return self.loss_grad(rho, u, alpha, probe, y, bg=bg, nthreads=nthreads)[0]
+
+    def project_u(self, u, mask=None):
+        """Pi_U of Eq. 10 (see oracle_project_u); returns the projected u."""
+        lib = _load()
+        u = _d(u)
+        out = np.empty_like(u)
+        lib.oracle_project_u(ctypes.byref(self.c), _ptr(u), _ptr(None if mask is None else _d(mask)), _ptr(out))
+        return out
 
     def loss_grad_phases(self, rho, phi, alpha, probe, y, bg=None, frames=None, nthreads=0):
         """Per-peak-phase form: phi [D][n1][n2]; returns (loss, g_rho, g_phi, g_alpha)."""

@@ -30,7 +30,9 @@
  * independent phase maps, the paper's "TS" variables, Sec. 5); the auxiliary
  * variables of Eq. 8 (rho = mask e^{chi}, alpha_m = e^{alpha_t_m}, alpha_0 = 1)
  * with the chain rule to them; and the minibatch Adam iteration of Alg. 1
- * without its projector line (Adam as in Kingma and Ba, arXiv 1412.6980).
+ * without its projector line (Adam as in Kingma and Ba, arXiv 1412.6980); and
+ * that projector, Pi_U of Eq. 10, with a reliability-sorted 2-D phase
+ * unwrapper written from Herraez et al. (2002).
  *
  * Complex arrays are interleaved (re, im) doubles.  Layouts (row-major):
  *   rho [n1][n2], u [C][n1][n2], alpha [D], G [D][C], scan [J][2] (row, col of
@@ -536,6 +538,179 @@ void oracle_step(const oracle_problem *p, const double *probe, const double *bg,
         alpha[mpk] = alpha_prev[mpk] - st->t * prm->w_alpha * galpha_prev[mpk];
     st->k += 1;
     free(grho); free(gu); free(galpha);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 9 / Eq. 10: phase wrapping, 2-D unwrapping, the projector Pi_U       */
+/* ------------------------------------------------------------------------ */
+
+static const double TWO_PI = 6.283185307179586476925286766559;
+
+/* W: the wrapped value of x in [-pi, pi) */
+static double wrap_phase(double x)
+{
+    return x - TWO_PI * floor(x / TWO_PI + 0.5);
+}
+
+typedef struct { double w; long id; } unwrap_edge;
+
+/* descending reliability, then ascending edge number: a strict total order */
+static int edge_cmp(const void *a, const void *b)
+{
+    const unwrap_edge *x = a, *y = b;
+    if (x->w > y->w) return -1;
+    if (x->w < y->w) return 1;
+    return (x->id > y->id) - (x->id < y->id);
+}
+
+/* 2-D phase unwrapping by reliability-sorted, non-continuous path following
+ * (Herraez, Burton, Lalor and Gdeisat, Appl. Opt. 41, 7437 (2002)), written
+ * from that description in the plainest form:
+ *   reliability R = 1 / D of a pixel whose eight neighbours are inside the
+ *     grid and the mask, D^2 = H^2 + V^2 + D1^2 + D2^2 with the second
+ *     differences H, V, D1, D2 of the wrapped phase along the two axes and
+ *     the two diagonals (each first difference wrapped); R = 0 elsewhere;
+ *   an edge joins two 4-neighbours in the mask, with reliability R_p + R_q;
+ *   edges are taken in order of decreasing reliability (ties: lower edge
+ *     number first; edge 2r joins pixel r to its right neighbour, 2r + 1 to
+ *     the one below); when an edge joins two groups, the group of its second
+ *     pixel is shifted by the multiple of 2 pi that brings the difference
+ *     across the edge into [-pi, pi), and the groups merge.
+ * Finally every group is shifted by the multiple of 2 pi that gives its
+ * lowest-numbered pixel back its wrapped value (so the result is unique for
+ * data without residues).  Pixels off the mask keep their wrapped value.
+ * mask (nullable = all pixels) is [n1][n2] with nonzero = inside. */
+void oracle_unwrap2d(int n1, int n2, const double *wrapped, const double *mask, double *out)
+{
+    long n = (long)n1 * n2;
+    double *R = calloc(n, sizeof(double));
+    long *label = malloc(sizeof(long) * n);
+    unwrap_edge *e = malloc(sizeof(unwrap_edge) * 2 * n);
+#define IN(i, j) ((i) >= 0 && (i) < n1 && (j) >= 0 && (j) < n2 && (!mask || mask[(long)(i) * n2 + (j)] != 0.0))
+#define PH(i, j) wrapped[(long)(i) * n2 + (j)]
+    for (int i = 0; i < n1; ++i)
+        for (int j = 0; j < n2; ++j) {
+            int ok = 1;
+            for (int di = -1; di <= 1; ++di)
+                for (int dj = -1; dj <= 1; ++dj)
+                    ok = ok && IN(i + di, j + dj);
+            if (!ok) continue;
+            double c = PH(i, j);
+            double h = wrap_phase(PH(i, j - 1) - c) - wrap_phase(c - PH(i, j + 1));
+            double v = wrap_phase(PH(i - 1, j) - c) - wrap_phase(c - PH(i + 1, j));
+            double d1 = wrap_phase(PH(i - 1, j - 1) - c) - wrap_phase(c - PH(i + 1, j + 1));
+            double d2 = wrap_phase(PH(i - 1, j + 1) - c) - wrap_phase(c - PH(i + 1, j - 1));
+            double dd = sqrt(h * h + v * v + d1 * d1 + d2 * d2);
+            R[(long)i * n2 + j] = 1.0 / (dd > 1e-300 ? dd : 1e-300);
+        }
+    long ne = 0;
+    for (int i = 0; i < n1; ++i)
+        for (int j = 0; j < n2; ++j) {
+            long r = (long)i * n2 + j;
+            if (!IN(i, j)) continue;
+            if (IN(i, j + 1)) { e[ne].w = R[r] + R[r + 1]; e[ne].id = 2 * r; ++ne; }
+            if (IN(i + 1, j)) { e[ne].w = R[r] + R[r + n2]; e[ne].id = 2 * r + 1; ++ne; }
+        }
+    qsort(e, ne, sizeof(unwrap_edge), edge_cmp);
+    for (long r = 0; r < n; ++r) { out[r] = wrapped[r]; label[r] = r; }
+    for (long k = 0; k < ne; ++k) {
+        long pa = e[k].id / 2;
+        long pb = (e[k].id & 1) ? pa + n2 : pa + 1;
+        long la = label[pa], lb = label[pb];
+        if (la == lb) continue;
+        double shift = TWO_PI * floor((out[pa] - out[pb]) / TWO_PI + 0.5);
+        for (long r = 0; r < n; ++r)
+            if (label[r] == lb) { out[r] += shift; label[r] = la; }
+    }
+    /* each group's lowest-numbered pixel keeps its wrapped value */
+    for (long r = 0; r < n; ++r) {
+        if (label[r] < 0) continue;                 /* group already normalised */
+        long l = label[r];
+        double shift = wrapped[r] - out[r];
+        for (long q = r; q < n; ++q)
+            if (label[q] == l) { out[q] += shift; label[q] = -1; }
+    }
+#undef IN
+#undef PH
+    free(R); free(label); free(e);
+}
+
+/* Moore-Penrose pseudo-inverse pinv [C][D] of G [D][C] (C <= 3) through the
+ * eigen-decomposition of G^T G by cyclic Jacobi rotations; eigenvalues below
+ * 1e-12 of the largest count as zero. */
+static void pinv_g(int D, int C, const double *G, double *pinv)
+{
+    double A[3][3] = {{0}}, V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    for (int a = 0; a < C; ++a)
+        for (int b = 0; b < C; ++b)
+            for (int m = 0; m < D; ++m) A[a][b] += G[m * C + a] * G[m * C + b];
+    for (int sweep = 0; sweep < 50; ++sweep)
+        for (int pq = 0; pq < C; ++pq)
+            for (int qq = pq + 1; qq < C; ++qq) {
+                if (fabs(A[pq][qq]) < 1e-300) continue;
+                double th = 0.5 * atan2(2 * A[pq][qq], A[qq][qq] - A[pq][pq]);
+                double c = cos(th), sn = sin(th);
+                for (int k = 0; k < C; ++k) {         /* A = J^T A J */
+                    double akp = A[k][pq], akq = A[k][qq];
+                    A[k][pq] = c * akp - sn * akq;
+                    A[k][qq] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < C; ++k) {
+                    double apk = A[pq][k], aqk = A[qq][k];
+                    A[pq][k] = c * apk - sn * aqk;
+                    A[qq][k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < C; ++k) {
+                    double vkp = V[k][pq], vkq = V[k][qq];
+                    V[k][pq] = c * vkp - sn * vkq;
+                    V[k][qq] = sn * vkp + c * vkq;
+                }
+            }
+    double lmax = 0.0;
+    for (int a = 0; a < C; ++a) lmax = fmax(lmax, fabs(A[a][a]));
+    double Ainv[3][3] = {{0}};
+    for (int a = 0; a < C; ++a)
+        for (int b = 0; b < C; ++b)
+            for (int k = 0; k < C; ++k)
+                if (A[k][k] > 1e-12 * lmax) Ainv[a][b] += V[a][k] * V[b][k] / A[k][k];
+    for (int a = 0; a < C; ++a)
+        for (int m = 0; m < D; ++m) {
+            double s = 0.0;
+            for (int b = 0; b < C; ++b) s += Ainv[a][b] * G[m * C + b];
+            pinv[a * D + m] = s;
+        }
+}
+
+/* Pi_U of Eq. 10: phases Phi_m = phase_scale G_m . u, wrapped (Eq. 9's W),
+ * unwrapped per peak inside the mask, and mapped back to u by the
+ * pseudo-inverse of G (the (H H^T)^{-1} H of Eq. 9 when the G_m span the
+ * components of u).  Written as a correction, u_out = u + (Phi' - Phi) G^+^T /
+ * phase_scale, so that components outside the span of the G_m (u_z for
+ * in-plane peaks) are left as they are.  Pixels off the mask are unchanged. */
+void oracle_project_u(const oracle_problem *p, const double *u, const double *mask, double *u_out)
+{
+    int D = p->npeaks, C = p->ncomp;
+    long npix = (long)p->n1 * p->n2;
+    double *phi = malloc(sizeof(double) * npix), *wr = malloc(sizeof(double) * npix);
+    double *un = malloc(sizeof(double) * npix), *dphi = malloc(sizeof(double) * D * npix);
+    double pinv[3 * 16];
+    pinv_g(D, C, p->G, pinv);
+    for (int m = 0; m < D; ++m) {
+        for (long r = 0; r < npix; ++r) {
+            phi[r] = phase_at(p, u, m, r);
+            wr[r] = wrap_phase(phi[r]);
+        }
+        oracle_unwrap2d(p->n1, p->n2, wr, mask, un);
+        for (long r = 0; r < npix; ++r) dphi[m * npix + r] = un[r] - phi[r];
+    }
+    for (int c = 0; c < C; ++c)
+        for (long r = 0; r < npix; ++r) {
+            double s = 0.0;
+            if (!mask || mask[r] != 0.0)
+                for (int m = 0; m < D; ++m) s += pinv[c * D + m] * dphi[m * npix + r];
+            u_out[c * npix + r] = u[c * npix + r] + s / p->phase_scale;
+        }
+    free(phi); free(wr); free(un); free(dphi);
 }
 
 int oracle_max_threads(void)
