@@ -254,6 +254,32 @@ mpbp_status mpbp_adam_set_state(mpbp_ctx *ctx, const float *m_chi, const float *
                                 const float *m_u, const float *v_u, const double *m_alpha,
                                 const double *v_alpha, void *stream);
 
+/* W^{-1} of Eq. 9: 2-D phase unwrapping of D maps (dev [D][n1][n2], the
+ * context's grid, values in [-pi, pi)) into out (dev, same shape; may be the
+ * input), inside mask (dev [n1][n2], nonzero = inside, or NULL).  The method
+ * is reliability-ordered path following (Herraez et al., Appl. Opt. 41, 7437,
+ * 2002): pixel reliability 1 / sqrt(H^2 + V^2 + D1^2 + D2^2) from the wrapped
+ * second differences (0 at the border and next to the mask's edge), edges
+ * between 4-neighbours weighted by the sum of their pixels' reliabilities and
+ * taken in decreasing order (ties: lower edge number, 2 r + {0: right,
+ * 1: down}), i.e. integration along the maximum spanning forest.  Each
+ * connected region is then shifted by the multiple of 2 pi that gives its
+ * lowest-numbered pixel its wrapped value; pixels off the mask keep theirs.
+ * The first call allocates the unwrapper's workspace (~52 bytes per pixel
+ * and map) and synchronises.  One cooperative launch; its grid barriers are
+ * bounded in time (MPBP_ERR_TIMEOUT via mpbp_sync_status if one runs out). */
+mpbp_status mpbp_unwrap_phases(mpbp_ctx *ctx, const float *wrapped, const float *mask,
+                               float *out, void *stream);
+
+/* Pi_U of Eq. 10 on u (dev [C][n1][n2], in place): Phi_m = phase_scale G_m . u,
+ * wrapped, unwrapped as mpbp_unwrap_phases inside mask, and mapped back with
+ * the Moore-Penrose pseudo-inverse of G (the H^T (H H^T)^{-1} of Eq. 10 when
+ * the G_m span the components of u), as the correction
+ * u += (Phi' - Phi) pinv(G)^T / phase_scale; components no G_m reaches and
+ * pixels off the mask are left as they are.  Alg. 1 applies it after every
+ * Adam step (the paper's C-UW reconstruction). */
+mpbp_status mpbp_project_displacement(mpbp_ctx *ctx, float *u, const float *mask, void *stream);
+
 /* The per-peak-phase form of Eq. 3 (the variables of the paper's two-step
  * reconstruction, Sec. 5): objects O_m = alpha_m rho e^{i phi_m} from D
  * independent phase maps phi (dev [D][n1][n2]) instead of the displacement

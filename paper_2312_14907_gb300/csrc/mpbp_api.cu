@@ -13,6 +13,7 @@
 
 #include "aux_launch.h"
 #include "frames_launch.h"
+#include "unwrap_launch.h"
 
 using namespace mpbp;
 
@@ -27,6 +28,7 @@ struct mpbp_ctx {
   long long npix = 0;
   long long nframes = 0;  // D * J
   PhaseCoef pc{};
+  std::vector<double> G;   // [D][C] scattering vectors
   // kernel schedule
   FrameKernelInfo fk{};       // the gradient kernel in use
   FrameKernelInfo fk_fft{};   // the FFT kernels (forward mode always uses them)
@@ -97,6 +99,11 @@ struct mpbp_ctx {
   float *m_chi = nullptr, *v_chi = nullptr, *m_u = nullptr, *v_u = nullptr;
   double *m_a = nullptr, *v_a = nullptr;
   float *rho_x = nullptr, *alpha_x = nullptr;
+  // phase unwrapping / projector workspace (lazily allocated)
+  void* uw_buf = nullptr;
+  UnwrapArgs uw{};
+  float *pj_phi = nullptr, *pj_wrapped = nullptr;
+  int uw_grid = 0;
   // one optimizer step captured as a CUDA graph (mpbp_step_capture)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t step_exec = nullptr;
@@ -335,6 +342,7 @@ mpbp_status mpbp_create(const mpbp_problem* pr, mpbp_ctx** out) {
   for (int m = 0; m < c->D; ++m)
     for (int k = 0; k < kMaxComp; ++k) {
       const double g = k < c->C ? pr->G[m * c->C + k] : 0.0;
+      if (k < c->C) c->G.push_back(g);
       c->pc.kpi[m][k] = (float)(pr->phase_scale * g / 3.14159265358979323846);
       c->pc.kps[m][k] = (float)(pr->phase_scale * g);
     }
@@ -434,6 +442,7 @@ void mpbp_destroy(mpbp_ctx* c) {
   if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->adam_buf) cudaFree(c->adam_buf);
+  if (c->uw_buf) cudaFree(c->uw_buf);
   delete c;
 }
 
@@ -941,6 +950,136 @@ mpbp_status mpbp_loss_grad_phases(mpbp_ctx* c, const float* rho, const float* ph
   if (!c->has_probe || !c->has_data) return fail(c, MPBP_ERR_NO_DATA, "probe or data not set");
   return enqueue_loss_grad(c, rho, nullptr, alpha, frames, frames ? nframes : 0, loss, g_rho, nullptr,
                            g_alpha, nullptr, S(stream), phi, g_phi);
+}
+
+// the unwrapper's workspace for the context's D maps
+mpbp_status unwrap_setup(mpbp_ctx* c, cudaStream_t s) {
+  if (c->uw_buf) return MPBP_OK;
+  if (!unwrap_prepare(c->num_sms, &c->uw_grid)) return fail(c, MPBP_ERR_CUDA, "unwrap kernel cannot run here");
+  const long long nodes = c->npix * c->D;
+  Carver cv;
+  const size_t o_rel = cv.take<float>(nodes), o_p = cv.take<int>(nodes), o_o = cv.take<int>(nodes),
+               o_p2 = cv.take<int>(nodes), o_o2 = cv.take<int>(nodes), o_hp = cv.take<int>(nodes),
+               o_ho = cv.take<int>(nodes), o_mn = cv.take<int>(nodes),
+               o_b = cv.take<unsigned long long>(nodes), o_f = cv.take<int>(3), o_bc = cv.take<unsigned>(2),
+               o_phi = cv.take<float>(nodes), o_w = cv.take<float>(nodes);
+  void* b = nullptr;
+  MPBP_CUDA(c, cudaStreamSynchronize(s));
+  if (cudaMalloc(&b, align_up(cv.off, 256)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, MPBP_ERR_OOM, "unwrap workspace");
+  }
+  c->uw_buf = b;
+  char* p = static_cast<char*>(b);
+  UnwrapArgs& a = c->uw;
+  a.rel = reinterpret_cast<float*>(p + o_rel);
+  a.parent = reinterpret_cast<int*>(p + o_p);
+  a.off = reinterpret_cast<int*>(p + o_o);
+  a.parent2 = reinterpret_cast<int*>(p + o_p2);
+  a.off2 = reinterpret_cast<int*>(p + o_o2);
+  a.hook_parent = reinterpret_cast<int*>(p + o_hp);
+  a.hook_off = reinterpret_cast<int*>(p + o_ho);
+  a.minnode = reinterpret_cast<int*>(p + o_mn);
+  a.best = reinterpret_cast<unsigned long long*>(p + o_b);
+  a.flags = reinterpret_cast<int*>(p + o_f);
+  a.bar_count = reinterpret_cast<unsigned*>(p + o_bc);
+  a.bar_gen = a.bar_count + 1;
+  a.err = c->err;
+  a.npix = c->npix;
+  a.nodes = nodes;
+  a.n1 = c->n1;
+  a.n2 = c->n2;
+  int rounds = 2;
+  while ((1ll << rounds) < nodes) ++rounds;
+  a.max_rounds = rounds + 2;
+  c->pj_phi = reinterpret_cast<float*>(p + o_phi);
+  c->pj_wrapped = reinterpret_cast<float*>(p + o_w);
+  return MPBP_OK;
+}
+
+mpbp_status enqueue_unwrap(mpbp_ctx* c, const float* wrapped, const float* mask, float* out, cudaStream_t s) {
+  UnwrapArgs a = c->uw;
+  a.wrapped = wrapped;
+  a.mask = mask;
+  a.out = out;
+  MPBP_CUDA(c, cudaMemsetAsync(a.flags, 0, sizeof(int) * 3, s));
+  MPBP_CUDA(c, cudaMemsetAsync(a.bar_count, 0, sizeof(unsigned) * 2, s));
+  MPBP_CUDA(c, unwrap_launch(a, c->uw_grid, s));
+  return MPBP_OK;
+}
+
+// Moore-Penrose pseudo-inverse [C][D] of G [D][C] (C <= 3) as the limit of
+// (G^T G + delta I)^{-1} G^T: delta = 1e-12 trace(G^T G) leaves full-rank
+// cases exact to ~1e-12 and maps directions no G_m reaches to zero.
+void pseudo_inverse(int D, int C, const std::vector<double>& G, double* pinv) {
+  double A[3][3] = {{0}};
+  double tr = 0.0;
+  for (int a = 0; a < C; ++a)
+    for (int b = 0; b < C; ++b) {
+      for (int m = 0; m < D; ++m) A[a][b] += G[m * C + a] * G[m * C + b];
+    }
+  for (int a = 0; a < C; ++a) tr += A[a][a];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      if (a >= C || b >= C) A[a][b] = (a == b) ? 1.0 : 0.0;
+      else if (a == b) A[a][b] += 1e-12 * tr;
+    }
+  // 3 x 3 inverse by cofactors
+  double inv[3][3];
+  const double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+                     A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+                     A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+  inv[0][0] = (A[1][1] * A[2][2] - A[1][2] * A[2][1]) / det;
+  inv[0][1] = (A[0][2] * A[2][1] - A[0][1] * A[2][2]) / det;
+  inv[0][2] = (A[0][1] * A[1][2] - A[0][2] * A[1][1]) / det;
+  inv[1][0] = (A[1][2] * A[2][0] - A[1][0] * A[2][2]) / det;
+  inv[1][1] = (A[0][0] * A[2][2] - A[0][2] * A[2][0]) / det;
+  inv[1][2] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) / det;
+  inv[2][0] = (A[1][0] * A[2][1] - A[1][1] * A[2][0]) / det;
+  inv[2][1] = (A[0][1] * A[2][0] - A[0][0] * A[2][1]) / det;
+  inv[2][2] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) / det;
+  for (int a = 0; a < C; ++a)
+    for (int m = 0; m < D; ++m) {
+      double v = 0.0;
+      for (int b = 0; b < C; ++b) v += inv[a][b] * G[m * C + b];
+      pinv[a * D + m] = v;
+    }
+}
+
+mpbp_status mpbp_unwrap_phases(mpbp_ctx* c, const float* wrapped, const float* mask, float* out, void* stream) {
+  if (!c || !wrapped || !out) return fail(c, MPBP_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = S(stream);
+  mpbp_status r = unwrap_setup(c, s);
+  if (r != MPBP_OK) return r;
+  return enqueue_unwrap(c, wrapped, mask, out, s);
+}
+
+mpbp_status mpbp_project_displacement(mpbp_ctx* c, float* u, const float* mask, void* stream) {
+  if (!c || !u) return fail(c, MPBP_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = S(stream);
+  mpbp_status r = unwrap_setup(c, s);
+  if (r != MPBP_OK) return r;
+  ProjectArgs pa{};
+  pa.u = u;
+  pa.mask = mask;
+  pa.phi = c->pj_phi;
+  pa.wrapped = c->pj_wrapped;
+  pa.unwrapped = c->pj_wrapped;   // unwrapped in place of the wrapped copy
+  pa.npix = c->npix;
+  pa.C = c->C;
+  pa.D = c->D;
+  double pinv[kMaxComp * kMaxPeaks];
+  pseudo_inverse(c->D, c->C, c->G, pinv);
+  for (int m = 0; m < c->D; ++m)
+    for (int k = 0; k < c->C; ++k) {
+      pa.g_scaled[m * kMaxComp + k] = (float)(c->phase_scale * c->G[m * c->C + k]);
+      pa.pinv_scaled[k * kMaxPeaks + m] = (float)(pinv[k * c->D + m] / c->phase_scale);
+    }
+  MPBP_CUDA(c, project_phase_launch(pa, c->num_sms, s));
+  r = enqueue_unwrap(c, c->pj_wrapped, mask, c->pj_wrapped, s);
+  if (r != MPBP_OK) return r;
+  MPBP_CUDA(c, project_correct_launch(pa, c->num_sms, s));
+  return MPBP_OK;
 }
 
 mpbp_status mpbp_step_capture(mpbp_ctx* c, float* rho, float* u, float* alpha, mpbp_step_state* st) {

@@ -1,0 +1,286 @@
+// mpbp_unwrap.cu -- the projector Pi_U of Eq. 10 on the GPU: the phases
+// Phi_m = phase_scale G_m . u, wrapped (Eq. 9's W), unwrapped by
+// reliability-ordered path following (Herraez et al., Appl. Opt. 2002), and
+// mapped back to u with the pseudo-inverse of G.
+//
+// Path-following unwrappers merge pixel groups along edges taken in order of
+// decreasing reliability, i.e. they integrate the wrapped phase differences
+// along the maximum spanning forest of the pixel grid (edge weight = the sum
+// of its pixels' reliabilities, ties broken by the edge number so that the
+// order is strict and the forest unique).  Here that forest is built in
+// parallel by Boruvka rounds instead of a sorted sweep:
+//   - every component takes its heaviest incident edge (64-bit atomicMax of
+//     (weight bits, ~edge number)); a root whose choice is shared with the
+//     component on the other side keeps its place if its index is the lower;
+//   - each other root hooks under the component across its edge with the
+//     multiple of 2 pi that brings the phase difference across the edge into
+//     [-pi, pi) (its offset relative to its new parent);
+//   - pointer jumping compresses the forest, adding offsets along the way,
+//     until every pixel points at its root with its offset to it.
+// The rounds repeat until no root hooks; each group is then shifted so that
+// its lowest-numbered pixel keeps its wrapped value.  The D phase maps form
+// one graph with D disconnected parts.
+//
+// All of it runs in one cooperative launch (every block resident), with grid
+// barriers that are bounded in time: if one runs out, the block records
+// kErrTimeout and leaves, and the rest run out at their next barrier.
+#include <cmath>
+#include <climits>
+
+#include "unwrap_launch.h"
+
+namespace mpbp {
+
+namespace {
+
+constexpr float kTwoPi = 6.28318530717958647692f;
+constexpr unsigned long long kBarrierNs = 100ull * 1000 * 1000;   // 0.1 s per barrier
+constexpr int kUnwrapThreads = 256;
+
+__device__ __forceinline__ float wrapf(float x) { return x - kTwoPi * floorf(x / kTwoPi + 0.5f); }
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Sense by generation: the last block to arrive resets the count and bumps
+// the generation; the others wait (bounded) for the generation to change.
+// Returns false (in every thread of the block) if this block's wait ran out.
+__device__ bool grid_sync(UnwrapArgs& a) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned* genp = a.bar_gen;
+    const unsigned g = *genp;
+    __threadfence();
+    if (atomicAdd(a.bar_count, 1u) == gridDim.x - 1) {
+      *a.bar_count = 0u;
+      __threadfence();
+      atomicAdd(a.bar_gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*genp == g) {
+        if (global_ns() - t0 > kBarrierNs) {
+          atomicOr(a.err, kErrTimeout);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+__device__ __forceinline__ bool in_mask(const UnwrapArgs& a, long long r) { return !a.mask || a.mask[r] != 0.0f; }
+
+// reliability of node v: 1 / sqrt(H^2 + V^2 + D1^2 + D2^2) when all eight
+// neighbours are in the grid and the mask, else 0
+__device__ float reliability(const UnwrapArgs& a, long long v) {
+  const long long m = v / a.npix, r = v - m * a.npix;
+  const int i = (int)(r / a.n2), j = (int)(r - (long long)i * a.n2);
+  if (i < 1 || j < 1 || i > a.n1 - 2 || j > a.n2 - 2) return 0.0f;
+  for (int di = -1; di <= 1; ++di)
+    for (int dj = -1; dj <= 1; ++dj)
+      if (!in_mask(a, r + (long long)di * a.n2 + dj)) return 0.0f;
+  const float* w = a.wrapped + m * a.npix;
+  auto P = [&](int ii, int jj) { return w[(long long)ii * a.n2 + jj]; };
+  const float c = P(i, j);
+  const float h = wrapf(P(i, j - 1) - c) - wrapf(c - P(i, j + 1));
+  const float vv = wrapf(P(i - 1, j) - c) - wrapf(c - P(i + 1, j));
+  const float d1 = wrapf(P(i - 1, j - 1) - c) - wrapf(c - P(i + 1, j + 1));
+  const float d2 = wrapf(P(i - 1, j + 1) - c) - wrapf(c - P(i + 1, j - 1));
+  const float dd = sqrtf(h * h + vv * vv + d1 * d1 + d2 * d2);
+  return 1.0f / fmaxf(dd, 1e-30f);
+}
+
+// the other end of edge e = 2 v + dir (dir 0: right, 1: down), or -1
+__device__ __forceinline__ long long edge_other(const UnwrapArgs& a, long long e) {
+  const long long v = e >> 1;
+  const long long r = v % a.npix;
+  const int i = (int)(r / a.n2), j = (int)(r - (long long)i * a.n2);
+  long long q;
+  if (e & 1) {
+    if (i + 1 >= a.n1) return -1;
+    q = v + a.n2;
+  } else {
+    if (j + 1 >= a.n2) return -1;
+    q = v + 1;
+  }
+  if (!in_mask(a, r) || !in_mask(a, q % a.npix)) return -1;
+  return q;
+}
+
+__device__ __forceinline__ unsigned long long edge_key(float w, long long e) {
+  return ((unsigned long long)__float_as_uint(w) << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)e);
+}
+
+__global__ void __launch_bounds__(kUnwrapThreads) unwrap_kernel(UnwrapArgs a) {
+  const long long n = a.nodes;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  int* par[2] = {a.parent, a.parent2};
+  int* off[2] = {a.off, a.off2};
+  int cur = 0;   // which buffer holds the forest
+
+  for (long long v = tid; v < n; v += stride) {
+    a.rel[v] = reliability(a, v);
+    a.parent[v] = (int)v;
+    a.off[v] = 0;
+  }
+  if (!grid_sync(a)) return;
+
+  int flag_it = 0;   // flags rotate over 3 slots (see next_flag)
+  auto next_flag = [&]() {
+    // the slot of the next use is cleared now; it was last read two uses ago
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.flags[(flag_it + 1) % 3] = 0;
+  };
+
+  for (int round = 0; round < a.max_rounds; ++round) {
+    int* P = par[cur];
+    int* O = off[cur];
+    for (long long v = tid; v < n; v += stride) a.best[v] = 0ull;
+    if (!grid_sync(a)) return;
+    // heaviest incident edge of every component
+    for (long long e = tid; e < 2 * n; e += stride) {
+      const long long q = edge_other(a, e);
+      if (q < 0) continue;
+      const long long p = e >> 1;
+      const int rp = P[p], rq = P[q];
+      if (rp == rq) continue;
+      const unsigned long long key = edge_key(a.rel[p] + a.rel[q], e);
+      atomicMax(&a.best[rp], key);
+      atomicMax(&a.best[rq], key);
+    }
+    if (!grid_sync(a)) return;
+    // hooks, decided from a consistent snapshot
+    const int fs = flag_it % 3;
+    for (long long r = tid; r < n; r += stride) {
+      a.hook_parent[r] = -1;
+      if (P[r] != (int)r || a.best[r] == 0ull) continue;
+      const long long e = 0xFFFFFFFFll - (long long)(a.best[r] & 0xFFFFFFFFull);
+      const long long p = e >> 1, q = edge_other(a, e);
+      const bool p_in_r = P[p] == (int)r;
+      const long long pr = p_in_r ? p : q, ps = p_in_r ? q : p;
+      const int s = P[ps];
+      if (a.best[s] == a.best[r] && r < s) continue;   // the shared edge: s hooks under r
+      const float d = (a.wrapped[pr] + kTwoPi * (float)O[pr]) - (a.wrapped[ps] + kTwoPi * (float)O[ps]);
+      a.hook_parent[r] = s;
+      a.hook_off[r] = -(int)floorf(d / kTwoPi + 0.5f);
+      a.flags[fs] = 1;
+    }
+    next_flag();
+    if (!grid_sync(a)) return;
+    const bool any = *(volatile int*)&a.flags[fs] != 0;
+    ++flag_it;
+    for (long long r = tid; r < n; r += stride) {
+      if (a.hook_parent[r] >= 0) {
+        P[r] = a.hook_parent[r];
+        O[r] = a.hook_off[r];
+      }
+    }
+    if (!grid_sync(a)) return;
+    if (!any) break;
+    // pointer jumping until every node points at its root (an acyclic
+    // forest of n nodes needs at most log2(n) + 1 passes; the cap only
+    // guards against a forest that is not)
+    for (int jump = 0;; ++jump) {
+      if (jump > 64) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(a.err, kErrTimeout);
+        break;
+      }
+      int* Pi = par[cur];
+      int* Oi = off[cur];
+      int* Po = par[cur ^ 1];
+      int* Oo = off[cur ^ 1];
+      const int fj = flag_it % 3;
+      for (long long v = tid; v < n; v += stride) {
+        const int p = Pi[v], pp = Pi[p];
+        Po[v] = pp;
+        Oo[v] = Oi[v] + (pp != p ? Oi[p] : 0);
+        if (pp != p) a.flags[fj] = 1;
+      }
+      next_flag();
+      if (!grid_sync(a)) return;
+      const bool changed = *(volatile int*)&a.flags[fj] != 0;
+      ++flag_it;
+      cur ^= 1;
+      if (!changed) break;
+    }
+  }
+
+  // each group's lowest-numbered node keeps its wrapped value
+  int* P = par[cur];
+  int* O = off[cur];
+  for (long long v = tid; v < n; v += stride) a.minnode[v] = INT_MAX;
+  if (!grid_sync(a)) return;
+  for (long long v = tid; v < n; v += stride) atomicMin(&a.minnode[P[v]], (int)v);
+  if (!grid_sync(a)) return;
+  for (long long v = tid; v < n; v += stride) {
+    const int mn = a.minnode[P[v]];
+    a.out[v] = a.wrapped[v] + kTwoPi * (float)(O[v] - O[mn]);
+  }
+}
+
+// Phi_m = phase_scale G_m . u, wrapped
+__global__ void project_phase_kernel(ProjectArgs a) {
+  const long long n = a.npix * a.D;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(i / a.npix);
+    const long long r = i - (long long)m * a.npix;
+    float ph = 0.0f;
+    for (int c = 0; c < a.C; ++c) ph = fmaf(a.g_scaled[m * kMaxComp + c], a.u[c * a.npix + r], ph);
+    a.phi[i] = ph;
+    a.wrapped[i] = wrapf(ph);
+  }
+}
+
+// u += (Phi' - Phi) pinv^T / phase_scale inside the mask
+__global__ void project_correct_kernel(ProjectArgs a) {
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < a.npix;
+       r += (long long)gridDim.x * blockDim.x) {
+    if (a.mask && a.mask[r] == 0.0f) continue;
+    for (int c = 0; c < a.C; ++c) {
+      float s = 0.0f;
+      for (int m = 0; m < a.D; ++m) s = fmaf(a.pinv_scaled[c * kMaxPeaks + m], a.unwrapped[m * a.npix + r] - a.phi[m * a.npix + r], s);
+      a.u[c * a.npix + r] += s;
+    }
+  }
+}
+
+}  // namespace
+
+bool unwrap_prepare(int num_sms, int* grid) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unwrap_kernel, kUnwrapThreads, 0) != cudaSuccess ||
+      per_sm < 1)
+    return false;
+  *grid = num_sms * (per_sm < 4 ? per_sm : 4);
+  return true;
+}
+
+cudaError_t unwrap_launch(const UnwrapArgs& a, int grid, cudaStream_t s) {
+  void* args[] = {const_cast<UnwrapArgs*>(&a)};
+  return cudaLaunchCooperativeKernel((const void*)unwrap_kernel, dim3(grid), dim3(kUnwrapThreads), args, 0, s);
+}
+
+cudaError_t project_phase_launch(const ProjectArgs& a, int num_sms, cudaStream_t s) {
+  const long long n = a.npix * a.D;
+  const long long b = (n + 255) / 256;
+  project_phase_kernel<<<(int)(b < num_sms * 8 ? b : num_sms * 8), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t project_correct_launch(const ProjectArgs& a, int num_sms, cudaStream_t s) {
+  const long long b = (a.npix + 255) / 256;
+  project_correct_kernel<<<(int)(b < num_sms * 8 ? b : num_sms * 8), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace mpbp

@@ -79,7 +79,7 @@ EXPORTS = ["mpbp_status_string", "mpbp_create", "mpbp_destroy", "mpbp_last_error
            "mpbp_set_batch_schedule", "mpbp_autotune", "mpbp_autotune_batched",
            "mpbp_set_precision", "mpbp_step_capture", "mpbp_step_replay",
            "mpbp_adam_init", "mpbp_adam_step", "mpbp_adam_get_state", "mpbp_adam_set_state",
-           "mpbp_loss_grad_phases"]
+           "mpbp_loss_grad_phases", "mpbp_unwrap_phases", "mpbp_project_displacement"]
 
 PRECISION_FP32 = 0        # FFTs on the CUDA cores
 PRECISION_TC_SPLIT16 = 1  # dense DFT matrices on the tensor cores, split FP16
@@ -144,6 +144,10 @@ def load(build_if_missing=True):
     lib.mpbp_adam_set_state.restype = st
     lib.mpbp_loss_grad_phases.argtypes = [V, V, V, V, V, I32, V, V, V, V, V]
     lib.mpbp_loss_grad_phases.restype = st
+    lib.mpbp_unwrap_phases.argtypes = [V, V, V, V, V]
+    lib.mpbp_unwrap_phases.restype = st
+    lib.mpbp_project_displacement.argtypes = [V, V, V, V]
+    lib.mpbp_project_displacement.restype = st
     lib.mpbp_step_capture.argtypes = [V, V, V, V, V]
     lib.mpbp_step_capture.restype = st
     lib.mpbp_step_replay.argtypes = [V, V]
@@ -362,6 +366,27 @@ class Problem:
                                                     nfr, _p(loss), _p(g_rho), _p(g_phi), _p(g_alpha),
                                                     _stream()), "mpbp_loss_grad_phases")
         return loss, g_rho, g_phi, g_alpha
+
+    def unwrap_phases(self, wrapped, mask=None, out=None):
+        """2-D unwrapping of D phase maps [D][n1][n2] (mpbp_unwrap_phases)."""
+        shp = (self.npeaks,) + tuple(self.shapes["rho"])
+        _dev(wrapped, torch.float32, shp, "wrapped")
+        if mask is not None:
+            _dev(mask, torch.float32, self.shapes["rho"], "mask")
+        if out is None:
+            out = torch.empty_like(wrapped)
+        self._check(self._lib.mpbp_unwrap_phases(self._h, _p(wrapped), _p(mask), _p(out), _stream()),
+                    "mpbp_unwrap_phases")
+        return out
+
+    def project_displacement(self, u, mask=None):
+        """Pi_U of Eq. 10 on u, in place (mpbp_project_displacement)."""
+        _dev(u, torch.float32, self.shapes["u"], "u")
+        if mask is not None:
+            _dev(mask, torch.float32, self.shapes["rho"], "mask")
+        self._check(self._lib.mpbp_project_displacement(self._h, _p(u), _p(mask), _stream()),
+                    "mpbp_project_displacement")
+        return u
 
     def adam_init(self, lr_u=0.01, lr_chi=0.1, lr_alpha=0.1, beta1=0.9, beta2=0.999, eps=1e-8,
                   state=None):
