@@ -354,11 +354,27 @@ def run_gpu(args):
     torch.cuda.synchronize()
     prob.sync_status()
     ep_ms = e0.elapsed_time(e1) / (len(batches) - 1)
+    # with the projector line: Pi_U on u after every Adam step (C-UW)
+    torch.cuda.synchronize()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    prob.project_displacement(ua, mask)      # workspace set-up outside the timing
+    torch.cuda.synchronize()
+    e2.record(stream)
+    for fr in batches[1]:
+        prob.adam_step(fr, chi, ua, at, ast, mask=mask)
+        prob.project_displacement(ua, mask)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    prob.sync_status()
+    cuw_ms = e2.elapsed_time(e3)
     line["alg1"] = {
         "iteration": "Alg. 1 minus the projector: minibatch of %d frames, Adam (0.01 u, 0.1 chi, 0.1 alpha)" % bsz,
         "ms_per_epoch": ep_ms, "minibatches_per_epoch": len(batches[0]),
         "ms_per_minibatch": ep_ms / len(batches[0]), "value": spec.nframes / (ep_ms / 1e3), "unit": UNIT,
-        "launches_per_minibatch": 5}
+        "launches_per_minibatch": 5,
+        "with_projector": {"ms_per_epoch": cuw_ms, "ms_per_minibatch": cuw_ms / len(batches[1]),
+                           "projector_ms": (cuw_ms - ep_ms) / len(batches[1]),
+                           "value": spec.nframes / (cuw_ms / 1e3), "unit": UNIT}}
     if rank == 0 and not args.no_cpu_baseline:
         def gpu_eval(rho, u, alpha, precision):
             prob.set_precision(precision)

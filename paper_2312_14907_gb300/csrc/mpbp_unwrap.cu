@@ -63,6 +63,7 @@ __device__ bool grid_sync(UnwrapArgs& a) {
     } else {
       const unsigned long long t0 = global_ns();
       while (*genp == g) {
+        __nanosleep(32);
         if (global_ns() - t0 > kBarrierNs) {
           atomicOr(a.err, kErrTimeout);
           ok = 0;
@@ -132,6 +133,7 @@ __global__ void __launch_bounds__(kUnwrapThreads) unwrap_kernel(UnwrapArgs a) {
     a.rel[v] = reliability(a, v);
     a.parent[v] = (int)v;
     a.off[v] = 0;
+    a.best[v] = 0ull;
   }
   if (!grid_sync(a)) return;
 
@@ -144,9 +146,7 @@ __global__ void __launch_bounds__(kUnwrapThreads) unwrap_kernel(UnwrapArgs a) {
   for (int round = 0; round < a.max_rounds; ++round) {
     int* P = par[cur];
     int* O = off[cur];
-    for (long long v = tid; v < n; v += stride) a.best[v] = 0ull;
-    if (!grid_sync(a)) return;
-    // heaviest incident edge of every component
+    // heaviest incident edge of every component (best[] is all zero here)
     for (long long e = tid; e < 2 * n; e += stride) {
       const long long q = edge_other(a, e);
       if (q < 0) continue;
@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(kUnwrapThreads) unwrap_kernel(UnwrapArgs a) {
         P[r] = a.hook_parent[r];
         O[r] = a.hook_off[r];
       }
+      a.best[r] = 0ull;   // every decision that read it is behind the last barrier
     }
     if (!grid_sync(a)) return;
     if (!any) break;
@@ -261,7 +262,7 @@ bool unwrap_prepare(int num_sms, int* grid) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unwrap_kernel, kUnwrapThreads, 0) != cudaSuccess ||
       per_sm < 1)
     return false;
-  *grid = num_sms * (per_sm < 4 ? per_sm : 4);
+  *grid = num_sms * (per_sm < 2 ? per_sm : 2);   // 2 per SM: measured fastest (fewer barrier arrivals)
   return true;
 }
 

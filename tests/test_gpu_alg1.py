@@ -163,3 +163,34 @@ def test_adam_epoch_lowers_the_loss_and_resumes_from_a_checkpoint():
     assert p.read_adam_state(st).t == q.read_adam_state(st_q).t
     p.sync_status()
     q.sync_status()
+
+
+def test_concurrent_unwrapped_iteration_lowers_the_loss():
+    """Alg. 1 with its projector line (the paper's C-UW): an Adam step, then
+    Pi_U on u inside the support; one shuffled epoch lowers the full loss,
+    and the projected field is a fixed point of Pi_U."""
+    from paper_2312_14907_gb300 import synth
+    case = _case()
+    spec = case.spec
+    mask = _mask(spec)
+    md = torch.from_numpy(mask).cuda()
+    p = _problem(case)
+    st = p.adam_init(lr_u=0.005, lr_chi=0.02, lr_alpha=0.02)
+    chi0, u0, at0 = _log_state(case)
+    chi, u, at = [torch.from_numpy(a.copy()).cuda() for a in (chi0, u0, at0)]
+
+    def full_loss():
+        rho = (md * torch.exp(chi)).contiguous()
+        alpha = torch.exp(at)
+        alpha[0] = 1.0
+        return p.loss_grad(rho, u, alpha.contiguous())[0].item()
+
+    f0 = full_loss()
+    order = torch.from_numpy(synth.epoch_order(spec.nframes, 5)).cuda()
+    for k in range(0, spec.nframes, 25):
+        p.adam_step(order[k:k + 25].contiguous(), chi, u, at, st, mask=md)
+        p.project_displacement(u, md)
+    assert full_loss() < f0
+    again = p.project_displacement(u.clone(), md)
+    assert rel_l2(again.cpu().numpy(), u.cpu().numpy()) <= 1e-6
+    p.sync_status()
