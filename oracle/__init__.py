@@ -97,6 +97,8 @@ def _load():
         lib.oracle_unwrap2d.restype = None
         lib.oracle_project_u.argtypes = [pp, dp, dp, dp]
         lib.oracle_project_u.restype = None
+        lib.oracle_illumination.argtypes = [pp, dp, dp]
+        lib.oracle_illumination.restype = None
         lib.oracle_max_threads.argtypes = []
         lib.oracle_max_threads.restype = ctypes.c_int
         _lib = lib
@@ -238,6 +240,13 @@ class OracleProblem:
 
     def loss(self, rho, u, alpha, probe, y, bg=None, nthreads=0):
         return self.loss_grad(rho, u, alpha, probe, y, bg=bg, nthreads=nthreads)[0]
+
+    def illumination(self, probe):
+        """sum over frames of |P(r - s_j)|^2 on the object grid (oracle_illumination)."""
+        lib = _load()
+        out = np.empty(self.shape)
+        lib.oracle_illumination(ctypes.byref(self.c), _ptr(_c(probe)), _ptr(out))
+        return out
 
     def project_u(self, u, mask=None):
         """Pi_U of Eq. 10 (see oracle_project_u); returns the projected u."""

@@ -713,6 +713,28 @@ void oracle_project_u(const oracle_problem *p, const double *u, const double *ma
     free(phi); free(wr); free(un); free(dphi);
 }
 
+/* The illumination of Eq. 8's closing remark: out(r) = sum over every frame
+ * (peak m, scan j) of |P_m(r - s_j)|^2 where r - s_j lies in the frame,
+ * on the object grid [n1][n2] (overwritten).  The reconstruction's final
+ * threshold sets the density to zero where this is small. */
+void oracle_illumination(const oracle_problem *p, const double *probe, double *out)
+{
+    int m = p->m;
+    long npix = (long)p->n1 * p->n2, mm = (long)m * m;
+    for (long r = 0; r < npix; ++r) out[r] = 0.0;
+    for (int mpk = 0; mpk < p->npeaks; ++mpk) {
+        const double *P = probe + (p->probe_per_peak ? (long)mpk * 2 * mm : 0);
+        for (int j = 0; j < p->nscan; ++j)
+            for (int k0 = 0; k0 < m; ++k0)
+                for (int k1 = 0; k1 < m; ++k1) {
+                    int r0 = p->scan[2 * j] + k0, r1 = p->scan[2 * j + 1] + k1;
+                    if (r0 < 0 || r0 >= p->n1 || r1 < 0 || r1 >= p->n2) continue;
+                    long kk = (long)k0 * m + k1;
+                    out[(long)r0 * p->n2 + r1] += P[2 * kk] * P[2 * kk] + P[2 * kk + 1] * P[2 * kk + 1];
+                }
+    }
+}
+
 int oracle_max_threads(void)
 {
 #ifdef _OPENMP

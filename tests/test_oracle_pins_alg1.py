@@ -150,3 +150,25 @@ def test_adam_epoch_of_minibatches_lowers_the_loss(oracle_mod):
     assert alpha_t[0] == math.log(alpha[0])
     np.testing.assert_array_equal(chi[0], chi0[0])
     assert opt.t.value == -(-spec.nframes // 5)
+
+
+def test_illumination_closed_forms(oracle_mod):
+    """A constant probe of amplitude c over a scan that tiles the grid once
+    gives c^2 per peak everywhere; a single frame gives |P|^2 itself, cut by
+    the grid edge; per-peak probes add up."""
+    D, m = 2, 4
+    G = np.eye(3)[:D]
+    scan = np.array([[0, 0], [0, 4], [4, 0], [4, 4]], np.int32)
+    p = oracle_mod.OracleProblem(8, 8, 3, D, m, scan, G)
+    ill = p.illumination(np.full((m, m), 1.5 + 2.0j))
+    np.testing.assert_allclose(ill, D * 6.25 * np.ones((8, 8)), rtol=1e-14)
+    rng = np.random.default_rng(9)
+    P = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
+    one = oracle_mod.OracleProblem(6, 7, 3, 1, m, np.array([[3, -1]], np.int32), G[:1])
+    ill = one.illumination(P)
+    ref = np.zeros((6, 7))
+    ref[3:6, 0:3] = np.abs(P[0:3, 1:4]) ** 2
+    np.testing.assert_allclose(ill, ref, rtol=1e-14, atol=0)
+    pp = oracle_mod.OracleProblem(8, 8, 3, D, m, scan, G, probe_per_peak=True)
+    P2 = np.stack([np.full((m, m), 1.0 + 0j), np.full((m, m), 2.0 + 0j)])
+    np.testing.assert_allclose(pp.illumination(P2), 5.0 * np.ones((8, 8)), rtol=1e-14)
