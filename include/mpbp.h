@@ -254,6 +254,12 @@ mpbp_status mpbp_adam_set_state(mpbp_ctx *ctx, const float *m_chi, const float *
                                 const float *m_u, const float *v_u, const double *m_alpha,
                                 const double *v_alpha, void *stream);
 
+/* The illumination behind the final threshold of the reconstruction (the
+ * remark after Eq. 8: the density is set to zero where the probe did not
+ * illuminate the object): out (dev [n1][n2], overwritten) = sum over every
+ * frame (peak m, scan j) of |P_m(r - s_j)|^2.  Needs the probe. */
+mpbp_status mpbp_illumination(mpbp_ctx *ctx, float *out, void *stream);
+
 /* W^{-1} of Eq. 9: 2-D phase unwrapping of D maps (dev [D][n1][n2], the
  * context's grid, values in [-pi, pi)) into out (dev, same shape; may be the
  * input), inside mask (dev [n1][n2], nonzero = inside, or NULL).  The method

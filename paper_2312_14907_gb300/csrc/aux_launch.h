@@ -47,6 +47,16 @@ struct AdamArgs {
 cudaError_t launch_adam_prep(const AdamArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_adam_update(const AdamArgs& a, int num_sms, cudaStream_t s);
 
+// illumination map: sum over frames of |P_m(r - s_j)|^2 (mpbp_alg1.cu)
+struct IllumArgs {
+  const cf* probe;       // [Dp][M][M]
+  const int2* scan;      // [J]
+  float* out;            // [n1][n2], zeroed before the launch
+  int nframes, J, m, n1, n2;
+  long long probe_stride;   // M*M per peak, or 0
+};
+cudaError_t launch_illumination(const IllumArgs& a, int num_sms, cudaStream_t s);
+
 cudaError_t launch_object_build(const ObjectArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_frame_transpose(const float* in, float* out, long long nframes, int m,
                                    bool take_sqrt, cudaStream_t s);

@@ -84,3 +84,34 @@ cudaError_t launch_adam_update(const AdamArgs& a, int num_sms, cudaStream_t s) {
 }
 
 }  // namespace mpbp
+
+namespace mpbp {
+
+namespace {
+
+// one thread per (frame, frame pixel): out(s_j + k) += |P_m(k)|^2
+__global__ void illumination_kernel(IllumArgs a) {
+  const long long mm = (long long)a.m * a.m;
+  const long long n = (long long)a.nframes * mm;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long f = i / mm, k = i - f * mm;
+    const int mk = (int)(f / a.J), j = (int)(f - (long long)mk * a.J);
+    const int k0 = (int)(k / a.m), k1 = (int)(k - (long long)k0 * a.m);
+    const int r0 = a.scan[j].x + k0, r1 = a.scan[j].y + k1;
+    if (r0 < 0 || r0 >= a.n1 || r1 < 0 || r1 >= a.n2) continue;
+    const float2 P = reinterpret_cast<const float2*>(a.probe)[mk * a.probe_stride + k];
+    atomicAdd(a.out + (long long)r0 * a.n2 + r1, P.x * P.x + P.y * P.y);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_illumination(const IllumArgs& a, int num_sms, cudaStream_t s) {
+  const long long n = (long long)a.nframes * a.m * a.m;
+  const long long b = (n + 255) / 256;
+  illumination_kernel<<<(int)(b < num_sms * 16 ? b : num_sms * 16), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace mpbp

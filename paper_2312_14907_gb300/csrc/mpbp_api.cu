@@ -1082,6 +1082,25 @@ mpbp_status mpbp_project_displacement(mpbp_ctx* c, float* u, const float* mask, 
   return MPBP_OK;
 }
 
+mpbp_status mpbp_illumination(mpbp_ctx* c, float* out, void* stream) {
+  if (!c || !out) return fail(c, MPBP_ERR_INVALID_ARG, "null argument");
+  if (!c->has_probe) return fail(c, MPBP_ERR_NO_DATA, "probe not set");
+  cudaStream_t s = S(stream);
+  MPBP_CUDA(c, cudaMemsetAsync(out, 0, sizeof(float) * c->npix, s));
+  IllumArgs a{};
+  a.probe = c->probe;
+  a.scan = c->scan;
+  a.out = out;
+  a.nframes = (int)c->nframes;
+  a.J = c->J;
+  a.m = c->M;
+  a.n1 = c->n1;
+  a.n2 = c->n2;
+  a.probe_stride = c->probe_per_peak ? (long long)c->M * c->M : 0;
+  MPBP_CUDA(c, launch_illumination(a, c->num_sms, s));
+  return MPBP_OK;
+}
+
 mpbp_status mpbp_step_capture(mpbp_ctx* c, float* rho, float* u, float* alpha, mpbp_step_state* st) {
   if (!c || !rho || !u || !alpha || !st) return fail(c, MPBP_ERR_INVALID_ARG, "null argument");
   if (!c->has_probe || !c->has_data) return fail(c, MPBP_ERR_NO_DATA, "probe or data not set");

@@ -79,7 +79,8 @@ EXPORTS = ["mpbp_status_string", "mpbp_create", "mpbp_destroy", "mpbp_last_error
            "mpbp_set_batch_schedule", "mpbp_autotune", "mpbp_autotune_batched",
            "mpbp_set_precision", "mpbp_step_capture", "mpbp_step_replay",
            "mpbp_adam_init", "mpbp_adam_step", "mpbp_adam_get_state", "mpbp_adam_set_state",
-           "mpbp_loss_grad_phases", "mpbp_unwrap_phases", "mpbp_project_displacement"]
+           "mpbp_loss_grad_phases", "mpbp_unwrap_phases", "mpbp_project_displacement",
+           "mpbp_illumination"]
 
 PRECISION_FP32 = 0        # FFTs on the CUDA cores
 PRECISION_TC_SPLIT16 = 1  # dense DFT matrices on the tensor cores, split FP16
@@ -144,6 +145,8 @@ def load(build_if_missing=True):
     lib.mpbp_adam_set_state.restype = st
     lib.mpbp_loss_grad_phases.argtypes = [V, V, V, V, V, I32, V, V, V, V, V]
     lib.mpbp_loss_grad_phases.restype = st
+    lib.mpbp_illumination.argtypes = [V, V, V]
+    lib.mpbp_illumination.restype = st
     lib.mpbp_unwrap_phases.argtypes = [V, V, V, V, V]
     lib.mpbp_unwrap_phases.restype = st
     lib.mpbp_project_displacement.argtypes = [V, V, V, V]
@@ -366,6 +369,12 @@ class Problem:
                                                     nfr, _p(loss), _p(g_rho), _p(g_phi), _p(g_alpha),
                                                     _stream()), "mpbp_loss_grad_phases")
         return loss, g_rho, g_phi, g_alpha
+
+    def illumination(self):
+        """sum over frames of |P_m(r - s_j)|^2 on the object grid (mpbp_illumination)."""
+        out = torch.empty(self.shapes["rho"], dtype=torch.float32, device="cuda")
+        self._check(self._lib.mpbp_illumination(self._h, _p(out), _stream()), "mpbp_illumination")
+        return out
 
     def unwrap_phases(self, wrapped, mask=None, out=None):
         """2-D unwrapping of D phase maps [D][n1][n2] (mpbp_unwrap_phases)."""

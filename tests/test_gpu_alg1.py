@@ -194,3 +194,18 @@ def test_concurrent_unwrapped_iteration_lowers_the_loss():
     again = p.project_displacement(u.clone(), md)
     assert rel_l2(again.cpu().numpy(), u.cpu().numpy()) <= 1e-6
     p.sync_status()
+
+
+def test_illumination_map_matches_oracle():
+    """The map behind the final threshold, with frames cut by the grid edge
+    and one probe per peak."""
+    spec, scan = custom_spec(90, 32, 5, 16, npeaks=3, offset=-9, probe_per_peak=True)
+    rng = np.random.default_rng(12)
+    probe = (rng.standard_normal((3, 32, 32)) + 1j * rng.standard_normal((3, 32, 32))).astype(np.complex64)
+    case = Case(spec, scan=scan, probe=probe, state="perturbed")
+    p = _problem(case)
+    got = p.illumination().cpu().numpy()
+    ref = case.oracle.illumination(case.probe)
+    assert rel_l2(got, ref) <= 1e-6
+    assert np.all(got[ref == 0] == 0)
+    p.sync_status()
