@@ -103,6 +103,10 @@ typedef struct {
   int32_t launches_loss_grad; /* kernels + memsets enqueued by mpbp_loss_grad  */
   int32_t launches_step;      /* kernels + memsets enqueued by mpbp_step       */
   int32_t precision;          /* MPBP_PRECISION_* of the gradient evaluations */
+  int32_t tile_copies;        /* FFT kernels that take their inputs by TMA tile and
+                                 bulk copies: bit 0 the gradient kernel, bit 1 the
+                                 forward kernel (none when a row of O is not a
+                                 multiple of 16 bytes, i.e. odd n2: cp.async)  */
 } mpbp_info;
 
 /* Arithmetic of the 2-D DFTs (F of Eq. 2 and its adjoint in the gradient). */

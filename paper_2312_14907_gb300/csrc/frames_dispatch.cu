@@ -8,11 +8,11 @@ bool frames_prepare_m16(FrameKernelInfo*);
 bool frames_prepare_m32(FrameKernelInfo*);
 bool frames_prepare_m64(FrameKernelInfo*);
 bool frames_prepare_m128(FrameKernelInfo*);
-cudaError_t frames_launch_m8(const FrameArgs&, int, bool, cudaStream_t);
-cudaError_t frames_launch_m16(const FrameArgs&, int, bool, cudaStream_t);
-cudaError_t frames_launch_m32(const FrameArgs&, int, bool, cudaStream_t);
-cudaError_t frames_launch_m64(const FrameArgs&, int, bool, cudaStream_t);
-cudaError_t frames_launch_m128(const FrameArgs&, int, bool, cudaStream_t);
+cudaError_t frames_launch_m8(const FrameArgs&, int, bool, cudaStream_t, const TmaMap*);
+cudaError_t frames_launch_m16(const FrameArgs&, int, bool, cudaStream_t, const TmaMap*);
+cudaError_t frames_launch_m32(const FrameArgs&, int, bool, cudaStream_t, const TmaMap*);
+cudaError_t frames_launch_m64(const FrameArgs&, int, bool, cudaStream_t, const TmaMap*);
+cudaError_t frames_launch_m128(const FrameArgs&, int, bool, cudaStream_t, const TmaMap*);
 cudaError_t frames_launch_raw_m32(const FrameArgs&, int, cudaStream_t);
 cudaError_t frames_launch_raw_m64(const FrameArgs&, int, cudaStream_t);
 cudaError_t frames_launch_raw_m128(const FrameArgs&, int, cudaStream_t);
@@ -28,13 +28,13 @@ bool frames_prepare(int m, FrameKernelInfo* info) {
   }
 }
 
-cudaError_t frames_launch(int m, const FrameArgs& a, int grid, bool forward, cudaStream_t s) {
+cudaError_t frames_launch(int m, const FrameArgs& a, int grid, bool forward, cudaStream_t s, const TmaMap* tm) {
   switch (m) {
-    case 8: return frames_launch_m8(a, grid, forward, s);
-    case 16: return frames_launch_m16(a, grid, forward, s);
-    case 32: return frames_launch_m32(a, grid, forward, s);
-    case 64: return frames_launch_m64(a, grid, forward, s);
-    case 128: return frames_launch_m128(a, grid, forward, s);
+    case 8: return frames_launch_m8(a, grid, forward, s, tm);
+    case 16: return frames_launch_m16(a, grid, forward, s, tm);
+    case 32: return frames_launch_m32(a, grid, forward, s, tm);
+    case 64: return frames_launch_m64(a, grid, forward, s, tm);
+    case 128: return frames_launch_m128(a, grid, forward, s, tm);
     default: return cudaErrorInvalidValue;
   }
 }

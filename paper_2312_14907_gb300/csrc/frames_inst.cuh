@@ -29,55 +29,86 @@ struct UseQuads {
 template <int M, bool PAIRS = UsePairs<M>::value>
 struct FramesKernel;
 
-// T, SMEM: the loss-and-gradient kernel; TF, SMEM_F: the forward and the
-// raw-data kernels
+// The kernels of one frame side: loss and gradient, forward, raw-data
+// gradient; the first two also as tile-copy (TMA) instances where the layout
+// has one (tile width > 0).
+struct KernelShape {
+  void (*fn)(const FrameArgs, const TmaMap);
+  int threads;
+  int smem;
+};
+
 template <int M>
 struct FramesKernel<M, false> {
   using C = T1Cfg<M>;
-  static constexpr int T = C::T, SMEM = C::SMEM, NG = C::NG;
-  static constexpr int TF = T, SMEM_F = SMEM;
-  static auto fn(bool fwd) { return fwd ? frames_t1<M, true> : frames_t1<M, false>; }
+  static constexpr int NG = C::NG;
+  static constexpr int kTileGrad = 0, kTileFwd = 0;
+  static KernelShape grad(bool) { return {frames_t1<M, false>, C::T, C::SMEM}; }
+  static KernelShape fwd(bool) { return {frames_t1<M, true>, C::T, C::SMEM}; }
   static constexpr bool kRaw = false;
-  static auto fn_raw() { return frames_t1<M, false>; }
+  static KernelShape raw() { return grad(false); }
 };
 
 template <int M>
 struct FramesKernel<M, true> {
   using C = T2Cfg<M>;
   static constexpr bool kQuads = UseQuads<M>::value;
-  using GC = std::conditional_t<kQuads, T4Cfg<M>, T2Cfg<M>>;
-  static constexpr int T = GC::T, SMEM = GC::SMEM;
   static constexpr int NG = 1;
-  static constexpr int TF = C::T, SMEM_F = C::SMEM;
-  static auto fn(bool fwd) {
-    if constexpr (kQuads) return fwd ? frames_t2<M, true> : frames_t4<M>;
-    else return fwd ? frames_t2<M, true> : frames_t2<M, false>;
+  static constexpr int kTileFwd = C::PW;
+  static constexpr int kTileGrad = kQuads ? T4Cfg<M>::PW : (C::SWZ ? 0 : C::PW);
+  static KernelShape grad(bool tma) {
+    if constexpr (kQuads) {
+      return {tma ? frames_t4<M, true> : frames_t4<M, false>, T4Cfg<M>::T, T4Cfg<M>::SMEM};
+    } else if constexpr (C::SWZ) {
+      return {frames_t2<M, false>, C::T, C::SMEM};
+    } else {
+      return tma ? KernelShape{frames_t2<M, false, false, true>, C::T, C::SMEM_TMA}
+                 : KernelShape{frames_t2<M, false>, C::T, C::SMEM};
+    }
+  }
+  static KernelShape fwd(bool tma) {
+    return tma ? KernelShape{frames_t2<M, true, false, true>, C::T, C::SMEM_TMA}
+               : KernelShape{frames_t2<M, true>, C::T, C::SMEM};
   }
   static constexpr bool kRaw = true;
-  static auto fn_raw() { return frames_t2<M, false, true>; }
+  static KernelShape raw() { return {frames_t2<M, false, true>, C::T, C::SMEM}; }
 };
+
+inline bool set_smem(const KernelShape& k) {
+  return cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k.smem) == cudaSuccess;
+}
 
 template <int M>
 bool frames_prepare_impl(FrameKernelInfo* info) {
   using K = FramesKernel<M>;
-  cudaFuncSetAttribute(K::fn(false), cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
-  cudaFuncSetAttribute(K::fn(true), cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM_F);
-  if (K::kRaw) cudaFuncSetAttribute(K::fn_raw(), cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM_F);
-  info->threads = K::T;
-  info->smem = K::SMEM;
+  bool ok = true;
+  for (int t = 0; t < 2; ++t) ok = set_smem(K::grad(t != 0)) && set_smem(K::fwd(t != 0)) && ok;
+  if (K::kRaw) ok = set_smem(K::raw()) && ok;
+  if (!ok) return false;
+  info->threads = K::grad(false).threads;
+  info->smem = K::grad(false).smem;
   info->frames_per_block = K::NG;
-  int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, K::fn(false), K::T, K::SMEM) != cudaSuccess)
-    return false;
+  info->tile_w_grad = K::kTileGrad;
+  info->tile_w_fwd = K::kTileFwd;
+  // the schedule's blocks per SM must hold for both copy variants
+  int nb = 1 << 20;
+  for (int t = 0; t < 2; ++t) {
+    const KernelShape k = K::grad(t != 0);
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k.fn, k.threads, k.smem) != cudaSuccess) return false;
+    nb = b < nb ? b : nb;
+  }
   info->blocks_per_sm = nb;
   return nb > 0;
 }
 
 template <int M>
-cudaError_t frames_launch_impl(const FrameArgs& a, int grid, bool forward, cudaStream_t s) {
+cudaError_t frames_launch_impl(const FrameArgs& a, int grid, bool forward, cudaStream_t s, const TmaMap* tm) {
   using K = FramesKernel<M>;
-  if (forward) K::fn(true)<<<grid, K::TF, K::SMEM_F, s>>>(a);
-  else K::fn(false)<<<grid, K::T, K::SMEM, s>>>(a);
+  static const TmaMap kNone{};
+  const bool tile = tm != nullptr && (forward ? K::kTileFwd : K::kTileGrad) > 0;
+  const KernelShape k = forward ? K::fwd(tile) : K::grad(tile);
+  k.fn<<<grid, k.threads, k.smem, s>>>(a, tile ? *tm : kNone);
   return cudaGetLastError();
 }
 
@@ -86,7 +117,9 @@ template <int M>
 cudaError_t frames_launch_raw_impl(const FrameArgs& a, int grid, cudaStream_t s) {
   using K = FramesKernel<M>;
   if (!K::kRaw) return cudaErrorNotSupported;
-  K::fn_raw()<<<grid, K::TF, K::SMEM_F, s>>>(a);
+  static const TmaMap kNone{};
+  const KernelShape k = K::raw();
+  k.fn<<<grid, k.threads, k.smem, s>>>(a, kNone);
   return cudaGetLastError();
 }
 
@@ -95,8 +128,9 @@ cudaError_t frames_launch_raw_impl(const FrameArgs& a, int grid, cudaStream_t s)
 #define MPBP_DEFINE_FRAMES(M)                                                              \
   namespace mpbp {                                                                         \
   bool frames_prepare_m##M(FrameKernelInfo* info) { return frames_prepare_impl<M>(info); } \
-  cudaError_t frames_launch_m##M(const FrameArgs& a, int grid, bool forward, cudaStream_t s) { \
-    return frames_launch_impl<M>(a, grid, forward, s);                                     \
+  cudaError_t frames_launch_m##M(const FrameArgs& a, int grid, bool forward, cudaStream_t s, \
+                                 const TmaMap* tm) {                                       \
+    return frames_launch_impl<M>(a, grid, forward, s, tm);                                 \
   }                                                                                        \
   cudaError_t frames_launch_raw_m##M(const FrameArgs& a, int grid, cudaStream_t s) {       \
     return frames_launch_raw_impl<M>(a, grid, s);                                          \

@@ -1,5 +1,6 @@
 // frames_launch.h -- host entry points of the per-M fused frame kernels.
 #pragma once
+#include "bulk.cuh"
 #include "mpbp_internal.h"
 
 namespace mpbp {
@@ -9,6 +10,8 @@ struct FrameKernelInfo {
   int smem;             // dynamic shared memory per block (bytes)
   int frames_per_block; // frames in flight per block
   int blocks_per_sm;    // occupancy limit on the current device
+  int tile_w_grad;      // box width (columns) of the objects' tensor map for the
+  int tile_w_fwd;       //   gradient / forward kernels' tile copies; 0: none
 };
 
 //
@@ -53,8 +56,11 @@ cudaError_t batched_m_launch(int m, const BatchArgs& b, int grid, cudaStream_t s
 bool frames_prepare(int m, FrameKernelInfo* info);
 
 // Enqueues the fused kernel for frame side m: forward mode writes I_out,
-// otherwise loss partials and the gradient accumulator.
-cudaError_t frames_launch(int m, const FrameArgs& a, int grid, bool forward, cudaStream_t s);
+// otherwise loss partials and the gradient accumulator.  tm: the objects'
+// tensor map with the box width the kernel reports (tile_w_*), or nullptr
+// for the cp.async copies.
+cudaError_t frames_launch(int m, const FrameArgs& a, int grid, bool forward, cudaStream_t s,
+                          const TmaMap* tm = nullptr);
 
 // Raw-data gradient kernel (a.yraw: counts in their natural layout, device
 // memory; sqrt(y) written to a.aT_w).  Frame sides 32, 64, 128.

@@ -4,18 +4,19 @@
 //
 // A warp holds eight lines: lane = 8 h + (ln mod 8), so the four threads of a
 // line are lanes l, l^8, l^16, l^24 and every exchange of the line FFTs is a
-// shuffle.  The exchange buffer has no padding; the column index of row r is
-// XOR-swizzled with
-//   sw(r) = (r & 6) | 8 (bit 0 of r  XOR  bit b of r),   b = log2(M/4),
-// which keeps every 16-lane half of a warp on distinct 8-byte
-// banks for the three access patterns the kernel has:
-//   column ln, rows 4n + h    (the patch, the dec4 input of a column pass),
-//   column ln, rows Q g + t   (the blk4 output of a column pass: the rows of
-//                              the two halves differ by M/4, bit b),
-//   row ln, columns 4n + h    (the transposed dec4 input of a row pass).
-// The sqrt(y) tile [q1][q0] is staged with its 16-byte chunks XORed with
-// 2 ((q1 / Q) mod 4), so the four rows Q g + t that one warp reads at eight
-// consecutive q0 fall in different banks.
+// shuffle.  Each phase of a frame lays the shared buffers out for its own
+// access pattern (a buffer is fully consumed before the next phase writes
+// it), with paddings that keep every 16-lane half of a warp on distinct
+// 8-byte banks and every address a per-thread base plus a constant:
+//   patch     [k0][PW], PW = M + 8: column ln, rows 4n + h (the two row
+//             parities of a half-warp 8 banks apart); a tile starts at an
+//             even column, read from column s.y & 1 on
+//   transpose [r][TW] + 8 (r / (M/4)), TW = M + 2: column ln, rows Q g + t
+//             (the two halves' rows M/4 apart: 8 banks apart) and row ln,
+//             columns 4n + h (eight rows 2 banks apart)
+//   sqrt(y)   [q1][M] + 8 (q1 / Q) floats: the four rows Q g + t a warp reads
+//             at eight consecutive q0 fall in different bank octets; 16-row
+//             bands of M floats, one bulk copy each.
 #pragma once
 #include "fft_quad.cuh"
 #include "frames.cuh"
@@ -27,11 +28,19 @@ struct T4Cfg {
   static constexpr int T = 4 * M;     // threads per block (one frame)
   static constexpr int H = M / 4;     // values per thread
   static constexpr int Q = M / 8;
-  static constexpr int B = ct::ilog2(M / 4);
-  static constexpr int BUF = M * M * (int)sizeof(cf);
-  static constexpr int ABUF = M * M * (int)sizeof(float);
-  static constexpr int SMEM = BUF + ABUF;
+  static constexpr int PW = M + 8;    // patch row
+  static constexpr int TW = M + 2;    // transpose row
+  static constexpr int TB = M / 4;    // rows per transpose band (8 cf padding after each)
+  static constexpr int AB = Q;        // sqrt(y) rows per band (8 floats padding after each)
+  static constexpr int PATCH = M * PW * (int)sizeof(cf);
+  static constexpr int TRANS = (M * TW + 4 * 8) * (int)sizeof(cf);
+  static constexpr int BUF = PATCH > TRANS ? PATCH : TRANS;
+  static constexpr int ABAND = (AB * M + 8) * (int)sizeof(float);
+  static constexpr int ABUF = (M / AB) * ABAND;
+  static constexpr int SMEM = BUF + ABUF + 128;   // + alignment of the tile destination
+  static constexpr int MINB = M >= 128 ? 1 : 3;   // blocks per SM the registers must allow
   static_assert(M == 32 || M == 64 || M == 128, "four threads per line: M = 32, 64 or 128");
+  static_assert(BUF % 16 == 0 && ABAND % 16 == 0, "bulk copy alignment");
 };
 
 MPBP_DI cf xchg8(cf v) {
@@ -39,29 +48,29 @@ MPBP_DI cf xchg8(cf v) {
 }
 
 template <int M>
-MPBP_DI int t4_at(int r, int c) {
-  constexpr int B = T4Cfg<M>::B;
-  return r * M + (c ^ ((r & 6) | (((r ^ (r >> B)) & 1) << 3)));
+MPBP_DI int t4_tr(int r, int c) {
+  using C = T4Cfg<M>;
+  return r * C::TW + (r / C::TB) * 8 + c;
 }
 
-// the frame's sqrt(y) tile, 16-byte chunks swizzled by row band
+template <int M>
+MPBP_DI int t4_amp(int q1, int q0) {
+  using C = T4Cfg<M>;
+  return q1 * M + (q1 / C::AB) * 8 + q0;
+}
+
+// the frame's sqrt(y) tile by cp.async, into the banded layout
 template <int M>
 MPBP_DI void t4_fetch_amp(const PatchSrc& q, int t, float* dst) {
   if (!q.amp) return;
-  constexpr int CH = M * M / 4, CPR = M / 4, NT = T4Cfg<M>::T, QQ = T4Cfg<M>::Q;
+  constexpr int CH = M * M / 4, CPR = M / 4, NT = T4Cfg<M>::T;
   static_assert(CH % NT == 0, "tile chunks must divide among the threads");
 #pragma unroll
   for (int i = 0; i < CH / NT; ++i) {
     const int c = t + i * NT;
     const int row = c / CPR, cc = c - row * CPR;
-    cp_async16(dst + 4 * (row * CPR + (cc ^ (2 * ((row / QQ) & 3)))), q.amp + 4 * c);
+    cp_async16(dst + t4_amp<M>(row, 4 * cc), q.amp + 4 * c);
   }
-}
-
-template <int M>
-MPBP_DI float t4_amp_at(const float* abuf, int q1, int q0) {
-  constexpr int QQ = T4Cfg<M>::Q;
-  return abuf[q1 * M + 4 * ((q0 >> 2) ^ (2 * ((q1 / QQ) & 3))) + (q0 & 3)];
 }
 
 template <int M>
@@ -69,8 +78,8 @@ struct T4Group {
   int tid;
   int ln;          // line (column or row) index
   int h, h0, h1;   // quarter of the line: h = 2 h1 + h0
-  cf* buf;         // exchange buffer [M][M], swizzled
-  float* abuf;     // sqrt(y) staging [M][M], swizzled
+  cf* buf;         // patch / transpose buffer
+  float* abuf;     // sqrt(y) staging
   MPBP_DI static T4Group make(int tid, unsigned char* smem) {
     T4Group g;
     g.tid = tid;
@@ -91,24 +100,49 @@ struct T4Group {
   }
 };
 
-template <int M>
-MPBP_DI void t4_fetch(const FrameArgs& p, const T4Group<M>& g, const FrameRef& r) {
-  const PatchSrc q = patch_src<M>(p, r);
-  sfor<0, T4Cfg<M>::H>([&](auto n_) {
-    constexpr int n = decltype(n_)::value;
-    const int k0 = 4 * n + g.h;
-    fetch_patch_elem(q, k0, g.ln, g.buf + t4_at<M>(k0, g.ln));
-  });
-  t4_fetch_amp<M>(q, g.tid, g.abuf);
+// The inputs of frame r: TMA (thread 0 issues a tile load of the patch and
+// one bulk copy per sqrt(y) band on the block's mbarrier), else cp.async by
+// every thread (not committed).  Called after the barrier that freed the
+// buffers.
+template <int M, bool TMA>
+MPBP_DI void t4_fetch(const FrameArgs& p, const T4Group<M>& g, const FrameRef& r, const BulkState& bs,
+                      const CUtensorMap* map) {
+  using C = T4Cfg<M>;
+  if constexpr (TMA) {
+    if (g.tid == 0) {
+      constexpr uint32_t kPatch = M * C::PW * (uint32_t)sizeof(cf);
+      constexpr uint32_t kBand = C::AB * M * (uint32_t)sizeof(float);
+      fence_async_smem();
+      mbar_arrive_tx(bs.bar, r.valid ? kPatch + (M / C::AB) * kBand : 0u);
+      if (r.valid) {
+        tile_load_3d(smem_addr(g.buf), map, r.s.y - (r.s.y & 1), r.s.x, r.mpk, bs.bar);
+        const float* src = p.aT + (long long)r.f * M * M;
+        const uint32_t dst = smem_addr(g.abuf);
+#pragma unroll 1
+        for (int b = 0; b < M / C::AB; ++b) bulk_load(dst + b * C::ABAND, src + b * C::AB * M, kBand, bs.bar);
+      }
+    }
+  } else {
+    const PatchSrc q = patch_src<M>(p, r);
+    // a rolled loop keeps the copies' addresses out of the registers the
+    // values need (unrolled, they spill)
+#pragma unroll 2
+    for (int n = 0; n < C::H; ++n) {
+      const int k0 = 4 * n + g.h;
+      fetch_patch_elem(q, k0, g.ln, g.buf + k0 * C::PW + g.ln);
+    }
+    t4_fetch_amp<M>(q, g.tid, g.abuf);
+  }
 }
 
-// One frame's loss and gradient (inputs in flight, committed); fetches the
-// next frame's inputs as soon as their buffers are free.
-template <int M, typename AddLoss>
-MPBP_DI FrameRef t4_frame(const FrameArgs& p, const T4Group<M>& g, const FrameRef& cur, const FrameRef& nxt,
-                          AddLoss&& add_loss) {
+// One frame's loss and gradient (inputs in flight); fetches the next frame's
+// inputs as soon as their buffers are free.  TMA: a wait that runs out clears
+// bs.ok and returns at once.
+template <int M, bool TMA, typename AddLoss>
+MPBP_DI void t4_frame(const FrameArgs& p, const T4Group<M>& g, const FrameRef& cur, const FrameRef& nxt,
+                      AddLoss&& add_loss, BulkState& bs, const CUtensorMap* map) {
   using C = T4Cfg<M>;
-  constexpr int H = C::H;
+  constexpr int H = C::H, PW = C::PW;
   cf* buf = g.buf;
   const int ln = g.ln, h = g.h;
   auto x8 = [](cf v) { return xchg8(v); };
@@ -116,28 +150,36 @@ MPBP_DI FrameRef t4_frame(const FrameArgs& p, const T4Group<M>& g, const FrameRe
   const cf* P = p.probe + cur.mpk * p.probe_stride;
   const int col = cur.s.y + ln;
   const bool cok = cur.valid && col >= 0 && col < p.n2;
-  cp_async_wait_all();
-  __syncthreads();
+  if constexpr (TMA) {
+    bs.ok = bulk_wait(bs.bar, bs.parity);
+    bs.parity ^= 1u;
+    if (!bs.ok) return;
+  } else {
+    cp_async_wait_all();
+    __syncthreads();
+  }
+  const int dlt = TMA ? (cur.s.y & 1) : 0;   // a tile starts at an even column
 
   // A2: column ln, rows 4n + h
   cf v[H];
   sfor<0, H>([&](auto n_) {
     constexpr int n = decltype(n_)::value;
     const int k0 = 4 * n + h;
-    v[n] = cmul(ldg_cf(P + k0 * M + ln), buf[t4_at<M>(k0, ln)]);
+    v[n] = cmul(ldg_cf(P + k0 * M + ln), buf[k0 * PW + ln + dlt]);
   });
 
-  // A3: columns, transpose, rows
+  // A3: columns, transpose, rows; the barrier orders the patch reads above
+  // before the transpose writes of other threads
   fft_quad_dec_to_blk<M>(v, g.h0, g.h1, x8, x16);
-  __syncwarp();   // the other three threads of the line read the rows this thread writes
+  __syncthreads();
   sfor<0, H>([&](auto i_) {
     constexpr int i = decltype(i_)::value;
-    buf[t4_at<M>(g.blk(i), ln)] = v[i];
+    buf[t4_tr<M>(g.blk(i), ln)] = v[i];
   });
   __syncthreads();
   sfor<0, H>([&](auto n_) {
     constexpr int n = decltype(n_)::value;
-    v[n] = buf[t4_at<M>(ln, 4 * n + h)];
+    v[n] = buf[t4_tr<M>(ln, 4 * n + h)];
   });
   fft_quad_dec_to_blk<M>(v, g.h0, g.h1, x8, x16);
   // row ln: Psi[ln][blk(i)] in slot i
@@ -149,7 +191,7 @@ MPBP_DI FrameRef t4_frame(const FrameArgs& p, const T4Group<M>& g, const FrameRe
     constexpr int i = decltype(i_)::value;
     const int q1 = g.blk(i);
     const float bv = b ? b[q1 * M + ln] : 0.0f;
-    v[i] = residual(v[i], t4_amp_at<M>(g.abuf, q1, ln), bv, fl);
+    v[i] = residual(v[i], g.abuf[t4_amp<M>(q1, ln)], bv, fl);
   });
   add_loss(cur.valid ? fl : 0.0f);
 
@@ -159,57 +201,74 @@ MPBP_DI FrameRef t4_frame(const FrameArgs& p, const T4Group<M>& g, const FrameRe
   __syncthreads();
   sfor<0, H>([&](auto k_) {
     constexpr int k = decltype(k_)::value;
-    buf[t4_at<M>(ln, 4 * k + h)] = v[ct::brev<H>(k)];
+    buf[t4_tr<M>(ln, 4 * k + h)] = v[ct::brev<H>(k)];
   });
   __syncthreads();
-  const PatchSrc q = patch_src<M>(p, nxt);
-  t4_fetch_amp<M>(q, g.tid, g.abuf);   // every thread is past its residual
+  if constexpr (!TMA) t4_fetch_amp<M>(patch_src<M>(p, nxt), g.tid, g.abuf);   // every thread is past its residual
   sfor<0, H>([&](auto i_) {
     constexpr int i = decltype(i_)::value;
-    v[i] = buf[t4_at<M>(g.blk(i), ln)];
+    v[i] = buf[t4_tr<M>(g.blk(i), ln)];
   });
-  __syncthreads();
-  // the exchange buffer is free again; a rolled loop here keeps the copies'
-  // addresses out of the registers the values need (unrolled, they spill)
+  __syncthreads();   // both buffers are free
+  if constexpr (TMA) {
+    t4_fetch<M, true>(p, g, nxt, bs, map);
+  } else {
+    const PatchSrc q = patch_src<M>(p, nxt);
 #pragma unroll 2
-  for (int n = 0; n < H; ++n) {
-    const int k0 = 4 * n + h;
-    fetch_patch_elem(q, k0, ln, buf + t4_at<M>(k0, ln));
+    for (int n = 0; n < H; ++n) {
+      const int k0 = 4 * n + h;
+      fetch_patch_elem(q, k0, ln, buf + k0 * PW + ln);
+    }
+    cp_async_commit();
   }
-  cp_async_commit();
   fft_quad_blk_to_dec<M>(v, g.h0, g.h1, x8, x16);   // Z[4k + h][ln] in slot brev(k)
 
   // A6 + A7
-  cf* acc = p.acc + cur.mpk * p.obj_stride;
+  // one running address and row, 4 rows a step
+  int row = cur.s.x + h;
+  cf* a = p.acc + cur.mpk * p.obj_stride + (long long)row * p.n2 + col;
+  const long long step = 4LL * p.n2;
+  const unsigned n1 = (unsigned)p.n1;
   sfor<0, H>([&](auto k_) {
     constexpr int k = decltype(k_)::value;
-    const int k0 = 4 * k + h;
-    const int row = cur.s.x + k0;
-    if (cok && row >= 0 && row < p.n1) {
-      const cf w = cmul(ldg_cf(P + k0 * M + ln), v[ct::brev<H>(k)]);
-      red_add_v2(acc + (long long)row * p.n2 + col, w);
-    }
+    const cf w = cmul(ldg_cf(P + (4 * k + h) * M + ln), v[ct::brev<H>(k)]);
+    if (cok && (unsigned)row < n1) red_add_v2(a, w);
+    a += step;
+    row += 4;
   });
-  return nxt;
 }
 
 // loss and gradient: one frame per block, frames round-robin over a
-// persistent grid
-template <int M>
-__global__ void __launch_bounds__(T4Cfg<M>::T, 1) frames_t4(FrameArgs p) {
+// persistent grid; TMA: inputs by tile and bulk copies (tm: the objects'
+// tensor map), else by cp.async
+template <int M, bool TMA>
+__global__ void __launch_bounds__(T4Cfg<M>::T, T4Cfg<M>::MINB)
+    frames_t4(const FrameArgs p, const __grid_constant__ TmaMap tm) {
   using C = T4Cfg<M>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[C::T / 32];
+  __shared__ __align__(8) uint64_t mbar;
   if (blockIdx.x == 0 && threadIdx.x == 0 && p.arrivals) *p.arrivals = 0u;
-  const T4Group<M> g = T4Group<M>::make(threadIdx.x, smem_raw);
+  unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+  const T4Group<M> g = T4Group<M>::make(threadIdx.x, smem);
+  BulkState bs{smem_addr(&mbar), 0u, true};
+  if constexpr (TMA) {
+    if (threadIdx.x == 0) mbar_init(bs.bar, 1);
+    __syncthreads();
+  }
   double lsum = 0.0;
   int it = blockIdx.x;
   FrameRef cur = frame_ref(p, it);
-  t4_fetch<M>(p, g, cur);
-  cp_async_commit();
+  t4_fetch<M, TMA>(p, g, cur, bs, &tm.map);
+  if constexpr (!TMA) cp_async_commit();
   for (; it < p.nframes; it += gridDim.x) {
     const FrameRef nxt = frame_ref(p, it + gridDim.x);
-    cur = t4_frame<M>(p, g, cur, nxt, [&](float fl) { lsum += (double)fl; });
+    t4_frame<M, TMA>(p, g, cur, nxt, [&](float fl) { lsum += (double)fl; }, bs, &tm.map);
+    if (TMA && !bs.ok) {
+      if (threadIdx.x == 0) atomicOr(p.err, kErrTimeout);
+      break;
+    }
+    cur = nxt;
   }
   cp_async_wait_all();
   const double tot = block_sum_d<C::T>(lsum, red);

@@ -32,6 +32,9 @@ struct mpbp_ctx {
   // kernel schedule
   FrameKernelInfo fk{};       // the gradient kernel in use
   FrameKernelInfo fk_fft{};   // the FFT kernels (forward mode always uses them)
+  // tensor maps of O for the FFT kernels' tile copies (box widths from fk_fft)
+  TmaMap tm_grad{}, tm_fwd{};
+  bool tile_grad = false, tile_fwd = false;
   int precision = MPBP_PRECISION_FP32;
   void* tc_w = nullptr;       // split DFT matrix of the tensor-core kernel
   int blocks_per_sm = 0;  // schedule in use
@@ -182,7 +185,45 @@ int frames_grid_fft(const mpbp_ctx* c, long long nframes) {
 // the gradient-mode frame kernel of the context's precision
 cudaError_t launch_frames(const mpbp_ctx* c, const FrameArgs& fa, int grid, cudaStream_t s) {
   if (c->precision == MPBP_PRECISION_TC_SPLIT16) return tc_launch(fa, c->tc_w, grid, s);
-  return frames_launch(c->M, fa, grid, false, s);
+  return frames_launch(c->M, fa, grid, false, s, c->tile_grad && fa.O == c->O ? &c->tm_grad : nullptr);
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// the driver's tensor-map encoder, looked up once through the runtime
+EncodeTiledFn encode_tiled_fn() {
+  static const EncodeTiledFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (EncodeTiledFn) nullptr;
+    }
+    return reinterpret_cast<EncodeTiledFn>(f);
+  }();
+  return fn;
+}
+
+// Tensor map of the objects O [D][n1][n2] (8-byte elements) for tiles of
+// w columns and M rows; false where the layout admits none (rows of O not a
+// multiple of 16 bytes) or the encoder is unavailable, and the kernels then
+// copy with cp.async.
+bool encode_objects_map(const mpbp_ctx* c, int w, TmaMap* out) {
+  if (w <= 0 || w > 256 || (c->n2 * sizeof(cf)) % 16 != 0 || (reinterpret_cast<uintptr_t>(c->O) & 15) != 0)
+    return false;
+  const EncodeTiledFn fn = encode_tiled_fn();
+  if (!fn) return false;
+  const cuuint64_t dim[3] = {(cuuint64_t)c->n2, (cuuint64_t)c->n1, (cuuint64_t)c->D};
+  const cuuint64_t stride[2] = {(cuuint64_t)c->n2 * sizeof(cf), (cuuint64_t)c->npix * sizeof(cf)};
+  const cuuint32_t box[3] = {(cuuint32_t)w, (cuuint32_t)c->M, 1u};
+  const cuuint32_t estride[3] = {1u, 1u, 1u};
+  return fn(&out->map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, c->O, dim, stride, box, estride,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 FrameArgs frame_args(mpbp_ctx* c, const int* frames, int nframes) {
@@ -402,6 +443,8 @@ mpbp_status mpbp_create(const mpbp_problem* pr, mpbp_ctx** out) {
   c->g_alpha_base = reinterpret_cast<double*>(b + oGAB);
   c->err = reinterpret_cast<int*>(b + oErr);
   c->arrivals = reinterpret_cast<unsigned*>(b + oArr);
+  c->tile_grad = encode_objects_map(c, c->fk_fft.tile_w_grad, &c->tm_grad);
+  c->tile_fwd = encode_objects_map(c, c->fk_fft.tile_w_fwd, &c->tm_fwd);
 
   std::vector<int2> sc(c->J);
   for (int j = 0; j < c->J; ++j) sc[j] = make_int2(pr->scan[2 * j], pr->scan[2 * j + 1]);
@@ -457,6 +500,7 @@ mpbp_status mpbp_get_info(const mpbp_ctx* c, mpbp_info* info) {
   info->launches_loss_grad = 3;  // object build, frames, gradient assembly + reductions
   info->launches_step = 4;       // + update
   info->precision = c->precision;
+  info->tile_copies = (c->tile_grad ? 1 : 0) | (c->tile_fwd ? 2 : 0);
   return MPBP_OK;
 }
 
@@ -554,7 +598,8 @@ mpbp_status mpbp_forward(mpbp_ctx* c, const float* rho, const float* u, const fl
   FrameArgs fa = frame_args(c, nullptr, (int)c->nframes);
   fa.I_out = I_out;
   fa.arrivals = nullptr;
-  MPBP_CUDA(c, frames_launch(c->M, fa, frames_grid_fft(c, c->nframes), true, S(stream)));
+  MPBP_CUDA(c, frames_launch(c->M, fa, frames_grid_fft(c, c->nframes), true, S(stream),
+                             c->tile_fwd ? &c->tm_fwd : nullptr));
   return MPBP_OK;
 }
 

@@ -68,7 +68,7 @@ class Info(ctypes.Structure):
                 ("frames_block", ctypes.c_int32), ("frames_smem", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("num_sms", ctypes.c_int32),
                 ("launches_loss_grad", ctypes.c_int32), ("launches_step", ctypes.c_int32),
-                ("precision", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("tile_copies", ctypes.c_int32)]
 
 
 EXPORTS = ["mpbp_status_string", "mpbp_create", "mpbp_destroy", "mpbp_last_error",

@@ -59,13 +59,14 @@ def rel_l2(a, b):
     return np.linalg.norm((a - b).ravel()) / (nb if nb > 0 else 1.0)
 
 
-def custom_spec(n, m, side, step, npeaks=3, ncomp=3, seed=0, offset=None, probe_per_peak=False):
-    """A problem of chosen size; offset (the first scan position) may be negative."""
+def custom_spec(n, m, side, step, npeaks=3, ncomp=3, seed=0, offset=None, probe_per_peak=False, n2=None):
+    """A problem of chosen size (n x n, or n x n2); offset (the first scan
+    position) may be negative."""
     G = (synth.AXIS_PEAKS if npeaks <= 3 else synth.PAPER_PEAKS)[:npeaks, :ncomp].copy()
     if ncomp < 3 and npeaks <= 3:
         G = np.array([[1.0, 0.0], [0.0, 1.0], [0.6, 0.8]])[:npeaks, :ncomp]
     sig, quad = 6.0 * m / 32, 0.01 * (32.0 / m) ** 2
-    spec = synth.ProblemSpec("custom-%d-m%d" % (n, m), n, n, ncomp, npeaks, m, side, step, G,
+    spec = synth.ProblemSpec("custom-%d-m%d" % (n, m), n, n if n2 is None else n2, ncomp, npeaks, m, side, step, G,
                              synth.SEED_BASE + 500 + seed, bumps=6, straight=2, curved=1,
                              sigma=sig, quad=quad, probe_per_peak=probe_per_peak)
     if offset is not None:

@@ -93,6 +93,23 @@ def test_random_probe_per_peak_and_background(m):
     assert rel_l2(I, I_ref) <= 1e-5
 
 
+@pytest.mark.parametrize("m", [32, 64, 128])
+def test_tile_and_plain_copies_match_oracle(m):
+    """Objects whose rows are a multiple of 16 bytes (even n2) reach the FFT
+    kernels by TMA tile and bulk copies, odd n2 by cp.async; both layouts,
+    with odd and negative scan offsets, against the oracle."""
+    for n2, tiles in ((2 * m + 8, 3), (2 * m + 7, 0)):
+        spec, scan = custom_spec(2 * m + 6, m, 3, m // 2 + 1, npeaks=2, offset=-3, n2=n2)
+        case = Case(spec, scan=scan, state="perturbed")
+        p, x = _gpu(case)
+        assert p.info()["tile_copies"] == tiles, (n2, p.info())
+        _check_loss_grad(case, p.loss_grad(*x))
+        I = p.forward(*x).cpu().numpy()
+        I_ref = case.oracle.forward(case.rho, case.u, case.alpha, case.probe)
+        assert rel_l2(I, I_ref) <= 1e-5
+        p.sync_status()
+
+
 def test_frame_subset_matches_oracle():
     spec, scan = custom_spec(64, 32, 6, 6, npeaks=3, offset=0)
     case = Case(spec, scan=scan, state="perturbed")
