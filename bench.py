@@ -283,7 +283,7 @@ def run_gpu(args):
         "hbm_roofline": {"bytes_per_frame": bpf, "achieved_gbs": value * bpf / 1e9 / world,
                          "peak_gbs": pk["hbm_gbs"], "frac": value * bpf / 1e9 / world / pk["hbm_gbs"],
                          "peak_src": pk["src"]},
-        "roofline": {"bound": "alu", "kernel": "frames_t2<64, false> (fused per-frame kernel)",
+        "roofline": {"bound": "alu", "kernel": "frames_t2<64, gradient, tile copies> (fused per-frame kernel)",
                      "achieved": achieved_tf, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
                      "frac": achieved_tf / pk["fp32_tflops"], "traffic": traffic,
                      "kernel_ms": kavg_ms, "kernel_share_of_step": kavg_ms / eager_ms,
@@ -398,7 +398,7 @@ def kernel_revision():
     import hashlib
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2312_14907_gb300", "csrc")
-    for name in ("frames.cuh", "fft_reg.cuh", "fft_pair.cuh", "frames_m64.cu"):
+    for name in ("frames.cuh", "bulk.cuh", "frames_inst.cuh", "fft_reg.cuh", "fft_pair.cuh", "frames_m64.cu"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]
