@@ -31,15 +31,13 @@ MPBP_DI void fft_pair_dec_to_blk(cf (&v)[L / 2], int h, Xchg&& xchg) {
   sfor<0, Q>([&](auto i_) {
     constexpr int i = decltype(i_)::value;
     constexpr int lo_slot = ct::brev<H>(i), hi_slot = ct::brev<H>(Q + i);
-    cf mine = csel(hi, v[hi_slot], v[lo_slot]);   // Y_h[Q h + i]
-    cf send = csel(hi, v[lo_slot], v[hi_slot]);   // what the partner needs
-    cf recv = xchg(send);
-    cf A = csel(hi, recv, mine);                  // Y_0[Q h + i]
-    cf B = csel(hi, mine, recv);                  // Y_1[Q h + i]
-    cf Bw = twmul<i, L>(B);
-    Bw = csel(hi, cf{Bw.y, -Bw.x}, Bw);
-    out[i] = cadd(A, Bw);
-    out[Q + i] = csub(A, Bw);
+    const cf recv = xchg(csel(hi, v[lo_slot], v[hi_slot]));   // Y_{1-h}[Q h + i]
+    cf a = csel(hi, recv, v[lo_slot]);                          // Y_0[Q h + i]
+    // (-i)^h Y_1[Q h + i]: the twiddle W_L^{Q h + i} = (-i)^h W_L^i
+    cf b = cf{hi ? v[hi_slot].y : recv.x, hi ? -v[hi_slot].x : recv.y};
+    bfly<i, L>(a, b);                                           // a + W_L^i b, a - W_L^i b
+    out[i] = a;
+    out[Q + i] = b;
   });
   sfor<0, H>([&](auto i_) { v[decltype(i_)::value] = out[decltype(i_)::value]; });
 }
@@ -51,14 +49,11 @@ MPBP_DI void fft_pair_blk_to_dec(cf (&v)[L / 2], int h, Xchg&& xchg) {
   const bool hi = h != 0;
   sfor<0, Q>([&](auto i_) {
     constexpr int i = decltype(i_)::value;
-    cf a = cadd(v[i], v[Q + i]);                  // x[n] + x[n+H], n = Q h + i
-    cf b = twmul<i, L>(csub(v[i], v[Q + i]));     // (x[n] - x[n+H]) W^n
-    b = csel(hi, cf{b.y, -b.x}, b);
-    cf send = csel(hi, a, b);
-    cf keep = csel(hi, b, a);
-    cf recv = xchg(send);
-    w[i] = csel(hi, recv, keep);
-    w[Q + i] = csel(hi, keep, recv);
+    const cf a = cadd(v[i], v[Q + i]);                    // x[n] + x[n+H], n = Q h + i
+    const cf b = twmul<i, L>(csub(v[i], v[Q + i]));       // (x[n] - x[n+H]) W_L^i; times (-i)^h below
+    const cf recv = xchg(csel(hi, a, b));                 // the low thread keeps the sums
+    w[i] = csel(hi, recv, a);
+    w[Q + i] = cf{hi ? b.y : recv.x, hi ? -b.x : recv.y};
   });
   fft_line<H>(w);
   sfor<0, H>([&](auto i_) { v[decltype(i_)::value] = w[decltype(i_)::value]; });

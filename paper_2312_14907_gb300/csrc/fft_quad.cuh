@@ -17,11 +17,11 @@
 
 namespace mpbp {
 
-// W_8^g, g in 0..3
-MPBP_DI cf w8_pow(int g) {
-  const float re = g == 0 ? 1.0f : g == 1 ? ct::Tw<1, 8>::re : g == 2 ? ct::Tw<2, 8>::re : ct::Tw<3, 8>::re;
-  const float im = g == 0 ? 0.0f : g == 1 ? ct::Tw<1, 8>::im : g == 2 ? ct::Tw<2, 8>::im : ct::Tw<3, 8>::im;
-  return cf{re, im};
+// W_8^h1 for h1 in {0, 1}: the per-thread factor of the cross-thread twiddle
+// W_L^{Q g + t} = W_L^t W_8^h1 (-i)^h0 (g = 2 h0 + h1; (-i)^h0 is folded into
+// the selects)
+MPBP_DI cf w8_h1(int h1) {
+  return cf{h1 ? ct::Tw<1, 8>::re : 1.0f, h1 ? ct::Tw<1, 8>::im : 0.0f};
 }
 
 template <int L, typename X8, typename X16>
@@ -29,18 +29,17 @@ MPBP_DI void fft_quad_dec_to_blk(cf (&v)[L / 4], int h0, int h1, X8&& xchg8, X16
   constexpr int Q = L / 8;
   fft_pair_dec_to_blk<L / 2>(v, h1, xchg16);   // E_h0[k] for k = Q h1 + i, L/4 + Q h1 + i
   const bool hi = h0 != 0;
-  const cf cg = w8_pow(2 * h0 + h1);
+  const cf c1 = w8_h1(h1);
   cf out[L / 4];
   sfor<0, Q>([&](auto t_) {
     constexpr int t = decltype(t_)::value;
-    const cf mine = csel(hi, v[Q + t], v[t]);   // E_h0[Q g + t]
-    const cf send = csel(hi, v[t], v[Q + t]);   // what the partner keeps
-    const cf recv = xchg8(send);
-    const cf e0 = csel(hi, recv, mine);
-    const cf e1 = csel(hi, mine, recv);
-    const cf tw = cmul(twmul<t, L>(e1), cg);    // W_L^{Q g + t} E_1
-    out[t] = cadd(e0, tw);
-    out[Q + t] = csub(e0, tw);
+    const cf recv = xchg8(csel(hi, v[t], v[Q + t]));   // E_{1-h0}[Q g + t]
+    cf a = csel(hi, recv, v[t]);                        // E_0[Q g + t]
+    cf b = cf{hi ? v[Q + t].y : recv.x, hi ? -v[Q + t].x : recv.y};   // (-i)^h0 E_1[Q g + t]
+    b = cmul(b, c1);
+    bfly<t, L>(a, b);                                   // a + W_L^t b, a - W_L^t b
+    out[t] = a;
+    out[Q + t] = b;
   });
   sfor<0, L / 4>([&](auto i_) { v[decltype(i_)::value] = out[decltype(i_)::value]; });
 }
@@ -49,16 +48,15 @@ template <int L, typename X8, typename X16>
 MPBP_DI void fft_quad_blk_to_dec(cf (&v)[L / 4], int h0, int h1, X8&& xchg8, X16&& xchg16) {
   constexpr int Q = L / 8;
   const bool hi = h0 != 0;
-  const cf cg = w8_pow(2 * h0 + h1);
+  const cf c1 = w8_h1(h1);
   cf w[L / 4];
   sfor<0, Q>([&](auto t_) {
     constexpr int t = decltype(t_)::value;
-    const cf a = cadd(v[t], v[Q + t]);                          // even outputs
-    const cf b = cmul(twmul<t, L>(csub(v[t], v[Q + t])), cg);   // odd outputs, W_L^{Q g + t}
-    const cf keep = csel(hi, b, a);
-    const cf recv = xchg8(csel(hi, a, b));
-    w[t] = csel(hi, recv, keep);
-    w[Q + t] = csel(hi, keep, recv);
+    const cf a = cadd(v[t], v[Q + t]);                                  // even outputs
+    const cf b = cmul(twmul<t, L>(csub(v[t], v[Q + t])), c1);          // odd: W_L^t W_8^h1; (-i)^h0 below
+    const cf recv = xchg8(csel(hi, a, b));                              // the h0 = 0 thread keeps the sums
+    w[t] = csel(hi, recv, a);
+    w[Q + t] = cf{hi ? b.y : recv.x, hi ? -b.x : recv.y};
   });
   fft_pair_blk_to_dec<L / 2>(w, h1, xchg16);
   sfor<0, L / 4>([&](auto i_) { v[decltype(i_)::value] = w[decltype(i_)::value]; });
