@@ -81,6 +81,8 @@ __global__ void frame_transpose_kernel(const float* __restrict__ in, float* __re
 // reduced quantity, partials read in a fixed order, so the result does not
 // depend on which block finishes last)
 // ----------------------------------------------------------------------------
+constexpr int kReduceLoads = 20;   // partials per lane issued together (up to 640 blocks)
+
 template <int T>
 __device__ void final_reduce(const ReduceArgs& a) {
   __shared__ double vals[kMaxPeaks + 3];
@@ -90,7 +92,19 @@ __device__ void final_reduce(const ReduceArgs& a) {
     // per-block partials: column D + 2 is the loss, columns 0..D+1 as named
     const int col = q == 0 ? a.D + 2 : q - 1;
     double v = 0.0;
-    for (int i = lane; i < a.n_part; i += 32) v += __ldcg(a.part + (long long)i * (a.D + 3) + col);
+    if (a.n_part <= 32 * kReduceLoads) {
+      // every load of this lane in flight at once, summed in index order
+      double x[kReduceLoads];
+#pragma unroll
+      for (int k = 0; k < kReduceLoads; ++k) {
+        const int i = lane + 32 * k;
+        x[k] = i < a.n_part ? __ldcg(a.part + (long long)i * (a.D + 3) + col) : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < kReduceLoads; ++k) v += x[k];
+    } else {
+      for (int i = lane; i < a.n_part; i += 32) v += __ldcg(a.part + (long long)i * (a.D + 3) + col);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) vals[q] = v;
@@ -143,12 +157,21 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a, Re
   for (int m = 0; m < kMaxPeaks; ++m) ap[m] = 0.f;
   float n_rho = 0.f, n_u = 0.f;
   const long long stride = (long long)gridDim.x * blockDim.x;
+  // this block's slice of the frame kernel's loss partials (FP64), issued
+  // first: nothing below depends on them
+  double lp = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n_loss_part; i += stride)
+    lp += __ldcg(a.loss_part + i);
   float2* acc = reinterpret_cast<float2*>(a.acc);
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < a.npix; p += stride) {
+    // every load of the pixel in flight before the phase arithmetic
     const float r = a.rho[p];
     float uc[kMaxComp];
 #pragma unroll
     for (int c = 0; c < kMaxComp; ++c) uc[c] = !PHI && c < a.C ? a.u[c * a.npix + p] : 0.f;
+    float2 Am[kMaxPeaks];
+#pragma unroll
+    for (int m = 0; m < kMaxPeaks; ++m) Am[m] = m < a.D ? __ldcg(acc + m * a.npix + p) : make_float2(0.f, 0.f);
     float gr = 0.f, gphi2 = 0.f;
     float gu[kMaxComp] = {0.f, 0.f, 0.f};
 #pragma unroll
@@ -163,7 +186,7 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a, Re
           for (int c = 0; c < kMaxComp; ++c) arg = fmaf(a.pc.kpi[m][c], uc[c], arg);
           sincospif(arg, &sn, &cs);
         }
-        const float2 A = acc[m * a.npix + p];
+        const float2 A = Am[m];
         acc[m * a.npix + p] = make_float2(0.f, 0.f);
         const float Tr = fmaf(cs, A.x, -sn * A.y);
         const float Ti = fmaf(cs, A.y, sn * A.x);
@@ -194,10 +217,6 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a, Re
     n_rho = fmaf(gr, gr, n_rho);
     n_u += su;
   }
-  // this block's slice of the frame kernel's loss partials (FP64)
-  double lp = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n_loss_part; i += stride)
-    lp += __ldcg(a.loss_part + i);
   // partial sums: FP32 within the warp (a few pixels per lane), FP64 across
   // warps and blocks; one barrier for all D + 3 quantities
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
