@@ -49,7 +49,8 @@ typedef enum {
   MPBP_ERR_UNSUPPORTED = 2,  /* valid problem the kernels do not cover (M)   */
   MPBP_ERR_CUDA = 3,         /* a CUDA runtime call failed                   */
   MPBP_ERR_NONFINITE = 4,    /* the loss came out NaN or infinite            */
-  MPBP_ERR_TIMEOUT = 5,      /* a bounded wait of the tensor-core kernel ran out */
+  MPBP_ERR_TIMEOUT = 5,      /* a bounded wait on the GPU ran out (tile copies,
+                                tensor-core MMAs, grid barriers)             */
   MPBP_ERR_BOUNDS = 6,       /* a frame index outside [0, npeaks*nscan)      */
   MPBP_ERR_OOM = 7,          /* device allocation failed                     */
   MPBP_ERR_NO_DATA = 8       /* probe or measured data not set yet           */
@@ -354,6 +355,15 @@ mpbp_status mpbp_set_schedule(mpbp_ctx *ctx, int32_t blocks_per_sm);
  * table and synchronises the device.  A device error word bit from a bounded
  * wait of that kernel is reported by mpbp_sync_status as MPBP_ERR_TIMEOUT. */
 mpbp_status mpbp_set_precision(mpbp_ctx *ctx, int32_t mode);
+
+/* Test hook for the timeout path (on != 0): the FFT gradient kernels' tile-copy
+ * barriers are told to expect 16 bytes more than the copies deliver, so each
+ * block's bounded wait (0.2 s) runs out; the kernel records the event and
+ * leaves with no copy in flight, and the next mpbp_sync_status returns
+ * MPBP_ERR_TIMEOUT.  Results of calls made while it is on are meaningless.
+ * No effect on contexts whose frame kernels use cp.async copies (odd n2,
+ * M <= 16) or tensor cores.  Off by default. */
+mpbp_status mpbp_set_test_stall(mpbp_ctx *ctx, int32_t on);
 
 /* Turns on (enable != 0) or off the recording of CUDA events around every
  * launch of the fused frame kernel, on the stream it is launched on.  Off by

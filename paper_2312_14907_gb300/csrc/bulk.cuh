@@ -16,6 +16,9 @@ namespace mpbp {
 // kernel reads it from column s.y & 1 on.
 struct TmaMap {
   CUtensorMap map;
+  // bytes announced on a tile-copy barrier beyond what the copies deliver
+  // (0; > 0 only to test the bounded wait, which then runs out)
+  unsigned tx_extra;
 };
 
 constexpr unsigned long long kBulkWaitNs = 200ull * 1000 * 1000;   // 0.2 s

@@ -106,16 +106,16 @@ struct T4Group {
 // buffers.
 template <int M, bool TMA>
 MPBP_DI void t4_fetch(const FrameArgs& p, const T4Group<M>& g, const FrameRef& r, const BulkState& bs,
-                      const CUtensorMap* map) {
+                      const TmaMap* tm) {
   using C = T4Cfg<M>;
   if constexpr (TMA) {
     if (g.tid == 0) {
       constexpr uint32_t kPatch = M * C::PW * (uint32_t)sizeof(cf);
       constexpr uint32_t kBand = C::AB * M * (uint32_t)sizeof(float);
       fence_async_smem();
-      mbar_arrive_tx(bs.bar, r.valid ? kPatch + (M / C::AB) * kBand : 0u);
+      mbar_arrive_tx(bs.bar, (r.valid ? kPatch + (M / C::AB) * kBand : 0u) + tm->tx_extra);
       if (r.valid) {
-        tile_load_3d(smem_addr(g.buf), map, r.s.y - (r.s.y & 1), r.s.x, r.mpk, bs.bar);
+        tile_load_3d(smem_addr(g.buf), &tm->map, r.s.y - (r.s.y & 1), r.s.x, r.mpk, bs.bar);
         const float* src = p.aT + (long long)r.f * M * M;
         const uint32_t dst = smem_addr(g.abuf);
 #pragma unroll 1
@@ -140,7 +140,7 @@ MPBP_DI void t4_fetch(const FrameArgs& p, const T4Group<M>& g, const FrameRef& r
 // bs.ok and returns at once.
 template <int M, bool TMA, typename AddLoss>
 MPBP_DI void t4_frame(const FrameArgs& p, const T4Group<M>& g, const FrameRef& cur, const FrameRef& nxt,
-                      AddLoss&& add_loss, BulkState& bs, const CUtensorMap* map) {
+                      AddLoss&& add_loss, BulkState& bs, const TmaMap* tm) {
   using C = T4Cfg<M>;
   constexpr int H = C::H, PW = C::PW;
   cf* buf = g.buf;
@@ -211,7 +211,7 @@ MPBP_DI void t4_frame(const FrameArgs& p, const T4Group<M>& g, const FrameRef& c
   });
   __syncthreads();   // both buffers are free
   if constexpr (TMA) {
-    t4_fetch<M, true>(p, g, nxt, bs, map);
+    t4_fetch<M, true>(p, g, nxt, bs, tm);
   } else {
     const PatchSrc q = patch_src<M>(p, nxt);
 #pragma unroll 2
@@ -259,11 +259,11 @@ __global__ void __launch_bounds__(T4Cfg<M>::T, T4Cfg<M>::MINB)
   double lsum = 0.0;
   int it = blockIdx.x;
   FrameRef cur = frame_ref(p, it);
-  t4_fetch<M, TMA>(p, g, cur, bs, &tm.map);
+  t4_fetch<M, TMA>(p, g, cur, bs, &tm);
   if constexpr (!TMA) cp_async_commit();
   for (; it < p.nframes; it += gridDim.x) {
     const FrameRef nxt = frame_ref(p, it + gridDim.x);
-    t4_frame<M, TMA>(p, g, cur, nxt, [&](float fl) { lsum += (double)fl; }, bs, &tm.map);
+    t4_frame<M, TMA>(p, g, cur, nxt, [&](float fl) { lsum += (double)fl; }, bs, &tm);
     if (TMA && !bs.ok) {
       if (threadIdx.x == 0) atomicOr(p.err, kErrTimeout);
       break;

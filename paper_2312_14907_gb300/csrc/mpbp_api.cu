@@ -35,6 +35,7 @@ struct mpbp_ctx {
   // tensor maps of O for the FFT kernels' tile copies (box widths from fk_fft)
   TmaMap tm_grad{}, tm_fwd{};
   bool tile_grad = false, tile_fwd = false;
+  unsigned test_tx_extra = 0;   // mpbp_set_test_stall
   int precision = MPBP_PRECISION_FP32;
   void* tc_w = nullptr;       // split DFT matrix of the tensor-core kernel
   int blocks_per_sm = 0;  // schedule in use
@@ -185,7 +186,10 @@ int frames_grid_fft(const mpbp_ctx* c, long long nframes) {
 // the gradient-mode frame kernel of the context's precision
 cudaError_t launch_frames(const mpbp_ctx* c, const FrameArgs& fa, int grid, cudaStream_t s) {
   if (c->precision == MPBP_PRECISION_TC_SPLIT16) return tc_launch(fa, c->tc_w, grid, s);
-  return frames_launch(c->M, fa, grid, false, s, c->tile_grad && fa.O == c->O ? &c->tm_grad : nullptr);
+  if (!c->tile_grad || fa.O != c->O) return frames_launch(c->M, fa, grid, false, s, nullptr);
+  TmaMap tm = c->tm_grad;
+  tm.tx_extra = c->test_tx_extra;
+  return frames_launch(c->M, fa, grid, false, s, &tm);
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -1570,6 +1574,12 @@ mpbp_status mpbp_frames_timing_read(mpbp_ctx* c, double* total_ms, int32_t* coun
   return MPBP_OK;
 }
 
+mpbp_status mpbp_set_test_stall(mpbp_ctx* c, int32_t on) {
+  if (!c) return MPBP_ERR_INVALID_ARG;
+  c->test_tx_extra = on ? 16u : 0u;
+  return MPBP_OK;
+}
+
 mpbp_status mpbp_sync_status(mpbp_ctx* c, void* stream) {
   if (!c) return MPBP_ERR_INVALID_ARG;
   MPBP_CUDA(c, cudaStreamSynchronize(S(stream)));
@@ -1578,7 +1588,7 @@ mpbp_status mpbp_sync_status(mpbp_ctx* c, void* stream) {
   if (h) MPBP_CUDA(c, cudaMemset(c->err, 0, sizeof(int)));
   if (h & kErrBounds) return fail(c, MPBP_ERR_BOUNDS, "frame index out of range");
   if (h & kErrNonfinite) return fail(c, MPBP_ERR_NONFINITE, "non-finite loss");
-  if (h & kErrTimeout) return fail(c, MPBP_ERR_TIMEOUT, "a tensor-core wait ran out");
+  if (h & kErrTimeout) return fail(c, MPBP_ERR_TIMEOUT, "a bounded wait on the GPU ran out");
   return MPBP_OK;
 }
 

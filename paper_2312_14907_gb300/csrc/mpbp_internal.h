@@ -14,7 +14,7 @@ constexpr int kMaxComp = 3;
 // device error word bits
 constexpr int kErrBounds = 1;
 constexpr int kErrNonfinite = 2;
-constexpr int kErrTimeout = 4;     // a bounded wait on the tensor cores ran out
+constexpr int kErrTimeout = 4;     // a bounded wait on the GPU ran out
 
 // Arguments of the fused per-frame kernel (A2..A7 of the hot path).
 struct FrameArgs {

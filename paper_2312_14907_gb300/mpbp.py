@@ -80,7 +80,7 @@ EXPORTS = ["mpbp_status_string", "mpbp_create", "mpbp_destroy", "mpbp_last_error
            "mpbp_set_precision", "mpbp_step_capture", "mpbp_step_replay",
            "mpbp_adam_init", "mpbp_adam_step", "mpbp_adam_get_state", "mpbp_adam_set_state",
            "mpbp_loss_grad_phases", "mpbp_unwrap_phases", "mpbp_project_displacement",
-           "mpbp_illumination"]
+           "mpbp_illumination", "mpbp_set_test_stall"]
 
 PRECISION_FP32 = 0        # FFTs on the CUDA cores
 PRECISION_TC_SPLIT16 = 1  # dense DFT matrices on the tensor cores, split FP16
@@ -165,6 +165,8 @@ def load(build_if_missing=True):
     lib.mpbp_sync_status.restype = st
     lib.mpbp_frames_timing.argtypes = [V, I32]
     lib.mpbp_frames_timing.restype = st
+    lib.mpbp_set_test_stall.argtypes = [V, I32]
+    lib.mpbp_set_test_stall.restype = st
     lib.mpbp_frames_timing_read.argtypes = [V, P(D), P(I32)]
     lib.mpbp_frames_timing_read.restype = st
     lib.mpbp_loss_grad_noalloc.argtypes = [P(_Problem), V, V, V, V, V, V, V, V, V, V]
@@ -486,6 +488,10 @@ class Problem:
     def read_state(state):
         raw = state.cpu().numpy().tobytes()
         return StepState.from_buffer_copy(raw)
+
+    def set_test_stall(self, on=True):
+        """Test hook: the tile-copy waits of the frame kernels run out (MPBP_ERR_TIMEOUT)."""
+        self._check(self._lib.mpbp_set_test_stall(self._h, int(bool(on))), "mpbp_set_test_stall")
 
     def frames_timing(self, enable=True):
         self._check(self._lib.mpbp_frames_timing(self._h, int(bool(enable))), "mpbp_frames_timing")

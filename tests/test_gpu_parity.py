@@ -283,3 +283,27 @@ def test_batched_matches_single_problems():
                 _check_loss_grad(c, o)
     for p in probs:
         p.sync_status()
+
+
+@pytest.mark.parametrize("m", [64, 128])
+def test_tile_copy_wait_runs_out_and_reports(m):
+    """The frame kernels' waits for their tile copies are bounded: with the
+    barrier told to expect bytes that never arrive, each block gives up
+    after its time limit, the call reports MPBP_ERR_TIMEOUT, and the context
+    computes correctly again afterwards."""
+    import time
+    from paper_2312_14907_gb300 import mpbp
+    spec, scan = custom_spec(2 * m + 8, m, 3, m // 2, npeaks=2, offset=-2)
+    case = Case(spec, scan=scan, state="perturbed")
+    p, x = _gpu(case)
+    assert p.info()["tile_copies"] == 3
+    p.set_test_stall(True)
+    t0 = time.time()
+    p.loss_grad(*x)
+    with pytest.raises(mpbp.MPBPError) as e:
+        p.sync_status()
+    assert e.value.status == 5, e.value           # MPBP_ERR_TIMEOUT
+    assert time.time() - t0 < 20.0
+    p.set_test_stall(False)
+    _check_loss_grad(case, p.loss_grad(*x))
+    p.sync_status()
