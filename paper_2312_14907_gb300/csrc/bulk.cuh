@@ -16,6 +16,9 @@ namespace mpbp {
 // kernel reads it from column s.y & 1 on.
 struct TmaMap {
   CUtensorMap map;
+  // raw-data variant: the staged counts of the launch's chunk, [rows][M]
+  // floats, boxes of 32 columns x M rows with the 128-byte swizzle
+  CUtensorMap ymap;
   // bytes announced on a tile-copy barrier beyond what the copies deliver
   // (0; > 0 only to test the bounded wait, which then runs out)
   unsigned tx_extra;
@@ -56,6 +59,14 @@ MPBP_DI void tile_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, in
       "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
       "[%5];" ::"r"(dst),
       "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+MPBP_DI void tile_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(dst),
+      "l"(map), "r"(x), "r"(y), "r"(bar)
       : "memory");
 }
 

@@ -46,7 +46,7 @@ struct FramesKernel<M, false> {
   static KernelShape grad(bool) { return {frames_t1<M, false>, C::T, C::SMEM}; }
   static KernelShape fwd(bool) { return {frames_t1<M, true>, C::T, C::SMEM}; }
   static constexpr bool kRaw = false;
-  static KernelShape raw() { return grad(false); }
+  static KernelShape raw(bool) { return grad(false); }
 };
 
 template <int M>
@@ -71,7 +71,10 @@ struct FramesKernel<M, true> {
                : KernelShape{frames_t2<M, true>, C::T, C::SMEM};
   }
   static constexpr bool kRaw = true;
-  static KernelShape raw() { return {frames_t2<M, false, true>, C::T, C::SMEM}; }
+  static KernelShape raw(bool tma) {
+    return tma ? KernelShape{frames_t2<M, false, true, true>, C::T, C::SMEM_RAW_TMA}
+               : KernelShape{frames_t2<M, false, true>, C::T, C::SMEM};
+  }
 };
 
 inline bool set_smem(const KernelShape& k) {
@@ -83,7 +86,7 @@ bool frames_prepare_impl(FrameKernelInfo* info) {
   using K = FramesKernel<M>;
   bool ok = true;
   for (int t = 0; t < 2; ++t) ok = set_smem(K::grad(t != 0)) && set_smem(K::fwd(t != 0)) && ok;
-  if (K::kRaw) ok = set_smem(K::raw()) && ok;
+  if (K::kRaw) ok = set_smem(K::raw(false)) && set_smem(K::raw(true)) && ok;
   if (!ok) return false;
   info->threads = K::grad(false).threads;
   info->smem = K::grad(false).smem;
@@ -114,12 +117,12 @@ cudaError_t frames_launch_impl(const FrameArgs& a, int grid, bool forward, cudaS
 
 // the raw-data gradient kernel (FrameArgs::yraw); thread-pair sides only
 template <int M>
-cudaError_t frames_launch_raw_impl(const FrameArgs& a, int grid, cudaStream_t s) {
+cudaError_t frames_launch_raw_impl(const FrameArgs& a, int grid, cudaStream_t s, const TmaMap* tm) {
   using K = FramesKernel<M>;
   if (!K::kRaw) return cudaErrorNotSupported;
   static const TmaMap kNone{};
-  const KernelShape k = K::raw();
-  k.fn<<<grid, k.threads, k.smem, s>>>(a, kNone);
+  const KernelShape k = K::raw(tm != nullptr);
+  k.fn<<<grid, k.threads, k.smem, s>>>(a, tm ? *tm : kNone);
   return cudaGetLastError();
 }
 
@@ -132,7 +135,8 @@ cudaError_t frames_launch_raw_impl(const FrameArgs& a, int grid, cudaStream_t s)
                                  const TmaMap* tm) {                                       \
     return frames_launch_impl<M>(a, grid, forward, s, tm);                                 \
   }                                                                                        \
-  cudaError_t frames_launch_raw_m##M(const FrameArgs& a, int grid, cudaStream_t s) {       \
-    return frames_launch_raw_impl<M>(a, grid, s);                                          \
+  cudaError_t frames_launch_raw_m##M(const FrameArgs& a, int grid, cudaStream_t s,        \
+                                     const TmaMap* tm) {                                   \
+    return frames_launch_raw_impl<M>(a, grid, s, tm);                                      \
   }                                                                                        \
   }

@@ -17,6 +17,8 @@
 
 using namespace mpbp;
 
+constexpr int kStageSlots = 3;   // staging buffers of the host-buffer entry point
+
 struct mpbp_ctx {
   unsigned long long serial = 0;   // unique per context created in this process
   int device = 0;
@@ -36,6 +38,9 @@ struct mpbp_ctx {
   TmaMap tm_grad{}, tm_fwd{};
   bool tile_grad = false, tile_fwd = false;
   unsigned test_tx_extra = 0;   // mpbp_set_test_stall
+  // host path: tensor maps of the staged counts, one per staging slot
+  CUtensorMap ymap[kStageSlots];
+  long long ymap_per = 0;       // frames per slot they were encoded for (0: none)
   int precision = MPBP_PRECISION_FP32;
   void* tc_w = nullptr;       // split DFT matrix of the tensor-core kernel
   int blocks_per_sm = 0;  // schedule in use
@@ -158,7 +163,6 @@ bool batch_fused_side(int mode, int m) {
 // frame-range launches of one host-path evaluation (each writes its own
 // slice of the loss partials)
 constexpr int kMaxHostChunks = 8;
-constexpr int kStageSlots = 3;   // staging buffers of the host-buffer entry point
 
 // device address of page-locked (CUDA-registered) host memory, else NULL
 void* mapped_host(const void* p) {
@@ -210,6 +214,21 @@ EncodeTiledFn encode_tiled_fn() {
     return reinterpret_cast<EncodeTiledFn>(f);
   }();
   return fn;
+}
+
+// Tensor map of one staging slot of counts, [per M rows][M] floats, in boxes
+// of 32 columns x M rows with the 128-byte swizzle (the raw-data kernel's
+// shared-memory layout).
+bool encode_counts_map(const mpbp_ctx* c, const float* base, long long per, CUtensorMap* out) {
+  const EncodeTiledFn fn = encode_tiled_fn();
+  if (!fn || c->M < 32 || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
+  const cuuint64_t dim[2] = {(cuuint64_t)c->M, (cuuint64_t)(per * c->M)};
+  const cuuint64_t stride[1] = {(cuuint64_t)c->M * sizeof(float)};
+  const cuuint32_t box[2] = {32u, (cuuint32_t)c->M};
+  const cuuint32_t estride[2] = {1u, 1u};
+  return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dim, stride, box, estride,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // Tensor map of the objects O [D][n1][n2] (8-byte elements) for tiles of
@@ -681,7 +700,16 @@ mpbp_status mpbp_loss_grad_host(mpbp_ctx* c, const float* y, const float* rho, c
         return fail(c, MPBP_ERR_OOM, "host-path staging buffers");
       }
       c->stage_elems = per * mm;
+      c->ymap_per = 0;
     }
+  }
+  // tile copies for the raw-data kernel: the objects' map of the pair layout
+  // (the forward kernel's box) and one counts map per staging slot
+  bool raw_tiles = raw && c->tile_fwd;
+  if (raw_tiles && c->ymap_per != per) {
+    for (int i = 0; i < kStageSlots && raw_tiles; ++i)
+      raw_tiles = encode_counts_map(c, c->stage + i * c->stage_elems, per, &c->ymap[i]);
+    c->ymap_per = raw_tiles ? per : 0;
   }
   auto copy_chunk = [&](int k) -> mpbp_status {
     const int slot = k % kStageSlots;
@@ -745,7 +773,14 @@ mpbp_status mpbp_loss_grad_host(mpbp_ctx* c, const float* y, const float* rho, c
         MPBP_CUDA(c, cudaStreamWaitEvent(cs, c->ev_copied[slot], 0));
         fa.yraw = st - f0 * mm;   // indexed by absolute frame number
         fa.aT_w = c->aT;
-        MPBP_CUDA(c, frames_launch_raw(c->M, fa, grid, cs));
+        if (raw_tiles) {
+          TmaMap tm = c->tm_fwd;
+          tm.ymap = c->ymap[slot];
+          tm.tx_extra = 0;
+          MPBP_CUDA(c, frames_launch_raw(c->M, fa, grid, cs, &tm));
+        } else {
+          MPBP_CUDA(c, frames_launch_raw(c->M, fa, grid, cs));
+        }
         MPBP_CUDA(c, cudaEventRecord(c->ev_consumed[slot], cs));
       } else {
         MPBP_CUDA(c, cudaStreamWaitEvent(s, c->ev_copied[slot], 0));

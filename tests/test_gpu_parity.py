@@ -97,7 +97,9 @@ def test_random_probe_per_peak_and_background(m):
 def test_tile_and_plain_copies_match_oracle(m):
     """Objects whose rows are a multiple of 16 bytes (even n2) reach the FFT
     kernels by TMA tile and bulk copies, odd n2 by cp.async; both layouts,
-    with odd and negative scan offsets, against the oracle."""
+    with odd and negative scan offsets, against the oracle, through the
+    device and the host-buffer entry points."""
+    from paper_2312_14907_gb300 import mpbp
     for n2, tiles in ((2 * m + 8, 3), (2 * m + 7, 0)):
         spec, scan = custom_spec(2 * m + 6, m, 3, m // 2 + 1, npeaks=2, offset=-3, n2=n2)
         case = Case(spec, scan=scan, state="perturbed")
@@ -108,6 +110,14 @@ def test_tile_and_plain_copies_match_oracle(m):
         I_ref = case.oracle.forward(case.rho, case.u, case.alpha, case.probe)
         assert rel_l2(I, I_ref) <= 1e-5
         p.sync_status()
+        # the host-buffer call: the raw-data kernel takes the staged counts
+        # by tile copies too (even n2) or by cp.async (odd n2)
+        q = mpbp.Problem.from_spec(case.spec, case.scan)
+        q.set_probe(torch.from_numpy(case.probe).cuda())
+        h = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        got = q.loss_grad_host(h(case.rho), h(case.u), h(case.alpha), y=h(case.y))
+        _check_loss_grad(case, got)
+        q.sync_status()
 
 
 def test_frame_subset_matches_oracle():
