@@ -238,6 +238,21 @@ def run_gpu(args):
     e2e_s = replicas.max_over_ranks(sum(e2e), device="cuda")
     h2d = y.nbytes + rh.numel() * 4 + uh.numel() * 4 + ah.numel() * 4
     d2h = 8 + outs[1].numel() * 4 + outs[2].numel() * 4 + outs[3].numel() * 8
+    # the same call with the photon counts as 16-bit integers (exact: the
+    # data are Poisson counts below 65536)
+    assert np.all(y == np.round(y)) and y.max() < 65536
+    yh16 = pin(y.astype(np.uint16))
+    for _ in range(max(2, args.warmup)):
+        prob.loss_grad_host(rh, uh, ah, y=yh16, out=outs)
+    e2e16 = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        prob.loss_grad_host(rh, uh, ah, y=yh16, out=outs)
+        e2e16.append(time.perf_counter() - t1)
+    e2e16_s = replicas.max_over_ranks(sum(e2e16), device="cuda")
+    h2d16 = yh16.numel() * 2 + rh.numel() * 4 + uh.numel() * 4 + ah.numel() * 4
 
     frames_total = spec.nframes * args.steps * world
     value = replicas.whole_job_rate(spec.nframes, args.steps, world, tot_ms)
@@ -294,6 +309,9 @@ def run_gpu(args):
         "e2e": {"value": frames_total / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h),
                 "call": "mpbp_loss_grad_host (host y, rho, u, alpha in; loss and gradients out)"},
+        "e2e_counts16": {"value": frames_total / e2e16_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d16),
+                         "d2h_bytes_per_step": int(d2h),
+                         "call": "mpbp_loss_grad_host_counts16 (y as 16-bit photon counts; otherwise as e2e)"},
         "gpu_launches": info["launches_step"] * args.steps,
         "clocks": clk.summary(),
         "wall_s": wall,

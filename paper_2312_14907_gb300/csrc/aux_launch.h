@@ -58,6 +58,8 @@ struct IllumArgs {
 cudaError_t launch_illumination(const IllumArgs& a, int num_sms, cudaStream_t s);
 
 cudaError_t launch_object_build(const ObjectArgs& a, int num_sms, cudaStream_t s);
+// out[i] = in[i] for n 16-bit counts
+cudaError_t launch_counts16(const unsigned short* in, float* out, long long n, int num_sms, cudaStream_t s);
 cudaError_t launch_frame_transpose(const float* in, float* out, long long nframes, int m,
                                    bool take_sqrt, cudaStream_t s);
 int finish_grid(long long npix, int num_sms);

@@ -13,9 +13,9 @@ cudaError_t frames_launch_m16(const FrameArgs&, int, bool, cudaStream_t, const T
 cudaError_t frames_launch_m32(const FrameArgs&, int, bool, cudaStream_t, const TmaMap*);
 cudaError_t frames_launch_m64(const FrameArgs&, int, bool, cudaStream_t, const TmaMap*);
 cudaError_t frames_launch_m128(const FrameArgs&, int, bool, cudaStream_t, const TmaMap*);
-cudaError_t frames_launch_raw_m32(const FrameArgs&, int, cudaStream_t, const TmaMap*);
-cudaError_t frames_launch_raw_m64(const FrameArgs&, int, cudaStream_t, const TmaMap*);
-cudaError_t frames_launch_raw_m128(const FrameArgs&, int, cudaStream_t, const TmaMap*);
+cudaError_t frames_launch_raw_m32(const FrameArgs&, int, cudaStream_t, const TmaMap*, bool);
+cudaError_t frames_launch_raw_m64(const FrameArgs&, int, cudaStream_t, const TmaMap*, bool);
+cudaError_t frames_launch_raw_m128(const FrameArgs&, int, cudaStream_t, const TmaMap*, bool);
 
 bool frames_prepare(int m, FrameKernelInfo* info) {
   switch (m) {
@@ -41,11 +41,14 @@ cudaError_t frames_launch(int m, const FrameArgs& a, int grid, bool forward, cud
 
 bool frames_raw_supported(int m) { return m == 32 || m == 64 || m == 128; }
 
-cudaError_t frames_launch_raw(int m, const FrameArgs& a, int grid, cudaStream_t s, const TmaMap* tm) {
+bool frames_raw16_supported(int m) { return m == 64 || m == 128; }
+
+cudaError_t frames_launch_raw(int m, const FrameArgs& a, int grid, cudaStream_t s, const TmaMap* tm,
+                              bool y16) {
   switch (m) {
-    case 32: return frames_launch_raw_m32(a, grid, s, tm);
-    case 64: return frames_launch_raw_m64(a, grid, s, tm);
-    case 128: return frames_launch_raw_m128(a, grid, s, tm);
+    case 32: return frames_launch_raw_m32(a, grid, s, tm, y16);
+    case 64: return frames_launch_raw_m64(a, grid, s, tm, y16);
+    case 128: return frames_launch_raw_m128(a, grid, s, tm, y16);
     default: return cudaErrorNotSupported;
   }
 }

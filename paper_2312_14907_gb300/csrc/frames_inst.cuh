@@ -46,7 +46,8 @@ struct FramesKernel<M, false> {
   static KernelShape grad(bool) { return {frames_t1<M, false>, C::T, C::SMEM}; }
   static KernelShape fwd(bool) { return {frames_t1<M, true>, C::T, C::SMEM}; }
   static constexpr bool kRaw = false;
-  static KernelShape raw(bool) { return grad(false); }
+  static constexpr bool kRaw16 = false;
+  static KernelShape raw(bool, bool = false) { return grad(false); }
 };
 
 template <int M>
@@ -71,7 +72,11 @@ struct FramesKernel<M, true> {
                : KernelShape{frames_t2<M, true>, C::T, C::SMEM};
   }
   static constexpr bool kRaw = true;
-  static KernelShape raw(bool tma) {
+  static constexpr bool kRaw16 = M >= 64;   // 16-bit counts by tile copies
+  static KernelShape raw(bool tma, bool y16 = false) {
+    if constexpr (kRaw16) {
+      if (y16) return {frames_t2<M, false, true, true, true>, C::T, C::SMEM_RAW_TMA};
+    }
     return tma ? KernelShape{frames_t2<M, false, true, true>, C::T, C::SMEM_RAW_TMA}
                : KernelShape{frames_t2<M, false, true>, C::T, C::SMEM};
   }
@@ -87,6 +92,7 @@ bool frames_prepare_impl(FrameKernelInfo* info) {
   bool ok = true;
   for (int t = 0; t < 2; ++t) ok = set_smem(K::grad(t != 0)) && set_smem(K::fwd(t != 0)) && ok;
   if (K::kRaw) ok = set_smem(K::raw(false)) && set_smem(K::raw(true)) && ok;
+  if (K::kRaw16) ok = set_smem(K::raw(true, true)) && ok;
   if (!ok) return false;
   info->threads = K::grad(false).threads;
   info->smem = K::grad(false).smem;
@@ -117,11 +123,11 @@ cudaError_t frames_launch_impl(const FrameArgs& a, int grid, bool forward, cudaS
 
 // the raw-data gradient kernel (FrameArgs::yraw); thread-pair sides only
 template <int M>
-cudaError_t frames_launch_raw_impl(const FrameArgs& a, int grid, cudaStream_t s, const TmaMap* tm) {
+cudaError_t frames_launch_raw_impl(const FrameArgs& a, int grid, cudaStream_t s, const TmaMap* tm, bool y16) {
   using K = FramesKernel<M>;
-  if (!K::kRaw) return cudaErrorNotSupported;
+  if (!K::kRaw || (y16 && (!K::kRaw16 || !tm))) return cudaErrorNotSupported;
   static const TmaMap kNone{};
-  const KernelShape k = K::raw(tm != nullptr);
+  const KernelShape k = K::raw(tm != nullptr, y16);
   k.fn<<<grid, k.threads, k.smem, s>>>(a, tm ? *tm : kNone);
   return cudaGetLastError();
 }
@@ -136,7 +142,7 @@ cudaError_t frames_launch_raw_impl(const FrameArgs& a, int grid, cudaStream_t s,
     return frames_launch_impl<M>(a, grid, forward, s, tm);                                 \
   }                                                                                        \
   cudaError_t frames_launch_raw_m##M(const FrameArgs& a, int grid, cudaStream_t s,        \
-                                     const TmaMap* tm) {                                   \
-    return frames_launch_raw_impl<M>(a, grid, s, tm);                                      \
+                                     const TmaMap* tm, bool y16) {                         \
+    return frames_launch_raw_impl<M>(a, grid, s, tm, y16);                                 \
   }                                                                                        \
   }

@@ -66,8 +66,11 @@ cudaError_t frames_launch(int m, const FrameArgs& a, int grid, bool forward, cud
 // memory; sqrt(y) written to a.aT_w).  Frame sides 32, 64, 128.
 bool frames_raw_supported(int m);
 // tm: tensor maps of the objects and of the staged counts (TmaMap::ymap),
-// or nullptr for the cp.async copies
-cudaError_t frames_launch_raw(int m, const FrameArgs& a, int grid, cudaStream_t s, const TmaMap* tm = nullptr);
+// or nullptr for the cp.async copies.  y16: the staged counts are 16-bit
+// unsigned integers (tile copies only; frame sides 64 and 128).
+bool frames_raw16_supported(int m);
+cudaError_t frames_launch_raw(int m, const FrameArgs& a, int grid, cudaStream_t s, const TmaMap* tm = nullptr,
+                              bool y16 = false);
 
 // Tensor-core variant of the gradient kernel for m = 64 (frames_tc.cu): the
 // DFT passes as split-FP16 GEMMs on tcgen05.  Two frames in flight per

@@ -41,6 +41,11 @@ struct mpbp_ctx {
   // host path: tensor maps of the staged counts, one per staging slot
   CUtensorMap ymap[kStageSlots];
   long long ymap_per = 0;       // frames per slot they were encoded for (0: none)
+  // host path with 16-bit counts: their staging slots and tensor maps
+  unsigned short* stage16 = nullptr;
+  size_t stage16_elems = 0;
+  CUtensorMap ymap16[kStageSlots];
+  long long ymap16_per = 0;
   int precision = MPBP_PRECISION_FP32;
   void* tc_w = nullptr;       // split DFT matrix of the tensor-core kernel
   int blocks_per_sm = 0;  // schedule in use
@@ -219,16 +224,18 @@ EncodeTiledFn encode_tiled_fn() {
 // Tensor map of one staging slot of counts, [per M rows][M] floats, in boxes
 // of 32 columns x M rows with the 128-byte swizzle (the raw-data kernel's
 // shared-memory layout).
-bool encode_counts_map(const mpbp_ctx* c, const float* base, long long per, CUtensorMap* out) {
+// (y16: 16-bit counts, boxes of 64 columns; the same 128 bytes a box row)
+bool encode_counts_map(const mpbp_ctx* c, const void* base, long long per, bool y16, CUtensorMap* out) {
   const EncodeTiledFn fn = encode_tiled_fn();
-  if (!fn || c->M < 32 || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
+  const int eb = y16 ? 2 : 4;
+  if (!fn || c->M * eb < 128 || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
   const cuuint64_t dim[2] = {(cuuint64_t)c->M, (cuuint64_t)(per * c->M)};
-  const cuuint64_t stride[1] = {(cuuint64_t)c->M * sizeof(float)};
-  const cuuint32_t box[2] = {32u, (cuuint32_t)c->M};
+  const cuuint64_t stride[1] = {(cuuint64_t)c->M * eb};
+  const cuuint32_t box[2] = {(cuuint32_t)(128 / eb), (cuuint32_t)c->M};
   const cuuint32_t estride[2] = {1u, 1u};
-  return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dim, stride, box, estride,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return fn(out, y16 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dim,
+            stride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // Tensor map of the objects O [D][n1][n2] (8-byte elements) for tiles of
@@ -503,6 +510,7 @@ void mpbp_destroy(mpbp_ctx* c) {
   }
   if (c->batch_ws) cudaFree(c->batch_ws);
   if (c->stage) cudaFree(c->stage);
+  if (c->stage16) cudaFree(c->stage16);
   if (c->bgT) cudaFree(c->bgT);
   if (c->tc_w) cudaFree(c->tc_w);
   if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
@@ -636,7 +644,12 @@ mpbp_status mpbp_loss_grad(mpbp_ctx* c, const float* rho, const float* u, const 
                            g_u ? g_u : c->g_u_ws, g_alpha, nullptr, S(stream));
 }
 
-mpbp_status mpbp_loss_grad_host(mpbp_ctx* c, const float* y, const float* rho, const float* u,
+}  // extern "C"
+
+namespace {
+
+// The host-buffer evaluation; y: float counts, or (y16) 16-bit counts.
+mpbp_status loss_grad_host_impl(mpbp_ctx* c, const void* y, bool y16, const float* rho, const float* u,
                                 const float* alpha, double* loss, float* g_rho, float* g_u,
                                 double* g_alpha, void* stream) {
   if (!c || !rho || !u || !alpha || !loss) return fail(c, MPBP_ERR_INVALID_ARG, "null argument");
@@ -667,6 +680,9 @@ mpbp_status mpbp_loss_grad_host(mpbp_ctx* c, const float* y, const float* rho, c
   // evaluated on the caller's stream.  The gradient accumulator sums over the
   // chunk launches, each with its own slice of loss partials.
   const bool raw = y && c->precision == MPBP_PRECISION_FP32 && frames_raw_supported(c->M);
+  // 16-bit counts read by the raw-data kernel itself (tile copies), or
+  // widened to floats on the device first (the other paths)
+  const bool fast16 = y16 && raw && c->tile_fwd && frames_raw16_supported(c->M);
   int nchunks = 1;
   if (y) nchunks = (int)std::min<long long>(kMaxHostChunks, std::max<long long>(1, c->nframes / (raw ? 256 : 512)));
   // chunk k holds frames [bound[k], bound[k+1]) (equal chunks: measured as
@@ -688,7 +704,7 @@ mpbp_status mpbp_loss_grad_host(mpbp_ctx* c, const float* y, const float* rho, c
              cudaEventCreateWithFlags(&c->ev_consumed[i], cudaEventDisableTiming) == cudaSuccess;
       if (!ok) return fail(c, MPBP_ERR_CUDA, "host-path streams");
     }
-    if ((size_t)(per * mm) > c->stage_elems) {
+    if (!fast16 && (size_t)(per * mm) > c->stage_elems) {
       MPBP_CUDA(c, cudaStreamSynchronize(s));
       MPBP_CUDA(c, cudaStreamSynchronize(c->copy_stream));
       if (c->stage) cudaFree(c->stage);
@@ -702,22 +718,48 @@ mpbp_status mpbp_loss_grad_host(mpbp_ctx* c, const float* y, const float* rho, c
       c->stage_elems = per * mm;
       c->ymap_per = 0;
     }
+    if (y16 && (size_t)(per * mm) > c->stage16_elems) {
+      MPBP_CUDA(c, cudaStreamSynchronize(s));
+      MPBP_CUDA(c, cudaStreamSynchronize(c->copy_stream));
+      if (c->stage16) cudaFree(c->stage16);
+      c->stage16 = nullptr;
+      c->stage16_elems = 0;
+      cudaError_t e = cudaMalloc(&c->stage16, sizeof(unsigned short) * kStageSlots * per * mm);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, MPBP_ERR_OOM, "host-path staging buffers");
+      }
+      c->stage16_elems = per * mm;
+      c->ymap16_per = 0;
+    }
   }
   // tile copies for the raw-data kernel: the objects' map of the pair layout
   // (the forward kernel's box) and one counts map per staging slot
   bool raw_tiles = raw && c->tile_fwd;
-  if (raw_tiles && c->ymap_per != per) {
+  if (raw_tiles && !fast16 && c->ymap_per != per) {
     for (int i = 0; i < kStageSlots && raw_tiles; ++i)
-      raw_tiles = encode_counts_map(c, c->stage + i * c->stage_elems, per, &c->ymap[i]);
+      raw_tiles = encode_counts_map(c, c->stage + i * c->stage_elems, per, false, &c->ymap[i]);
     c->ymap_per = raw_tiles ? per : 0;
+  }
+  if (fast16 && c->ymap16_per != per) {
+    bool ok = true;
+    for (int i = 0; i < kStageSlots && ok; ++i)
+      ok = encode_counts_map(c, c->stage16 + i * c->stage16_elems, per, true, &c->ymap16[i]);
+    if (!ok) return fail(c, MPBP_ERR_CUDA, "tensor map of the 16-bit counts");
+    c->ymap16_per = per;
   }
   auto copy_chunk = [&](int k) -> mpbp_status {
     const int slot = k % kStageSlots;
     const long long f0 = bound[k];
     const long long nf = bound[k + 1] - f0;
     if (k >= kStageSlots) MPBP_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->ev_consumed[slot], 0));
-    MPBP_CUDA(c, cudaMemcpyAsync(c->stage + slot * c->stage_elems, y + f0 * mm, sizeof(float) * nf * mm,
-                                 cudaMemcpyHostToDevice, c->copy_stream));
+    if (y16)
+      MPBP_CUDA(c, cudaMemcpyAsync(c->stage16 + slot * c->stage16_elems,
+                                   static_cast<const unsigned short*>(y) + f0 * mm,
+                                   sizeof(unsigned short) * nf * mm, cudaMemcpyHostToDevice, c->copy_stream));
+    else
+      MPBP_CUDA(c, cudaMemcpyAsync(c->stage + slot * c->stage_elems, static_cast<const float*>(y) + f0 * mm,
+                                   sizeof(float) * nf * mm, cudaMemcpyHostToDevice, c->copy_stream));
     MPBP_CUDA(c, cudaEventRecord(c->ev_copied[slot], c->copy_stream));
     return MPBP_OK;
   };
@@ -760,20 +802,33 @@ mpbp_status mpbp_loss_grad_host(mpbp_ctx* c, const float* y, const float* rho, c
     const int grid = frames_grid_for(c, nf);
     if (y) {
       const int slot = k % kStageSlots;
-      float* st = c->stage + slot * c->stage_elems;
+      float* st = fast16 ? nullptr : c->stage + slot * c->stage_elems;
       if (k >= kStageSlots) {
         mpbp_status rc = copy_chunk(k);
         if (rc != MPBP_OK) return rc;
       }
+      // 16-bit counts for a path that reads floats: widen them first
+      auto widen = [&](cudaStream_t ws) -> mpbp_status {
+        if (y16 && !fast16)
+          MPBP_CUDA(c, launch_counts16(c->stage16 + slot * c->stage16_elems, st, nf * mm, c->num_sms, ws));
+        return MPBP_OK;
+      };
       if (raw) {
         // the last chunk runs on the caller's stream, right before the finish
         const bool last = k == nchunks - 1;
         cudaStream_t cs = last ? s : c->chunk_stream[k & 1];
         if (k < 2 && !last) MPBP_CUDA(c, cudaStreamWaitEvent(cs, c->ev_ready, 0));
         MPBP_CUDA(c, cudaStreamWaitEvent(cs, c->ev_copied[slot], 0));
-        fa.yraw = st - f0 * mm;   // indexed by absolute frame number
+        mpbp_status wr = widen(cs);
+        if (wr != MPBP_OK) return wr;
+        fa.yraw = st ? st - f0 * mm : nullptr;   // indexed by absolute frame number
         fa.aT_w = c->aT;
-        if (raw_tiles) {
+        if (fast16) {
+          TmaMap tm = c->tm_fwd;
+          tm.ymap = c->ymap16[slot];
+          tm.tx_extra = 0;
+          MPBP_CUDA(c, frames_launch_raw(c->M, fa, grid, cs, &tm, true));
+        } else if (raw_tiles) {
           TmaMap tm = c->tm_fwd;
           tm.ymap = c->ymap[slot];
           tm.tx_extra = 0;
@@ -784,6 +839,8 @@ mpbp_status mpbp_loss_grad_host(mpbp_ctx* c, const float* y, const float* rho, c
         MPBP_CUDA(c, cudaEventRecord(c->ev_consumed[slot], cs));
       } else {
         MPBP_CUDA(c, cudaStreamWaitEvent(s, c->ev_copied[slot], 0));
+        mpbp_status wr = widen(s);
+        if (wr != MPBP_OK) return wr;
         MPBP_CUDA(c, launch_frame_transpose(st, c->aT + f0 * mm, nf, c->M, true, s));
         MPBP_CUDA(c, cudaEventRecord(c->ev_consumed[slot], s));
         MPBP_CUDA(c, launch_frames(c, fa, grid, s));
@@ -857,6 +914,23 @@ mpbp_status mpbp_loss_grad_host(mpbp_ctx* c, const float* y, const float* rho, c
                                  cudaMemcpyDeviceToHost, s));
   MPBP_CUDA(c, cudaStreamSynchronize(s));
   return MPBP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mpbp_status mpbp_loss_grad_host(mpbp_ctx* c, const float* y, const float* rho, const float* u,
+                                const float* alpha, double* loss, float* g_rho, float* g_u,
+                                double* g_alpha, void* stream) {
+  return loss_grad_host_impl(c, y, false, rho, u, alpha, loss, g_rho, g_u, g_alpha, stream);
+}
+
+mpbp_status mpbp_loss_grad_host_counts16(mpbp_ctx* c, const uint16_t* y, const float* rho, const float* u,
+                                         const float* alpha, double* loss, float* g_rho, float* g_u,
+                                         double* g_alpha, void* stream) {
+  if (!y) return fail(c, MPBP_ERR_INVALID_ARG, "null argument");
+  return loss_grad_host_impl(c, y, true, rho, u, alpha, loss, g_rho, g_u, g_alpha, stream);
 }
 
 mpbp_status mpbp_step_init(mpbp_ctx* c, const mpbp_step_params* prm, mpbp_step_state* st,

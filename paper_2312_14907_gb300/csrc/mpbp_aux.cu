@@ -40,6 +40,14 @@ __global__ void object_build_kernel(ObjectArgs a) {
 }
 
 // ----------------------------------------------------------------------------
+// 16-bit photon counts to floats (exact), for the paths that read floats
+// ----------------------------------------------------------------------------
+__global__ void counts16_kernel(const unsigned short* __restrict__ in, float* __restrict__ out, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+// ----------------------------------------------------------------------------
 // data: out[f][q1][q0] = g(in[f][q0][q1]), g = sqrt or identity
 // ----------------------------------------------------------------------------
 template <bool SQRT>
@@ -306,6 +314,12 @@ static int grid_for(long long n, int threads, int cap) {
 cudaError_t launch_object_build(const ObjectArgs& a, int num_sms, cudaStream_t s) {
   if (a.phi) object_build_kernel<true><<<grid_for(a.npix, 256, num_sms * 8), 256, 0, s>>>(a);
   else object_build_kernel<false><<<grid_for(a.npix, 256, num_sms * 8), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_counts16(const unsigned short* in, float* out, long long n, int num_sms, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  counts16_kernel<<<grid_for(n, 256, num_sms * 8), 256, 0, s>>>(in, out, n);
   return cudaGetLastError();
 }
 

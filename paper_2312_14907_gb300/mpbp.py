@@ -80,7 +80,7 @@ EXPORTS = ["mpbp_status_string", "mpbp_create", "mpbp_destroy", "mpbp_last_error
            "mpbp_set_precision", "mpbp_step_capture", "mpbp_step_replay",
            "mpbp_adam_init", "mpbp_adam_step", "mpbp_adam_get_state", "mpbp_adam_set_state",
            "mpbp_loss_grad_phases", "mpbp_unwrap_phases", "mpbp_project_displacement",
-           "mpbp_illumination", "mpbp_set_test_stall"]
+           "mpbp_illumination", "mpbp_set_test_stall", "mpbp_loss_grad_host_counts16"]
 
 PRECISION_FP32 = 0        # FFTs on the CUDA cores
 PRECISION_TC_SPLIT16 = 1  # dense DFT matrices on the tensor cores, split FP16
@@ -125,6 +125,8 @@ def load(build_if_missing=True):
     lib.mpbp_loss_grad.restype = st
     lib.mpbp_loss_grad_host.argtypes = [V, V, V, V, V, V, V, V, V, V]
     lib.mpbp_loss_grad_host.restype = st
+    lib.mpbp_loss_grad_host_counts16.argtypes = [V, V, V, V, V, V, V, V, V, V]
+    lib.mpbp_loss_grad_host_counts16.restype = st
     lib.mpbp_step_init.argtypes = [V, P(StepParams), V, V]
     lib.mpbp_step_init.restype = st
     lib.mpbp_step.argtypes = [V, V, V, V, V, V]
@@ -443,20 +445,22 @@ class Problem:
         return AdamState.from_buffer_copy(state.cpu().numpy().tobytes())
 
     def loss_grad_host(self, rho, u, alpha, y=None, out=None):
-        """Host-buffer variant (copies in, evaluates, copies out, synchronises)."""
+        """Host-buffer variant (copies in, evaluates, copies out, synchronises).
+        y: float32 counts, or uint16 photon counts (mpbp_loss_grad_host_counts16)."""
         sh = self.shapes
         _host(rho, torch.float32, sh["rho"], "rho")
         _host(u, torch.float32, sh["u"], "u")
         _host(alpha, torch.float32, sh["alpha"], "alpha")
+        counts16 = y is not None and y.dtype == torch.uint16
         if y is not None:
-            _host(y, torch.float32, sh["frames"], "y")
+            _host(y, torch.uint16 if counts16 else torch.float32, sh["frames"], "y")
         if out is None:
             out = (torch.empty(1, dtype=torch.float64), torch.empty(sh["rho"], dtype=torch.float32),
                    torch.empty(sh["u"], dtype=torch.float32), torch.empty(self.npeaks, dtype=torch.float64))
         loss, g_rho, g_u, g_alpha = out
-        self._check(self._lib.mpbp_loss_grad_host(self._h, _p(y), _p(rho), _p(u), _p(alpha),
-                                                  _p(loss), _p(g_rho), _p(g_u), _p(g_alpha),
-                                                  _stream()), "mpbp_loss_grad_host")
+        fn = self._lib.mpbp_loss_grad_host_counts16 if counts16 else self._lib.mpbp_loss_grad_host
+        self._check(fn(self._h, _p(y), _p(rho), _p(u), _p(alpha), _p(loss), _p(g_rho), _p(g_u), _p(g_alpha),
+                       _stream()), "mpbp_loss_grad_host")
         return loss, g_rho, g_u, g_alpha
 
     def step_init(self, t0, c_armijo=1e-4, grow=1.25, shrink=0.5, w_rho=1.0, w_u=1.0, w_alpha=1.0,

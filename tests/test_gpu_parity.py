@@ -117,6 +117,8 @@ def test_tile_and_plain_copies_match_oracle(m):
         h = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
         got = q.loss_grad_host(h(case.rho), h(case.u), h(case.alpha), y=h(case.y))
         _check_loss_grad(case, got)
+        got = q.loss_grad_host(h(case.rho), h(case.u), h(case.alpha), y=h(case.y.astype(np.uint16)))
+        _check_loss_grad(case, got)
         q.sync_status()
 
 
@@ -261,6 +263,17 @@ def test_host_entry_point_paths(m, pinned):
     for a, b in zip(again[1:], dev[1:]):
         assert rel_l2(a, b) <= 1e-5
     q.sync_status()
+    # the same counts as 16-bit integers (read by the frame kernel itself on
+    # M = 64 and 128, widened on the device first on M = 16 and 32)
+    assert np.all(case.y == np.round(case.y)) and case.y.max() < 65536
+    r = mpbp.Problem.from_spec(case.spec, case.scan)
+    r.set_probe(torch.from_numpy(case.probe).cuda())
+    h16 = [t.numpy() for t in r.loss_grad_host(wrap(case.rho), wrap(case.u), wrap(case.alpha),
+                                                y=wrap(case.y.astype(np.uint16)))]
+    assert abs(h16[0][0] - dev[0][0]) <= 1e-6 * abs(dev[0][0])
+    for a, b in zip(h16[1:], dev[1:]):
+        assert rel_l2(a, b) <= 1e-5
+    r.sync_status()
 
 
 def test_autograd_function():
