@@ -684,7 +684,9 @@ mpbp_status loss_grad_host_impl(mpbp_ctx* c, const void* y, bool y16, const floa
   // widened to floats on the device first (the other paths)
   const bool fast16 = y16 && raw && c->tile_fwd && frames_raw16_supported(c->M);
   int nchunks = 1;
-  if (y) nchunks = (int)std::min<long long>(kMaxHostChunks, std::max<long long>(1, c->nframes / (raw ? 256 : 512)));
+  // (about 512 frames a chunk: fewer chunks leave less overlap, more chunks
+  // cost more per-chunk launch and copy overhead; measured)
+  if (y) nchunks = (int)std::min<long long>(kMaxHostChunks, std::max<long long>(1, c->nframes / 512));
   // chunk k holds frames [bound[k], bound[k+1]) (equal chunks: measured as
   // fast as chunks shrinking towards the end)
   long long bound[kMaxHostChunks + 1];
