@@ -1121,7 +1121,8 @@ mpbp_status unwrap_setup(mpbp_ctx* c, cudaStream_t s) {
   const size_t o_rel = cv.take<float>(nodes), o_p = cv.take<int>(nodes), o_o = cv.take<int>(nodes),
                o_p2 = cv.take<int>(nodes), o_o2 = cv.take<int>(nodes), o_hp = cv.take<int>(nodes),
                o_ho = cv.take<int>(nodes), o_mn = cv.take<int>(nodes),
-               o_b = cv.take<unsigned long long>(nodes), o_f = cv.take<int>(3), o_bc = cv.take<unsigned>(2),
+               o_b = cv.take<unsigned long long>(nodes), o_ek = cv.take<unsigned long long>(2 * nodes),
+               o_f = cv.take<int>(3), o_bc = cv.take<unsigned>(2),
                o_phi = cv.take<float>(nodes), o_w = cv.take<float>(nodes);
   void* b = nullptr;
   MPBP_CUDA(c, cudaStreamSynchronize(s));
@@ -1141,6 +1142,7 @@ mpbp_status unwrap_setup(mpbp_ctx* c, cudaStream_t s) {
   a.hook_off = reinterpret_cast<int*>(p + o_ho);
   a.minnode = reinterpret_cast<int*>(p + o_mn);
   a.best = reinterpret_cast<unsigned long long*>(p + o_b);
+  a.ekey = reinterpret_cast<unsigned long long*>(p + o_ek);
   a.flags = reinterpret_cast<int*>(p + o_f);
   a.bar_count = reinterpret_cast<unsigned*>(p + o_bc);
   a.bar_gen = a.bar_count + 1;

@@ -121,6 +121,112 @@ __device__ __forceinline__ unsigned long long edge_key(float w, long long e) {
   return ((unsigned long long)__float_as_uint(w) << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)e);
 }
 
+// Local contraction.  In every 16 x 16 tile of a map, Boruvka rounds over the
+// tile in shared memory hook a component only when the heaviest edge incident
+// to it -- edges that leave the tile included -- lies inside the tile.  By the
+// cut property such an edge belongs to the maximum spanning forest, so the
+// global rounds continue from a forest of the same tree, with about one
+// component per tile left instead of one per pixel.  Writes parent and off
+// (multiple of 2 pi relative to the tile-local root) of every node.
+constexpr int kTile = 16;
+static_assert(kTile * kTile == kUnwrapThreads, "one node per thread");
+
+__device__ void local_contract(const UnwrapArgs& a) {
+  __shared__ int lp[kUnwrapThreads], lo[kUnwrapThreads], gid[kUnwrapThreads];
+  __shared__ float wv[kUnwrapThreads];
+  __shared__ unsigned long long bk[kUnwrapThreads];
+  const int t = threadIdx.x, ti = t / kTile, tj = t % kTile;
+  const int n1 = a.n1, n2 = a.n2;
+  const int tpr = (n2 + kTile - 1) / kTile, tpc = (n1 + kTile - 1) / kTile;
+  const int tiles_per_map = tpr * tpc;
+  const int ntiles = (int)(a.nodes / a.npix) * tiles_per_map;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int m = tile / tiles_per_map, rem = tile - m * tiles_per_map;
+    const int i0 = rem / tpr * kTile, j0 = rem % tpr * kTile;
+    const int i = i0 + ti, j = j0 + tj;
+    const bool in = i < n1 && j < n2;
+    const long long base = (long long)m * a.npix;
+    const long long v = in ? base + (long long)i * n2 + j : -1;
+    // the node's edges (keys never change): right and down ones, inside the
+    // tile or leaving it; left and up ones only where they leave it
+    unsigned long long kr = 0, kd = 0, kl = 0, ku = 0;
+    if (in) {
+      kr = a.ekey[2 * v];
+      kd = a.ekey[2 * v + 1];
+      if (tj == 0 && j > 0) kl = a.ekey[2 * (v - 1)];
+      if (ti == 0 && i > 0) ku = a.ekey[2 * (v - n2) + 1];
+    }
+    const bool r_in = tj + 1 < kTile, d_in = ti + 1 < kTile;
+    gid[t] = (int)v;
+    lp[t] = t;
+    lo[t] = 0;
+    wv[t] = in ? a.wrapped[v] : 0.0f;
+    for (int round = 0; round < 2 * kTile; ++round) {
+      bk[t] = 0ull;
+      __syncthreads();
+      const int r = lp[t];
+      if (kr) {
+        const int rq = r_in ? lp[t + 1] : -1;
+        if (rq != r) {
+          atomicMax(&bk[r], kr);
+          if (rq >= 0) atomicMax(&bk[rq], kr);
+        }
+      }
+      if (kd) {
+        const int rq = d_in ? lp[t + kTile] : -1;
+        if (rq != r) {
+          atomicMax(&bk[r], kd);
+          if (rq >= 0) atomicMax(&bk[rq], kd);
+        }
+      }
+      if (kl) atomicMax(&bk[r], kl);
+      if (ku) atomicMax(&bk[r], ku);
+      __syncthreads();
+      // hooks of the roots whose heaviest edge stays inside the tile
+      int hook_p = -1, hook_o = 0;
+      if (in && r == t && bk[t] != 0ull) {
+        const long long e = 0xFFFFFFFFll - (long long)(bk[t] & 0xFFFFFFFFull);
+        const long long pg = (e >> 1) - base;   // the edge's first end, within the map
+        const int pi = (int)(pg / n2), pj = (int)(pg - (long long)pi * n2);
+        const int qi = pi + (int)(e & 1), qj = pj + (int)(1 - (e & 1));
+        if (pi >= i0 && pj >= j0 && qi < i0 + kTile && qj < j0 + kTile) {
+          const int pl = (pi - i0) * kTile + (pj - j0), ql = (qi - i0) * kTile + (qj - j0);
+          const bool p_in_r = lp[pl] == t;
+          const int lr = p_in_r ? pl : ql, ls = p_in_r ? ql : pl;
+          const int sr = lp[ls];
+          if (!(bk[sr] == bk[t] && gid[t] < gid[sr])) {   // the shared edge: sr hooks under t
+            const float d = (wv[lr] + kTwoPi * (float)lo[lr]) - (wv[ls] + kTwoPi * (float)lo[ls]);
+            hook_p = sr;
+            hook_o = -(int)floorf(d / kTwoPi + 0.5f);
+          }
+        }
+      }
+      if (!__syncthreads_or(hook_p >= 0)) break;
+      if (hook_p >= 0) {
+        lp[t] = hook_p;
+        lo[t] = hook_o;
+      }
+      __syncthreads();
+      // pointer jumping to the roots (a forest of 256 nodes: at most 9 passes)
+      for (int jump = 0; jump < 2 * kTile; ++jump) {
+        const int p = lp[t], pp = lp[p];
+        const int no = lo[t] + (pp != p ? lo[p] : 0);
+        __syncthreads();
+        if (pp != p) {
+          lp[t] = pp;
+          lo[t] = no;
+        }
+        if (!__syncthreads_or(pp != p)) break;
+      }
+    }
+    if (in) {
+      a.parent[v] = gid[lp[t]];
+      a.off[v] = lo[t];
+    }
+    __syncthreads();   // the next tile reuses the shared arrays
+  }
+}
+
 __global__ void __launch_bounds__(kUnwrapThreads) unwrap_kernel(UnwrapArgs a) {
   const long long n = a.nodes;
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -131,10 +237,16 @@ __global__ void __launch_bounds__(kUnwrapThreads) unwrap_kernel(UnwrapArgs a) {
 
   for (long long v = tid; v < n; v += stride) {
     a.rel[v] = reliability(a, v);
-    a.parent[v] = (int)v;
-    a.off[v] = 0;
     a.best[v] = 0ull;
   }
+  if (!grid_sync(a)) return;
+  // edge keys (0: no edge), computed once
+  for (long long e = tid; e < 2 * n; e += stride) {
+    const long long q = edge_other(a, e);
+    a.ekey[e] = q < 0 ? 0ull : edge_key(a.rel[e >> 1] + a.rel[q], e);
+  }
+  if (!grid_sync(a)) return;
+  local_contract(a);   // writes parent and off of every node
   if (!grid_sync(a)) return;
 
   int flag_it = 0;   // flags rotate over 3 slots (see next_flag)
@@ -148,12 +260,11 @@ __global__ void __launch_bounds__(kUnwrapThreads) unwrap_kernel(UnwrapArgs a) {
     int* O = off[cur];
     // heaviest incident edge of every component (best[] is all zero here)
     for (long long e = tid; e < 2 * n; e += stride) {
-      const long long q = edge_other(a, e);
-      if (q < 0) continue;
-      const long long p = e >> 1;
+      const unsigned long long key = a.ekey[e];
+      if (!key) continue;
+      const long long p = e >> 1, q = p + ((e & 1) ? a.n2 : 1);
       const int rp = P[p], rq = P[q];
       if (rp == rq) continue;
-      const unsigned long long key = edge_key(a.rel[p] + a.rel[q], e);
       atomicMax(&a.best[rp], key);
       atomicMax(&a.best[rq], key);
     }
@@ -164,7 +275,7 @@ __global__ void __launch_bounds__(kUnwrapThreads) unwrap_kernel(UnwrapArgs a) {
       a.hook_parent[r] = -1;
       if (P[r] != (int)r || a.best[r] == 0ull) continue;
       const long long e = 0xFFFFFFFFll - (long long)(a.best[r] & 0xFFFFFFFFull);
-      const long long p = e >> 1, q = edge_other(a, e);
+      const long long p = e >> 1, q = p + ((e & 1) ? a.n2 : 1);
       const bool p_in_r = P[p] == (int)r;
       const long long pr = p_in_r ? p : q, ps = p_in_r ? q : p;
       const int s = P[ps];

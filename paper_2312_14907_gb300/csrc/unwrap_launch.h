@@ -18,6 +18,7 @@ struct UnwrapArgs {
   int* hook_off;
   int* minnode;           // [nodes] lowest node of each group (at its root)
   unsigned long long* best;   // [nodes] heaviest incident edge of each root
+  unsigned long long* ekey;   // [2 nodes] key of edge e = 2 v + dir (0: no edge)
   int* flags;             // [3] rotating "something changed" flags, zeroed before launch
   unsigned* bar_count;    // grid barrier, zeroed before launch
   unsigned* bar_gen;
