@@ -1,7 +1,8 @@
 // bulk.cuh -- the frame kernels' input copies through the tensor memory
 // accelerator: the object patch of a frame as one 2-D tile load
 // (cp.async.bulk.tensor; rows or columns outside the grid arrive as zeros),
-// its sqrt(y) tile as plain bulk copies, both completing on one mbarrier of
+// its sqrt(y) tile as plain bulk copies (or, in the raw-data variant, its
+// staged counts as swizzled 2-D tiles), all completing on one mbarrier of
 // the block.  One thread issues them; every thread waits with a time limit.
 #pragma once
 #include <cuda.h>
@@ -17,7 +18,8 @@ namespace mpbp {
 struct TmaMap {
   CUtensorMap map;
   // raw-data variant: the staged counts of the launch's chunk, [rows][M]
-  // floats, boxes of 32 columns x M rows with the 128-byte swizzle
+  // floats (16-bit counts), boxes of 32 (64) columns x M rows -- 128 bytes
+  // a box row -- with the 128-byte swizzle
   CUtensorMap ymap;
   // bytes announced on a tile-copy barrier beyond what the copies deliver
   // (0; > 0 only to test the bounded wait, which then runs out)
