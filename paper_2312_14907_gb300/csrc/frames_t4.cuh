@@ -193,7 +193,7 @@ MPBP_DI void t4_frame(const FrameArgs& p, const T4Group<M>& g, const FrameRef& c
     const float bv = b ? b[q1 * M + ln] : 0.0f;
     v[i] = residual(v[i], g.abuf[t4_amp<M>(q1, ln)], bv, fl);
   });
-  add_loss(cur.valid ? fl : 0.0f);
+  add_loss(cur.valid ? 0.5f * fl : 0.0f);
 
   // A5: rows (blk4 -> dec4), transpose, columns; the exchange buffer's last
   // reads (the transposed row input above) are behind this barrier

@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) frames_tc64(const FrameArgs p, 
         cim[j] = z.y;
         mx = abs_max(abs_max(mx, z.x), z.y);
       }
-      if (cur.valid) lsum += (double)fl;
+      if (cur.valid) lsum += 0.5 * (double)fl;
       e3 = scale_exp(group_max(mx, redf[gi][1], G.id));
       const float s = pow2f(e3);
 #pragma unroll
