@@ -140,6 +140,71 @@ def make_inputs(spec, scan, prob, torch):
     return probe, y
 
 
+def torch_loss_grad(torch, rho, u, alpha, probe, amp, scan, G, phase_scale, m):
+    """The same loss and gradient written as plain per-kernel PyTorch ops in
+    FP32 / complex64 -- object synthesis, patch gather with zero padding,
+    probe product, torch.fft.fft2, amplitude residual and loss, the gradient
+    by autograd: the unfused comparison path (not used by the library).
+    amp: sqrt(y) [D][J][M][M]; probe [M][M] or [D][M][M]."""
+    rho = rho.detach().clone().requires_grad_(True)
+    u = u.detach().clone().requires_grad_(True)
+    alpha = alpha.detach().clone().requires_grad_(True)
+    phi = phase_scale * torch.einsum("mc,cij->mij", G, u)
+    O = (alpha[:, None, None] * rho[None]) * torch.polar(torch.ones_like(phi), phi)
+    D, n1, n2 = O.shape
+    Op = O.new_zeros(D, n1 + 2 * m, n2 + 2 * m)
+    Op[:, m:m + n1, m:m + n2] = O
+    k = torch.arange(m, device=rho.device)
+    rows = (scan[:, 0:1] + m + k)[:, :, None]
+    cols = (scan[:, 1:2] + m + k)[:, None, :]
+    patches = Op[:, rows, cols]                                    # [D][J][M][M]
+    P = probe if probe.dim() == 2 else probe[:, None]
+    Psi = torch.fft.fft2(P * patches)
+    r = torch.sqrt(Psi.real * Psi.real + Psi.imag * Psi.imag) - amp
+    loss = 0.5 * (r * r).sum()
+    loss.backward()
+    return loss.detach(), rho.grad, u.grad, alpha.grad
+
+
+def unfused_comparison(torch, prob, spec, scan, probe, y, x, flush, stream, n=10):
+    """Times torch_loss_grad against the library's loss and gradient on the
+    same state and data (L2 flushed between evaluations, CUDA events)."""
+    dev = x[0].device
+    amp = torch.from_numpy(np.sqrt(y).astype(np.float32)).to(dev)
+    G = torch.tensor(np.asarray(spec.G), dtype=torch.float32, device=dev)
+    sc = torch.from_numpy(np.asarray(scan, np.int64)).to(dev)
+    pr = torch.from_numpy(probe).to(dev)
+    call = lambda: torch_loss_grad(torch, x[0], x[1], x[2], pr, amp, sc, G, spec.phase_scale, spec.m)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(n):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    t_torch = timed(call)
+    out = prob.loss_grad(*x)
+    t_fused = timed(lambda: prob.loss_grad(*x, out=out))
+    ref = [t.double() for t in call()]
+    got = [t.double() for t in prob.loss_grad(*x)]
+    rel = lambda a_, b_: float(torch.linalg.vector_norm(a_ - b_) / torch.linalg.vector_norm(b_))
+    return {"path": "plain per-kernel PyTorch FP32 (einsum, polar, gather, torch.fft.fft2, autograd)",
+            "ms_per_eval": t_torch, "value": spec.nframes / (t_torch / 1e3), "unit": UNIT,
+            "fused_ms_per_eval": t_fused, "speedup": t_torch / t_fused,
+            "unfused_vs_fused": {"loss_rel_err": abs(float(ref[0]) - float(got[0][0])) / abs(float(got[0][0])),
+                                 "g_rho_rel_l2": rel(ref[1], got[1]), "g_u_rel_l2": rel(ref[2], got[2]),
+                                 "g_alpha_rel_l2": rel(ref[3], got[3])}}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -348,6 +413,8 @@ def run_gpu(args):
             "tensor_flops_per_frame": tc_flops,
             "tensor_peak_tflops": pk["bf16_tflops"], "peak_src": pk["src"] + " (dense bf16 = fp16 rate)"}
         prob.set_precision(mpbp.PRECISION_FP32)
+    # the unfused comparison path on the same data and state
+    line["unfused_torch"] = unfused_comparison(torch, prob, spec, scan, probe, y, x, flush, stream)
     # the paper's own iteration (Alg. 1 without its projector): minibatches
     # of 50 frames from a seeded shuffle per epoch, Adam in the Eq. 8
     # variables with the paper's step sizes, inside the support mask
