@@ -297,13 +297,14 @@ mpbp_status enqueue_object_build(mpbp_ctx* c, const float* rho, const float* u,
   return MPBP_OK;
 }
 
-// A1..A8 without the optimizer update: objects, fused frames, gradient
-// assembly, reductions.  st != nullptr adds the line-search decision.
+// A1..A8: objects, fused frames, gradient assembly, reductions.  st != nullptr
+// adds the line-search decision, and step (with st) the optimizer update.
 mpbp_status enqueue_loss_grad(mpbp_ctx* c, const float* rho, const float* u, const float* alpha,
                               const int32_t* frames, int32_t nframes, double* loss,
                               float* g_rho, float* g_u, double* g_alpha,
                               mpbp_step_state* st, cudaStream_t s,
-                              const float* phi = nullptr, float* g_phi = nullptr) {
+                              const float* phi = nullptr, float* g_phi = nullptr,
+                              const StepPtrs* step = nullptr) {
   if (c->acc_dirty) {
     MPBP_CUDA(c, cudaMemsetAsync(c->acc, 0, sizeof(cf) * c->npix * c->D, s));
     c->acc_dirty = false;
@@ -357,6 +358,7 @@ mpbp_status enqueue_loss_grad(mpbp_ctx* c, const float* rho, const float* u, con
   ra.err = c->err;
   ra.st = st;
   ra.alpha_from = 1;
+  if (step) ra.step = *step;
   MPBP_CUDA(c, launch_finish(fi, ra, c->finish_grid, s));
   c->acc_dirty = false;
   return MPBP_OK;
@@ -529,7 +531,7 @@ mpbp_status mpbp_get_info(const mpbp_ctx* c, mpbp_info* info) {
   info->blocks_per_sm = c->blocks_per_sm;
   info->num_sms = c->num_sms;
   info->launches_loss_grad = 3;  // object build, frames, gradient assembly + reductions
-  info->launches_step = 4;       // + update
+  info->launches_step = 3;       // the same; the assembly also applies the update
   info->precision = c->precision;
   info->tile_copies = (c->tile_grad ? 1 : 0) | (c->tile_fwd ? 2 : 0);
   return MPBP_OK;
@@ -959,29 +961,18 @@ mpbp_status mpbp_step(mpbp_ctx* c, float* rho, float* u, float* alpha, mpbp_step
   if (!c || !rho || !u || !alpha || !st) return fail(c, MPBP_ERR_INVALID_ARG, "null argument");
   if (!c->has_probe || !c->has_data) return fail(c, MPBP_ERR_NO_DATA, "probe or data not set");
   cudaStream_t s = S(stream);
-  mpbp_status r = enqueue_loss_grad(c, rho, u, alpha, nullptr, 0, c->loss_ws, c->g_rho_ws,
-                                    c->g_u_ws, nullptr, st, s);
-  if (r != MPBP_OK) return r;
-  StepArgs sa{};
-  sa.rho = rho;
-  sa.u = u;
-  sa.alpha = alpha;
-  sa.g_rho = c->g_rho_ws;
-  sa.g_u = c->g_u_ws;
-  sa.g_alpha = c->g_alpha_ws;
-  sa.rho_base = c->rho_base;
-  sa.u_base = c->u_base;
-  sa.alpha_base = c->alpha_base;
-  sa.g_rho_base = c->g_rho_base;
-  sa.g_u_base = c->g_u_base;
-  sa.g_alpha_base = c->g_alpha_base;
-  sa.st = st;
-  sa.npix = c->npix;
-  sa.C = c->C;
-  sa.D = c->D;
-  sa.alpha_from = 1;
-  MPBP_CUDA(c, launch_step_update(sa, c->num_sms, s));
-  return MPBP_OK;
+  StepPtrs sp{};
+  sp.rho = rho;
+  sp.u = u;
+  sp.alpha = alpha;
+  sp.rho_base = c->rho_base;
+  sp.u_base = c->u_base;
+  sp.alpha_base = c->alpha_base;
+  sp.g_rho_base = c->g_rho_base;
+  sp.g_u_base = c->g_u_base;
+  sp.g_alpha_base = c->g_alpha_base;
+  return enqueue_loss_grad(c, rho, u, alpha, nullptr, 0, c->loss_ws, c->g_rho_ws, c->g_u_ws, nullptr,
+                           st, s, nullptr, nullptr, &sp);
 }
 
 mpbp_status mpbp_adam_init(mpbp_ctx* c, const mpbp_adam_params* prm, mpbp_adam_state* st,

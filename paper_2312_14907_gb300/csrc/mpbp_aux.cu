@@ -3,6 +3,7 @@
 //   data layout: a = sqrt(y) stored transposed per frame
 //   A6/A7 tail: gradient assembly from the patch accumulator
 //   A8  fixed-order FP64 reductions, the line-search decision and the update
+//       of mpbp_step (applied by the gradient assembly, pixel by pixel)
 #include "aux_launch.h"
 
 namespace mpbp {
@@ -91,12 +92,31 @@ __global__ void frame_transpose_kernel(const float* __restrict__ in, float* __re
 // ----------------------------------------------------------------------------
 constexpr int kReduceLoads = 20;   // partials per lane issued together (up to 640 blocks)
 
-template <int T>
-__device__ void final_reduce(const ReduceArgs& a) {
+// The lagged Armijo test of an optimizer step: a pure function of the state
+// and the loss at the trial point, so every block of the gradient assembly
+// reaches the same decision as the block that records it.
+struct StepDecision {
+  bool accept;
+  double t_new;   // step length of the next trial
+};
+
+__device__ StepDecision step_decide(const mpbp_step_state* st, double loss) {
+  const bool finite = isfinite(loss);
+  StepDecision d;
+  if (st->k == 0) d.accept = finite;
+  else d.accept = finite && (loss <= st->f_prev - st->c_armijo * st->t * st->gn2_prev);
+  d.t_new = d.accept ? (st->k > 0 ? st->t * st->grow : st->t) : st->t * st->shrink;
+  return d;
+}
+
+// STEP: the loss is the block's own fixed-order sum of all frame-kernel
+// partials (loss_all), and the alpha update of the step follows the decision.
+template <int T, bool STEP>
+__device__ void final_reduce(const ReduceArgs& a, double loss_all) {
   __shared__ double vals[kMaxPeaks + 3];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nq = a.D + 3;   // loss, df/dalpha_m (D), |g_rho|^2, |g_u|^2
-  for (int q = w; q < nq; q += T / 32) {
+  for (int q = (STEP ? 1 : 0) + w; q < nq; q += T / 32) {
     // per-block partials: column D + 2 is the loss, columns 0..D+1 as named
     const int col = q == 0 ? a.D + 2 : q - 1;
     double v = 0.0;
@@ -119,7 +139,7 @@ __device__ void final_reduce(const ReduceArgs& a) {
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
-  const double loss = vals[0];
+  const double loss = STEP ? loss_all : vals[0];
   const double* galpha = vals + 1;
   const bool finite = isfinite(loss);
   if (!finite) atomicOr(a.err, kErrNonfinite);
@@ -134,52 +154,114 @@ __device__ void final_reduce(const ReduceArgs& a) {
   // direction (alpha_0 is not a variable)
   double gn2 = st->w_rho * galpha[a.D] + st->w_u * galpha[a.D + 1];
   for (int m = a.alpha_from; m < a.D; ++m) gn2 += st->w_alpha * galpha[m] * galpha[m];
-  bool accept;
-  if (st->k == 0) accept = finite;
-  else accept = finite && (loss <= st->f_prev - st->c_armijo * st->t * st->gn2_prev);
-  if (accept) {
-    if (st->k > 0) st->t *= st->grow;
+  const StepDecision d = step_decide(st, loss);
+  if (d.accept) {
     st->f_prev = loss;
     st->gn2_prev = gn2;
     st->n_accept += 1;
   } else {
-    st->t *= st->shrink;
     st->n_reject += 1;
   }
-  st->accepted = accept ? 1 : 0;
+  st->t = d.t_new;
+  st->accepted = d.accept ? 1 : 0;
   st->f_last = loss;
   st->k += 1;
+  if constexpr (STEP) {
+    // alpha = alpha_base - t w g_alpha_base, alpha_0 held fixed; every block
+    // has finished reading alpha
+    const StepPtrs& x = a.step;
+    for (int m = 0; m < a.D; ++m) {
+      double base, gbase;
+      if (d.accept) {
+        base = x.alpha[m];
+        gbase = galpha[m];
+        x.alpha_base[m] = (float)base;
+        x.g_alpha_base[m] = gbase;
+      } else {
+        base = x.alpha_base[m];
+        gbase = x.g_alpha_base[m];
+      }
+      x.alpha[m] = m < a.alpha_from ? (float)base : (float)(base - d.t_new * st->w_alpha * gbase);
+    }
+  }
 }
 
 constexpr int kFinishThreads = 256;
 constexpr int kFinishPixelsPerThread = 1;   // latency-bound: many warps, few pixels each
 
+// the loads of one pixel, issued together before its phase arithmetic
 template <bool PHI>
+struct PixelIn {
+  float r;
+  float uc[kMaxComp];
+  float2 Am[kMaxPeaks];
+};
+
+template <bool PHI>
+__device__ __forceinline__ void pixel_load(const FinishArgs& a, long long p, PixelIn<PHI>& in) {
+  const float2* acc = reinterpret_cast<const float2*>(a.acc);
+  in.r = a.rho[p];
+#pragma unroll
+  for (int c = 0; c < kMaxComp; ++c) in.uc[c] = !PHI && c < a.C ? a.u[c * a.npix + p] : 0.f;
+#pragma unroll
+  for (int m = 0; m < kMaxPeaks; ++m) in.Am[m] = m < a.D ? __ldcg(acc + m * a.npix + p) : make_float2(0.f, 0.f);
+}
+
+// STEP: mpbp_step's update x = x_base - t w g_base is applied here, pixel by
+// pixel, after a decision that every block takes from the same fixed-order
+// loss sum; the last block updates alpha and records the state.
+template <bool PHI, bool STEP>
 __global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a, ReduceArgs ra) {
   constexpr int NW = kFinishThreads / 32;
   constexpr int NQ = kMaxPeaks + 3;
   __shared__ double wsum[NW][NQ];
+  __shared__ double wloss[NW];
+  __shared__ double s_loss;
+  __shared__ float s_w[2];
+  __shared__ int s_accept;
   __shared__ bool last;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float ap[kMaxPeaks];   // df/dalpha_m partials of this thread
 #pragma unroll
   for (int m = 0; m < kMaxPeaks; ++m) ap[m] = 0.f;
   float n_rho = 0.f, n_u = 0.f;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  // this block's slice of the frame kernel's loss partials (FP64), issued
-  // first: nothing below depends on them
+  const long long p0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  // the frame kernel's loss partials (FP64), issued first: this block's
+  // slice of them, or with STEP all of them in a fixed order
   double lp = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n_loss_part; i += stride)
-    lp += __ldcg(a.loss_part + i);
+  if constexpr (STEP) {
+    for (long long i = threadIdx.x; i < a.n_loss_part; i += blockDim.x) lp += __ldcg(a.loss_part + i);
+  } else {
+    for (long long i = p0; i < a.n_loss_part; i += stride) lp += __ldcg(a.loss_part + i);
+  }
+  PixelIn<PHI> in;
+  if (p0 < a.npix) pixel_load<PHI>(a, p0, in);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lp += __shfl_xor_sync(0xffffffffu, lp, o);
+  bool accept = false;
+  float wr = 0.f, wu = 0.f;
+  if constexpr (STEP) {
+    if (lane == 0) wloss[w] = lp;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double L = 0.0;
+#pragma unroll
+      for (int i = 0; i < NW; ++i) L += wloss[i];
+      const StepDecision d = step_decide(ra.st, L);
+      s_loss = L;
+      s_accept = d.accept ? 1 : 0;
+      s_w[0] = (float)(d.t_new * ra.st->w_rho);
+      s_w[1] = (float)(d.t_new * ra.st->w_u);
+    }
+    __syncthreads();
+    accept = s_accept != 0;
+    wr = s_w[0];
+    wu = s_w[1];
+  }
   float2* acc = reinterpret_cast<float2*>(a.acc);
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < a.npix; p += stride) {
-    // every load of the pixel in flight before the phase arithmetic
-    const float r = a.rho[p];
-    float uc[kMaxComp];
-#pragma unroll
-    for (int c = 0; c < kMaxComp; ++c) uc[c] = !PHI && c < a.C ? a.u[c * a.npix + p] : 0.f;
-    float2 Am[kMaxPeaks];
-#pragma unroll
-    for (int m = 0; m < kMaxPeaks; ++m) Am[m] = m < a.D ? __ldcg(acc + m * a.npix + p) : make_float2(0.f, 0.f);
+  for (long long p = p0; p < a.npix; p += stride) {
+    const float r = in.r;
     float gr = 0.f, gphi2 = 0.f;
     float gu[kMaxComp] = {0.f, 0.f, 0.f};
 #pragma unroll
@@ -191,10 +273,10 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a, Re
         } else {
           float arg = 0.f;
 #pragma unroll
-          for (int c = 0; c < kMaxComp; ++c) arg = fmaf(a.pc.kpi[m][c], uc[c], arg);
+          for (int c = 0; c < kMaxComp; ++c) arg = fmaf(a.pc.kpi[m][c], in.uc[c], arg);
           sincospif(arg, &sn, &cs);
         }
-        const float2 A = Am[m];
+        const float2 A = in.Am[m];
         acc[m * a.npix + p] = make_float2(0.f, 0.f);
         const float Tr = fmaf(cs, A.x, -sn * A.y);
         const float Ti = fmaf(cs, A.y, sn * A.x);
@@ -222,12 +304,42 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a, Re
         }
       }
     }
+    if constexpr (STEP) {
+      const StepPtrs& x = ra.step;
+      float base, gbase;
+      if (accept) {
+        base = r;
+        gbase = gr;
+        x.rho_base[p] = base;
+        x.g_rho_base[p] = gbase;
+      } else {
+        base = x.rho_base[p];
+        gbase = x.g_rho_base[p];
+      }
+      x.rho[p] = fmaf(-wr, gbase, base);
+#pragma unroll
+      for (int c = 0; c < kMaxComp; ++c) {
+        if (c < a.C) {
+          const long long i = c * a.npix + p;
+          if (accept) {
+            base = in.uc[c];
+            gbase = gu[c];
+            x.u_base[i] = base;
+            x.g_u_base[i] = gbase;
+          } else {
+            base = x.u_base[i];
+            gbase = x.g_u_base[i];
+          }
+          x.u[i] = fmaf(-wu, gbase, base);
+        }
+      }
+    }
     n_rho = fmaf(gr, gr, n_rho);
     n_u += su;
+    if (p + stride < a.npix) pixel_load<PHI>(a, p + stride, in);
   }
   // partial sums: FP32 within the warp (a few pixels per lane), FP64 across
   // warps and blocks; one barrier for all D + 3 quantities
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
     if (q < a.D + 2) {
@@ -237,8 +349,6 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a, Re
       if (lane == 0) wsum[w][q] = (double)v;
     }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) lp += __shfl_xor_sync(0xffffffffu, lp, o);
   if (lane == 0) wsum[w][a.D + 2] = lp;
   __syncthreads();
   double* out = a.part + (long long)blockIdx.x * (a.D + 3);
@@ -254,51 +364,7 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a, Re
   __syncthreads();
   if (!last) return;
   __threadfence();
-  final_reduce<kFinishThreads>(ra);
-}
-
-// ----------------------------------------------------------------------------
-// A8: x = x_base - t w g_base; on acceptance the current point becomes the base
-// ----------------------------------------------------------------------------
-__global__ void step_update_kernel(StepArgs a) {
-  const mpbp_step_state* st = a.st;
-  const bool acc = st->accepted != 0;
-  const float wr = (float)(st->t * st->w_rho), wu = (float)(st->t * st->w_u);
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  const long long n_ru = a.npix * (1 + a.C);
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_ru; i += stride) {
-    const bool is_rho = i < a.npix;
-    float* x = is_rho ? a.rho + i : a.u + (i - a.npix);
-    float* xb = is_rho ? a.rho_base + i : a.u_base + (i - a.npix);
-    const float* g = is_rho ? a.g_rho + i : a.g_u + (i - a.npix);
-    float* gb = is_rho ? a.g_rho_base + i : a.g_u_base + (i - a.npix);
-    const float w = is_rho ? wr : wu;
-    float base, gbase;
-    if (acc) {
-      base = *x;
-      gbase = *g;
-      *xb = base;
-      *gb = gbase;
-    } else {
-      base = *xb;
-      gbase = *gb;
-    }
-    *x = fmaf(-w, gbase, base);
-  }
-  if (blockIdx.x == 0 && threadIdx.x < a.D) {
-    const int m = threadIdx.x;
-    double base, gbase;
-    if (acc) {
-      base = a.alpha[m];
-      gbase = a.g_alpha[m];
-      a.alpha_base[m] = (float)base;
-      a.g_alpha_base[m] = gbase;
-    } else {
-      base = a.alpha_base[m];
-      gbase = a.g_alpha_base[m];
-    }
-    a.alpha[m] = m < a.alpha_from ? (float)base : (float)(base - st->t * st->w_alpha * gbase);
-  }
+  final_reduce<kFinishThreads, STEP>(ra, STEP ? s_loss : 0.0);
 }
 
 // ----------------------------------------------------------------------------
@@ -341,13 +407,15 @@ int finish_grid(long long npix, int num_sms) {
 }
 
 cudaError_t launch_finish(const FinishArgs& a, const ReduceArgs& r, int grid, cudaStream_t s) {
-  if (a.phi) finish_kernel<true><<<grid, kFinishThreads, 0, s>>>(a, r);
-  else finish_kernel<false><<<grid, kFinishThreads, 0, s>>>(a, r);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_step_update(const StepArgs& a, int num_sms, cudaStream_t s) {
-  step_update_kernel<<<grid_for(a.npix * (1 + a.C), 256, num_sms * 8), 256, 0, s>>>(a);
+  if (a.phi) {
+    if (r.step.rho) return cudaErrorInvalidValue;   // the step updates u, not per-peak phases
+    finish_kernel<true, false><<<grid, kFinishThreads, 0, s>>>(a, r);
+  } else if (r.step.rho) {
+    if (!r.st) return cudaErrorInvalidValue;
+    finish_kernel<false, true><<<grid, kFinishThreads, 0, s>>>(a, r);
+  } else {
+    finish_kernel<false, false><<<grid, kFinishThreads, 0, s>>>(a, r);
+  }
   return cudaGetLastError();
 }
 

@@ -80,6 +80,21 @@ struct FinishArgs {
   PhaseCoef pc;
 };
 
+// The optimizer update of mpbp_step, applied by the gradient assembly itself:
+// x = x_base - t w g_base, where on acceptance the current point and its
+// gradient become the base (rho, u, alpha are the iterate, updated in place).
+struct StepPtrs {
+  float* rho;
+  float* u;
+  float* alpha;
+  float* rho_base;
+  float* u_base;
+  float* alpha_base;
+  float* g_rho_base;
+  float* g_u_base;
+  double* g_alpha_base;
+};
+
 struct ReduceArgs {
   const double* part;
   int n_part;
@@ -90,6 +105,7 @@ struct ReduceArgs {
   int* err;
   mpbp_step_state* st;  // nullable: decide an optimizer step
   int alpha_from;       // first alpha index that is a variable (1)
+  StepPtrs step;        // with st: the iterate and base point to update
 };
 
 }  // namespace mpbp
