@@ -92,6 +92,30 @@ __global__ void frame_transpose_kernel(const float* __restrict__ in, float* __re
 // ----------------------------------------------------------------------------
 constexpr int kReduceLoads = 20;   // partials per lane issued together (up to 640 blocks)
 
+// The optimizer state as one thread reads it: every field loaded at once, so
+// the reads cost one round trip and can be issued long before they are used.
+struct StepView {
+  double f_prev, gn2_prev, t, c_armijo, grow, shrink, w_rho, w_u, w_alpha;
+  int k, n_accept, n_reject;
+};
+
+__device__ __forceinline__ StepView load_state(const mpbp_step_state* st) {
+  StepView v;
+  v.f_prev = __ldcg(&st->f_prev);
+  v.gn2_prev = __ldcg(&st->gn2_prev);
+  v.t = __ldcg(&st->t);
+  v.c_armijo = __ldcg(&st->c_armijo);
+  v.grow = __ldcg(&st->grow);
+  v.shrink = __ldcg(&st->shrink);
+  v.w_rho = __ldcg(&st->w_rho);
+  v.w_u = __ldcg(&st->w_u);
+  v.w_alpha = __ldcg(&st->w_alpha);
+  v.k = __ldcg(&st->k);
+  v.n_accept = __ldcg(&st->n_accept);
+  v.n_reject = __ldcg(&st->n_reject);
+  return v;
+}
+
 // The lagged Armijo test of an optimizer step: a pure function of the state
 // and the loss at the trial point, so every block of the gradient assembly
 // reaches the same decision as the block that records it.
@@ -100,21 +124,36 @@ struct StepDecision {
   double t_new;   // step length of the next trial
 };
 
-__device__ StepDecision step_decide(const mpbp_step_state* st, double loss) {
+__device__ StepDecision step_decide(const StepView& st, double loss) {
   const bool finite = isfinite(loss);
   StepDecision d;
-  if (st->k == 0) d.accept = finite;
-  else d.accept = finite && (loss <= st->f_prev - st->c_armijo * st->t * st->gn2_prev);
-  d.t_new = d.accept ? (st->k > 0 ? st->t * st->grow : st->t) : st->t * st->shrink;
+  if (st.k == 0) d.accept = finite;
+  else d.accept = finite && (loss <= st.f_prev - st.c_armijo * st.t * st.gn2_prev);
+  d.t_new = d.accept ? (st.k > 0 ? st.t * st.grow : st.t) : st.t * st.shrink;
   return d;
 }
 
 // STEP: the loss is the block's own fixed-order sum of all frame-kernel
-// partials (loss_all), and the alpha update of the step follows the decision.
+// partials (loss_all), and the alpha update of the step follows the decision
+// (thread m updates alpha_m).  The state and the alpha values are read
+// before the partials, so their latency overlaps the partial sums.
 template <int T, bool STEP>
 __device__ void final_reduce(const ReduceArgs& a, double loss_all) {
   __shared__ double vals[kMaxPeaks + 3];
+  __shared__ int s_accept;
+  __shared__ double s_step;   // t_new * w_alpha
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  mpbp_step_state* st = a.st;
+  StepView sv{};
+  if (st && threadIdx.x == 0) sv = load_state(st);
+  const StepPtrs& x = a.step;
+  float al = 0.f, alb = 0.f;
+  double galb = 0.0;
+  if (STEP && threadIdx.x < a.D) {
+    al = __ldcg(x.alpha + threadIdx.x);
+    alb = __ldcg(x.alpha_base + threadIdx.x);
+    galb = __ldcg(x.g_alpha_base + threadIdx.x);
+  }
   const int nq = a.D + 3;   // loss, df/dalpha_m (D), |g_rho|^2, |g_u|^2
   for (int q = (STEP ? 1 : 0) + w; q < nq; q += T / 32) {
     // per-block partials: column D + 2 is the loss, columns 0..D+1 as named
@@ -122,14 +161,14 @@ __device__ void final_reduce(const ReduceArgs& a, double loss_all) {
     double v = 0.0;
     if (a.n_part <= 32 * kReduceLoads) {
       // every load of this lane in flight at once, summed in index order
-      double x[kReduceLoads];
+      double xv[kReduceLoads];
 #pragma unroll
       for (int k = 0; k < kReduceLoads; ++k) {
         const int i = lane + 32 * k;
-        x[k] = i < a.n_part ? __ldcg(a.part + (long long)i * (a.D + 3) + col) : 0.0;
+        xv[k] = i < a.n_part ? __ldcg(a.part + (long long)i * (a.D + 3) + col) : 0.0;
       }
 #pragma unroll
-      for (int k = 0; k < kReduceLoads; ++k) v += x[k];
+      for (int k = 0; k < kReduceLoads; ++k) v += xv[k];
     } else {
       for (int i = lane; i < a.n_part; i += 32) v += __ldcg(a.part + (long long)i * (a.D + 3) + col);
     }
@@ -138,50 +177,54 @@ __device__ void final_reduce(const ReduceArgs& a, double loss_all) {
     if (lane == 0) vals[q] = v;
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  const double loss = STEP ? loss_all : vals[0];
   const double* galpha = vals + 1;
-  const bool finite = isfinite(loss);
-  if (!finite) atomicOr(a.err, kErrNonfinite);
-  if (a.loss_out) *a.loss_out = loss;
-  for (int m = 0; m < a.D; ++m) {
-    if (a.g_alpha_out) a.g_alpha_out[m] = galpha[m];
-    if (a.g_alpha_ws) a.g_alpha_ws[m] = galpha[m];
+  if (threadIdx.x == 0) {
+    const double loss = STEP ? loss_all : vals[0];
+    const bool finite = isfinite(loss);
+    if (!finite) atomicOr(a.err, kErrNonfinite);
+    if (a.loss_out) *a.loss_out = loss;
+    for (int m = 0; m < a.D; ++m) {
+      if (a.g_alpha_out) a.g_alpha_out[m] = galpha[m];
+      if (a.g_alpha_ws) a.g_alpha_ws[m] = galpha[m];
+    }
+    if (st) {
+      // lagged Armijo decision in FP64; weighted squared norm of the descent
+      // direction (alpha_0 is not a variable)
+      double gn2 = sv.w_rho * galpha[a.D] + sv.w_u * galpha[a.D + 1];
+      for (int m = a.alpha_from; m < a.D; ++m) gn2 += sv.w_alpha * galpha[m] * galpha[m];
+      const StepDecision d = step_decide(sv, loss);
+      if (d.accept) {
+        st->f_prev = loss;
+        st->gn2_prev = gn2;
+        st->n_accept = sv.n_accept + 1;
+      } else {
+        st->n_reject = sv.n_reject + 1;
+      }
+      st->t = d.t_new;
+      st->accepted = d.accept ? 1 : 0;
+      st->f_last = loss;
+      st->k = sv.k + 1;
+      s_accept = d.accept ? 1 : 0;
+      s_step = d.t_new * sv.w_alpha;
+    }
   }
-  mpbp_step_state* st = a.st;
-  if (!st) return;
-  // lagged Armijo decision in FP64; weighted squared norm of the descent
-  // direction (alpha_0 is not a variable)
-  double gn2 = st->w_rho * galpha[a.D] + st->w_u * galpha[a.D + 1];
-  for (int m = a.alpha_from; m < a.D; ++m) gn2 += st->w_alpha * galpha[m] * galpha[m];
-  const StepDecision d = step_decide(st, loss);
-  if (d.accept) {
-    st->f_prev = loss;
-    st->gn2_prev = gn2;
-    st->n_accept += 1;
-  } else {
-    st->n_reject += 1;
-  }
-  st->t = d.t_new;
-  st->accepted = d.accept ? 1 : 0;
-  st->f_last = loss;
-  st->k += 1;
   if constexpr (STEP) {
     // alpha = alpha_base - t w g_alpha_base, alpha_0 held fixed; every block
     // has finished reading alpha
-    const StepPtrs& x = a.step;
-    for (int m = 0; m < a.D; ++m) {
+    __syncthreads();
+    const int m = threadIdx.x;
+    if (m < a.D) {
       double base, gbase;
-      if (d.accept) {
-        base = x.alpha[m];
+      if (s_accept) {
+        base = al;
         gbase = galpha[m];
-        x.alpha_base[m] = (float)base;
+        x.alpha_base[m] = al;
         x.g_alpha_base[m] = gbase;
       } else {
-        base = x.alpha_base[m];
-        gbase = x.g_alpha_base[m];
+        base = alb;
+        gbase = galb;
       }
-      x.alpha[m] = m < a.alpha_from ? (float)base : (float)(base - d.t_new * st->w_alpha * gbase);
+      x.alpha[m] = m < a.alpha_from ? (float)base : (float)(base - s_step * gbase);
     }
   }
 }
@@ -230,7 +273,9 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a, Re
   // the frame kernel's loss partials (FP64), issued first: this block's
   // slice of them, or with STEP all of them in a fixed order
   double lp = 0.0;
+  StepView sv{};
   if constexpr (STEP) {
+    if (threadIdx.x == 0) sv = load_state(ra.st);
     for (long long i = threadIdx.x; i < a.n_loss_part; i += blockDim.x) lp += __ldcg(a.loss_part + i);
   } else {
     for (long long i = p0; i < a.n_loss_part; i += stride) lp += __ldcg(a.loss_part + i);
@@ -248,11 +293,11 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a, Re
       double L = 0.0;
 #pragma unroll
       for (int i = 0; i < NW; ++i) L += wloss[i];
-      const StepDecision d = step_decide(ra.st, L);
+      const StepDecision d = step_decide(sv, L);
       s_loss = L;
       s_accept = d.accept ? 1 : 0;
-      s_w[0] = (float)(d.t_new * ra.st->w_rho);
-      s_w[1] = (float)(d.t_new * ra.st->w_u);
+      s_w[0] = (float)(d.t_new * sv.w_rho);
+      s_w[1] = (float)(d.t_new * sv.w_u);
     }
     __syncthreads();
     accept = s_accept != 0;
