@@ -595,8 +595,9 @@ def run_reference(args):
 
 def run_drive(args):
     """Profiling driver: set up workload `--drive K` (1, 2, 3 or 5) with
-    synthetic data and run `--drive-evals` loss+gradient evaluations, without
-    timing (for `ncu` captures of the kernels)."""
+    synthetic data and run `--drive-evals` loss+gradient evaluations, then
+    `--drive-steps` optimizer steps, without timing (for `ncu` captures of
+    the kernels)."""
     import torch
     from paper_2312_14907_gb300 import mpbp
     spec = synth.config(args.drive)
@@ -609,9 +610,15 @@ def run_drive(args):
     prob.set_precision(args.drive_precision)
     for _ in range(args.drive_evals):
         prob.loss_grad(*x)
+    if args.drive_steps:
+        overlap = (spec.m / spec.step) ** 2 * spec.npeaks
+        t0 = 1.0 / (float(np.abs(probe).max() ** 2) * overlap)
+        state = prob.step_init(t0, w_rho=1.0, w_u=1e-3, w_alpha=1e-3)
+        for _ in range(args.drive_steps):
+            prob.step(*x, state)
     torch.cuda.synchronize()
     prob.sync_status()
-    print("drove %s: %d evaluations" % (spec.name, args.drive_evals))
+    print("drove %s: %d evaluations, %d steps" % (spec.name, args.drive_evals, args.drive_steps))
 
 
 def main():
@@ -626,6 +633,7 @@ def main():
     ap.add_argument("--drive", type=int, default=0,
                     help="profiling driver: run workload 1, 2, 3 or 5 untimed")
     ap.add_argument("--drive-evals", type=int, default=4)
+    ap.add_argument("--drive-steps", type=int, default=0)
     ap.add_argument("--drive-precision", type=int, default=0,
                     help="profiling driver: 0 = FP32 FFT kernels, 1 = tensor-core DFTs (M = 64)")
     args = ap.parse_args()

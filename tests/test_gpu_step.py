@@ -68,7 +68,9 @@ def test_step_replays_against_oracle():
         assert np.allclose(x1[2], a_exp, rtol=1e-5, atol=1e-7)
         assert x1[2][0] == base_x[2][0]
     assert after.n_accept == n_acc and after.n_reject == n_rej and after.k == 14
-    assert n_acc >= 3
+    # the first trial steps overshoot on this case (the FP64 oracle's own
+    # stepper rejects 9 of 14), so both branches of the update are replayed
+    assert n_acc >= 3 and n_rej >= 3
 
 
 def test_step_decreases_loss_on_noise_free_data():
