@@ -92,6 +92,28 @@ __global__ void frame_transpose_kernel(const float* __restrict__ in, float* __re
 // ----------------------------------------------------------------------------
 constexpr int kReduceLoads = 20;   // partials per lane issued together (up to 640 blocks)
 
+// One lane's share of a fixed-order sum over n partials p[i * stride]: the
+// lane adds i = lane, lane + 32, ... in index order (all its loads in flight
+// at once when n <= 32 kReduceLoads).  Followed by a shuffle tree, the same
+// partials give the same bits in every block that sums them.
+__device__ __forceinline__ double warp_slice_sum(const double* p, long long n, long long stride, int lane) {
+  double v = 0.0;
+  if (n <= 32 * kReduceLoads) {
+    double xv[kReduceLoads];
+#pragma unroll
+    for (int k = 0; k < kReduceLoads; ++k) {
+      const int i = lane + 32 * k;
+      xv[k] = i < n ? __ldcg(p + i * stride) : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < kReduceLoads; ++k)
+      if (lane + 32 * k < n) v += xv[k];
+  } else {
+    for (long long i = lane; i < n; i += 32) v += __ldcg(p + i * stride);
+  }
+  return v;
+}
+
 // The optimizer state as one thread reads it: every field loaded at once, so
 // the reads cost one round trip and can be issued long before they are used.
 struct StepView {
@@ -158,20 +180,7 @@ __device__ void final_reduce(const ReduceArgs& a, double loss_all) {
   for (int q = (STEP ? 1 : 0) + w; q < nq; q += T / 32) {
     // per-block partials: column D + 2 is the loss, columns 0..D+1 as named
     const int col = q == 0 ? a.D + 2 : q - 1;
-    double v = 0.0;
-    if (a.n_part <= 32 * kReduceLoads) {
-      // every load of this lane in flight at once, summed in index order
-      double xv[kReduceLoads];
-#pragma unroll
-      for (int k = 0; k < kReduceLoads; ++k) {
-        const int i = lane + 32 * k;
-        xv[k] = i < a.n_part ? __ldcg(a.part + (long long)i * (a.D + 3) + col) : 0.0;
-      }
-#pragma unroll
-      for (int k = 0; k < kReduceLoads; ++k) v += xv[k];
-    } else {
-      for (int i = lane; i < a.n_part; i += 32) v += __ldcg(a.part + (long long)i * (a.D + 3) + col);
-    }
+    double v = warp_slice_sum(a.part + col, a.n_part, a.D + 3, lane);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) vals[q] = v;
@@ -258,7 +267,6 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a, Re
   constexpr int NW = kFinishThreads / 32;
   constexpr int NQ = kMaxPeaks + 3;
   __shared__ double wsum[NW][NQ];
-  __shared__ double wloss[NW];
   __shared__ double s_loss;
   __shared__ float s_w[2];
   __shared__ int s_accept;
@@ -275,26 +283,25 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a, Re
   double lp = 0.0;
   StepView sv{};
   if constexpr (STEP) {
+    // warp 0 sums all of them (the FP64 pipe is narrow; one warp's share
+    // of the adds and one shuffle tree)
     if (threadIdx.x == 0) sv = load_state(ra.st);
-    for (long long i = threadIdx.x; i < a.n_loss_part; i += blockDim.x) lp += __ldcg(a.loss_part + i);
+    if (w == 0) lp = warp_slice_sum(a.loss_part, a.n_loss_part, 1, lane);
   } else {
     for (long long i = p0; i < a.n_loss_part; i += stride) lp += __ldcg(a.loss_part + i);
   }
   PixelIn<PHI> in;
   if (p0 < a.npix) pixel_load<PHI>(a, p0, in);
+  if (!STEP || w == 0) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) lp += __shfl_xor_sync(0xffffffffu, lp, o);
+    for (int o = 16; o > 0; o >>= 1) lp += __shfl_xor_sync(0xffffffffu, lp, o);
+  }
   bool accept = false;
   float wr = 0.f, wu = 0.f;
   if constexpr (STEP) {
-    if (lane == 0) wloss[w] = lp;
-    __syncthreads();
     if (threadIdx.x == 0) {
-      double L = 0.0;
-#pragma unroll
-      for (int i = 0; i < NW; ++i) L += wloss[i];
-      const StepDecision d = step_decide(sv, L);
-      s_loss = L;
+      const StepDecision d = step_decide(sv, lp);
+      s_loss = lp;
       s_accept = d.accept ? 1 : 0;
       s_w[0] = (float)(d.t_new * sv.w_rho);
       s_w[1] = (float)(d.t_new * sv.w_u);
