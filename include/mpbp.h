@@ -207,7 +207,8 @@ mpbp_status mpbp_step(mpbp_ctx *ctx, float *rho, float *u, float *alpha,
                       mpbp_step_state *st, void *stream);
 
 /* Records one mpbp_step(ctx, rho, u, alpha, st) -- object synthesis, fused
- * frame kernel, gradient assembly with the line-search decision, update --
+ * frame kernel, gradient assembly with the line-search decision and the
+ * update --
  * as a CUDA graph owned by the context (replacing an earlier one), on a
  * stream of the context's own; nothing runs.  The pointers (dev) are baked
  * into the graph, and so are the kernels and schedule chosen at capture
@@ -218,7 +219,7 @@ mpbp_status mpbp_step_capture(mpbp_ctx *ctx, float *rho, float *u, float *alpha,
                               mpbp_step_state *st);
 
 /* Launches the captured step on `stream`: the same work as mpbp_step with
- * the captured arguments, with one launch from the host instead of four.
+ * the captured arguments, with one launch from the host instead of three.
  * MPBP_ERR_INVALID_ARG if no step has been captured. */
 mpbp_status mpbp_step_replay(mpbp_ctx *ctx, void *stream);
 
