@@ -99,6 +99,8 @@ def _load():
         lib.oracle_project_u.restype = None
         lib.oracle_illumination.argtypes = [pp, dp, dp]
         lib.oracle_illumination.restype = None
+        lib.oracle_probe_shift.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, dp]
+        lib.oracle_probe_shift.restype = None
         lib.oracle_max_threads.argtypes = []
         lib.oracle_max_threads.restype = ctypes.c_int
         _lib = lib
@@ -171,6 +173,35 @@ def dft2(x, sign=-1):
     return out
 
 
+def probe_shift(P, d0, d1):
+    """P(k - d) for a probe [M][M] and a real offset d = (d0, d1): the
+    band-limited interpolation through the DFT (see oracle_probe_shift)."""
+    lib = _load()
+    P = np.ascontiguousarray(P, dtype=np.complex128)
+    m = P.shape[0]
+    assert P.shape == (m, m)
+    out = np.empty_like(P)
+    lib.oracle_probe_shift(m, _ptr(P.view(np.float64)), float(d0), float(d1), _ptr(out.view(np.float64)))
+    return out
+
+
+def frame_probes(problem, probe, offsets):
+    """One probe per frame [D*J][M][M] for scan positions off the pixel grid:
+    frame (m, j) takes probe P_m (or the shared P) shifted by offsets[j]
+    (the fractional part d_j of s_j = n_j + d_j; the integer part is the
+    problem's scan).  Use with a problem made with probe_per_peak=2."""
+    probe = np.asarray(probe, dtype=np.complex128)
+    offsets = np.asarray(offsets, dtype=np.float64).reshape(problem.nscan, 2)
+    D, J, m = problem.npeaks, problem.nscan, problem.m
+    per_peak = probe.ndim == 3 and probe.shape[0] == D and D > 1
+    out = np.empty((D * J, m, m), np.complex128)
+    for mpk in range(D):
+        P = probe[mpk] if per_peak else probe.reshape(-1, m, m)[0]
+        for j in range(J):
+            out[mpk * J + j] = probe_shift(P, offsets[j, 0], offsets[j, 1])
+    return out
+
+
 class OracleProblem:
     """Geometry of one MPBP problem (see mpbp_oracle.c for the layouts)."""
 
@@ -182,7 +213,8 @@ class OracleProblem:
         self.ncomp, self.npeaks, self.m = ncomp, npeaks, m
         self.nscan = self.scan.shape[0]
         self.phase_scale = float(phase_scale)
-        self.probe_per_peak = bool(probe_per_peak)
+        # False / 0: one probe; True / 1: one per peak; 2: one per frame
+        self.probe_per_peak = int(probe_per_peak)
         self.c = Problem(n1, n2, ncomp, npeaks, m, self.nscan,
                          _ptr(self.G), self.scan.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                          self.phase_scale, int(probe_per_peak))

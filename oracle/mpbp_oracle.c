@@ -36,8 +36,16 @@
  *
  * Complex arrays are interleaved (re, im) doubles.  Layouts (row-major):
  *   rho [n1][n2], u [C][n1][n2], alpha [D], G [D][C], scan [J][2] (row, col of
- *   the frame's top-left pixel), probe [Dp][M][M] (Dp = D or 1), y / bg / I
- *   [D][J][M][M]; frame index f = m*J + j.
+ *   the frame's top-left pixel), probe [Dp][M][M] (Dp = 1, D, or D*J when
+ *   every frame has its own probe), y / bg / I [D][J][M][M]; frame index
+ *   f = m*J + j.
+ *
+ * Scan positions off the pixel grid (Eq. 2's lateral shift S_j by a real
+ * s_j = n_j + d_j, n_j integer, |d_j| <= 1/2): the exit wave sampled on the
+ * object's pixels r = n_j + k is P(r - s_j) O(r) = P(k - d_j) O(n_j + k), so
+ * frame j keeps the integer window n_j and takes the probe shifted by d_j,
+ * P_d(k) = P(k - d) as the band-limited (Fourier) interpolation of P
+ * (oracle_probe_shift); those probes enter as one probe per frame.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -55,8 +63,17 @@ typedef struct {
     const double *G;     /* [D][C] scattering vectors                       */
     const int *scan;     /* [J][2] top-left (row, col)                      */
     double phase_scale;  /* phi = phase_scale * G.u                         */
-    int probe_per_peak;  /* 0: one probe for all peaks; 1: [D][M][M]        */
+    int probe_per_peak;  /* 0: one probe for all peaks; 1: [D][M][M];       */
+                         /* 2: one per frame, [D*J][M][M] (frame order)     */
 } oracle_problem;
+
+/* the probe of frame (peak mpk, scan j) */
+static const double *frame_probe(const oracle_problem *p, const double *probe, int mpk, int j)
+{
+    long mm = (long)p->m * p->m;
+    if (p->probe_per_peak == 2) return probe + ((long)mpk * p->nscan + j) * 2 * mm;
+    return probe + (p->probe_per_peak ? (long)mpk * 2 * mm : 0);
+}
 
 typedef struct {
     double c_armijo;     /* sufficient-decrease constant                    */
@@ -173,7 +190,7 @@ static void exit_wave(const oracle_problem *p, const double *O, const double *pr
 {
     int m = p->m;
     long npix = (long)p->n1 * p->n2;
-    const double *P = probe + (p->probe_per_peak ? (long)mpk * 2 * m * m : 0);
+    const double *P = frame_probe(p, probe, mpk, j);
     int s0 = p->scan[2 * j], s1 = p->scan[2 * j + 1];
     for (int k0 = 0; k0 < m; ++k0) {
         for (int k1 = 0; k1 < m; ++k1) {
@@ -275,7 +292,7 @@ static double loss_grad_core(const oracle_problem *p, const double *rho, const d
         for (long i = 0; i < nlist; ++i) {
             long f = frames ? frames[i] : i;
             int mpk = (int)(f / p->nscan), j = (int)(f % p->nscan);
-            const double *P = probe + (p->probe_per_peak ? (long)mpk * 2 * mm : 0);
+            const double *P = frame_probe(p, probe, mpk, j);
             int s0 = p->scan[2 * j], s1 = p->scan[2 * j + 1];
 
             exit_wave(p, O, probe, mpk, j, psi);
@@ -723,8 +740,8 @@ void oracle_illumination(const oracle_problem *p, const double *probe, double *o
     long npix = (long)p->n1 * p->n2, mm = (long)m * m;
     for (long r = 0; r < npix; ++r) out[r] = 0.0;
     for (int mpk = 0; mpk < p->npeaks; ++mpk) {
-        const double *P = probe + (p->probe_per_peak ? (long)mpk * 2 * mm : 0);
-        for (int j = 0; j < p->nscan; ++j)
+        for (int j = 0; j < p->nscan; ++j) {
+            const double *P = frame_probe(p, probe, mpk, j);
             for (int k0 = 0; k0 < m; ++k0)
                 for (int k1 = 0; k1 < m; ++k1) {
                     int r0 = p->scan[2 * j] + k0, r1 = p->scan[2 * j + 1] + k1;
@@ -732,7 +749,35 @@ void oracle_illumination(const oracle_problem *p, const double *probe, double *o
                     long kk = (long)k0 * m + k1;
                     out[(long)r0 * p->n2 + r1] += P[2 * kk] * P[2 * kk] + P[2 * kk + 1] * P[2 * kk + 1];
                 }
+        }
     }
+}
+
+/* P_d(k) = P(k - d) for a probe [M][M] and a real offset d = (d0, d1): the
+ * band-limited interpolation, by its definition through the DFT,
+ *   P_d(k) = (1/M^2) sum_q Phat(q) exp(2 pi i q.(k - d)/M),  Phat = F P,
+ * with each frequency component q taken in [-M/2, M/2).  out [M][M]
+ * (interleaved complex, overwritten). */
+void oracle_probe_shift(int m, const double *P, double d0, double d1, double *out)
+{
+    long mm = (long)m * m;
+    double *ct = malloc(sizeof(double) * m), *st = malloc(sizeof(double) * m);
+    double *Ph = malloc(sizeof(double) * 2 * mm), *tmp = malloc(sizeof(double) * 2 * mm);
+    twiddles(m, ct, st);
+    dft2_direct(m, P, Ph, -1, ct, st, tmp);
+    for (int q0 = 0; q0 < m; ++q0)
+        for (int q1 = 0; q1 < m; ++q1) {
+            double f0 = q0 < m / 2 ? q0 : q0 - m, f1 = q1 < m / 2 ? q1 : q1 - m;
+            double a = -2.0 * M_PI * (f0 * d0 + f1 * d1) / (double)m;
+            double c = cos(a), sn = sin(a);
+            long q = (long)q0 * m + q1;
+            double xr = Ph[2 * q], xi = Ph[2 * q + 1];
+            Ph[2 * q] = xr * c - xi * sn;
+            Ph[2 * q + 1] = xr * sn + xi * c;
+        }
+    dft2_direct(m, Ph, out, +1, ct, st, tmp);
+    for (long i = 0; i < 2 * mm; ++i) out[i] /= (double)mm;
+    free(ct); free(st); free(Ph); free(tmp);
 }
 
 int oracle_max_threads(void)
