@@ -138,6 +138,29 @@ mpbp_status mpbp_get_info(const mpbp_ctx *ctx, mpbp_info *info);
  * probe_per_peak, else 1), copied into the context. */
 mpbp_status mpbp_set_probe(mpbp_ctx *ctx, const float *probe, void *stream);
 
+/* Scan positions off the pixel grid.  Eq. 2's shift S_j moves the object
+ * laterally by the scan position; for s_j = n_j + d_j (n_j the integer
+ * position of mpbp_problem.scan, |d_j| <= 1/2 per axis) the exit wave on the
+ * object's pixels r = n_j + k is P(r - s_j) O(r) = P(k - d_j) O(n_j + k), so
+ * frame j keeps its integer window and takes the probe shifted by d_j, the
+ * band-limited interpolation P_d(k) = (1/M^2) sum_q Phat(q) exp(2 pi i q.(k -
+ * d)/M), Phat = F P, q of each axis in [-M/2, M/2).  d: host [J][2] (row,
+ * column) offsets, copied; NULL returns to the integer positions.  The
+ * shifted probes (J of them, or D*J with probe_per_peak, M*M complex each,
+ * owned by the context) are formed on `stream` from the current probe, and
+ * again by every later mpbp_set_probe; every evaluation, the forward model
+ * and the illumination map use them.  MPBP_ERR_INVALID_ARG if an offset is
+ * outside [-1/2, 1/2] (or not finite), MPBP_ERR_OOM if the probes do not fit. */
+mpbp_status mpbp_set_scan_offsets(mpbp_ctx *ctx, const double *d, void *stream);
+
+/* The same band-limited shift as a standalone call: out[i] = P(k - d_i) for
+ * one probe P (dev [M][M] complex, 1 <= M <= 128) and n offsets d (host
+ * [n][2], |d| <= 1/2); out: dev [n][M][M] complex.  FP32, on the CUDA cores.
+ * Synchronous (returns after the probes are written).  MPBP_ERR_INVALID_ARG
+ * for bad sizes or offsets. */
+mpbp_status mpbp_shift_probe(const float *probe, int32_t m, const double *d, int32_t n, float *out,
+                             void *stream);
+
 /* Sets the measured intensities y of Eq. 4: dev [D][J][M][M] float counts
  * (>= 0), and the optional background b of Eq. 2 (dev, same shape, or NULL).
  * The context derives and keeps a = sqrt(y) (and b) in its own layout; the

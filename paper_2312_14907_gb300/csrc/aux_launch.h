@@ -34,9 +34,24 @@ struct IllumArgs {
   const int2* scan;      // [J]
   float* out;            // [n1][n2], zeroed before the launch
   int nframes, J, m, n1, n2;
-  long long probe_stride;   // M*M per peak, or 0
+  long long probe_stride;   // M*M per peak, or 0; kProbePerScan / kProbePerFrame
+                            // (one probe per scan position / per frame)
 };
 cudaError_t launch_illumination(const IllumArgs& a, int num_sms, cudaStream_t s);
+
+// Probes for scan positions off the pixel grid: out[i] = P_src(i)(k - d_j(i)),
+// the band-limited (DFT) interpolation of the source probe, for i = 0 ..
+// nout - 1 with j(i) = i mod J and source probe i / J when per_peak (out
+// holds D*J probes), else j = i and the single source probe (J probes).
+struct ProbeShiftArgs {
+  const cf* src;        // [1 or D][M][M]
+  cf* out;              // [nout][M][M]
+  const float2* d;      // [J] offsets (row, col), |d| <= 1/2
+  int nout, J, m;
+  bool per_peak;
+};
+bool probe_shift_prepare(int m);
+cudaError_t launch_probe_shift(const ProbeShiftArgs& a, cudaStream_t s);
 
 cudaError_t launch_object_build(const ObjectArgs& a, int num_sms, cudaStream_t s);
 // out[i] = in[i] for n 16-bit counts

@@ -147,7 +147,7 @@ MPBP_DI void t4_frame(const FrameArgs& p, const T4Group<M>& g, const FrameRef& c
   const int ln = g.ln, h = g.h;
   auto x8 = [](cf v) { return xchg8(v); };
   auto x16 = [](cf v) { return xchg16(v); };
-  const cf* P = p.probe + cur.mpk * p.probe_stride;
+  const cf* P = frame_probe(p, cur, M * M);
   const int col = cur.s.y + ln;
   const bool cok = cur.valid && col >= 0 && col < p.n2;
   if constexpr (TMA) {

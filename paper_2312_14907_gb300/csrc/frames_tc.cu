@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) frames_tc64(const FrameArgs p, 
   for (; it < p.nframes && G.ok; it += stride) {
     const FrameRef nxt = frame_ref(p, it + stride);
     const bool has_next = it + stride < p.nframes;
-    const cf* P = p.probe + cur.mpk * p.probe_stride;
+    const cf* P = frame_probe(p, cur, TM * TM);
     cp_async_wait_all();
     group_bar(G.id);
 

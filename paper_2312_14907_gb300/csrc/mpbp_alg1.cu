@@ -100,7 +100,9 @@ __global__ void illumination_kernel(IllumArgs a) {
     const int k0 = (int)(k / a.m), k1 = (int)(k - (long long)k0 * a.m);
     const int r0 = a.scan[j].x + k0, r1 = a.scan[j].y + k1;
     if (r0 < 0 || r0 >= a.n1 || r1 < 0 || r1 >= a.n2) continue;
-    const float2 P = reinterpret_cast<const float2*>(a.probe)[mk * a.probe_stride + k];
+    const long long pi = a.probe_stride >= 0 ? mk * a.probe_stride
+                         : (a.probe_stride == kProbePerFrame ? f : j) * mm;
+    const float2 P = reinterpret_cast<const float2*>(a.probe)[pi + k];
     atomicAdd(a.out + (long long)r0 * a.n2 + r1, P.x * P.x + P.y * P.y);
   }
 }

@@ -106,6 +106,13 @@ struct mpbp_ctx {
   cudaEvent_t ev_done[2] = {nullptr, nullptr};
   bool has_probe = false, has_data = false;
   bool acc_dirty = false;
+  // scan positions off the pixel grid (mpbp_set_scan_offsets): the offsets
+  // d_j (empty: integer positions) and the probes shifted by them, one per
+  // scan position (shared probe) or per frame (one probe per peak)
+  std::vector<float2> scan_off_h;
+  float2* scan_off = nullptr;   // [J]
+  cf* probe_scan = nullptr;     // [J or D*J][M][M]
+  bool shift_ready = false;
   // optional event timing of the fused frame kernel
   bool timing = false;
   // Alg. 1: Adam moments and the materialised rho, alpha (mpbp_adam_init)
@@ -277,7 +284,45 @@ FrameArgs frame_args(mpbp_ctx* c, const int* frames, int nframes) {
   a.n2 = c->n2;
   a.J = c->J;
   a.probe_stride = c->probe_per_peak ? c->M * c->M : 0;
+  if (!c->scan_off_h.empty()) {
+    a.probe = c->probe_scan;
+    a.probe_stride = c->probe_per_peak ? kProbePerFrame : kProbePerScan;
+  }
   return a;
+}
+
+// the probes of the context's scan offsets from its probe (after either changed)
+mpbp_status enqueue_probe_shift(mpbp_ctx* c, cudaStream_t s) {
+  if (c->scan_off_h.empty() || !c->has_probe) return MPBP_OK;
+  const long long n = c->probe_per_peak ? c->nframes : c->J;
+  if (!c->probe_scan) {
+    if (cudaMalloc(&c->scan_off, sizeof(float2) * c->J) != cudaSuccess ||
+        cudaMalloc(&c->probe_scan, sizeof(cf) * n * c->M * c->M) != cudaSuccess) {
+      cudaGetLastError();
+      if (c->scan_off) cudaFree(c->scan_off);
+      if (c->probe_scan) cudaFree(c->probe_scan);
+      c->scan_off = nullptr;
+      c->probe_scan = nullptr;
+      c->scan_off_h.clear();
+      return fail(c, MPBP_ERR_OOM, "probes of the scan offsets");
+    }
+  }
+  if (!c->shift_ready) {
+    if (!probe_shift_prepare(c->M)) return fail(c, MPBP_ERR_CUDA, "probe shift kernel");
+    c->shift_ready = true;
+  }
+  MPBP_CUDA(c, cudaMemcpyAsync(c->scan_off, c->scan_off_h.data(), sizeof(float2) * c->J,
+                               cudaMemcpyHostToDevice, s));
+  ProbeShiftArgs a{};
+  a.src = c->probe;
+  a.out = c->probe_scan;
+  a.d = c->scan_off;
+  a.nout = (int)n;
+  a.J = c->J;
+  a.m = c->M;
+  a.per_peak = c->probe_per_peak != 0;
+  MPBP_CUDA(c, launch_probe_shift(a, s));
+  return MPBP_OK;
 }
 
 mpbp_status enqueue_object_build(mpbp_ctx* c, const float* rho, const float* u,
@@ -499,6 +544,8 @@ void mpbp_destroy(mpbp_ctx* c) {
   }
   if (c->ws) cudaFree(c->ws);
   if (c->io_x) cudaFree(c->io_x);
+  if (c->scan_off) cudaFree(c->scan_off);
+  if (c->probe_scan) cudaFree(c->probe_scan);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   if (c->ev_ready) cudaEventDestroy(c->ev_ready);
   if (c->ev_x) cudaEventDestroy(c->ev_x);
@@ -590,6 +637,59 @@ mpbp_status mpbp_set_probe(mpbp_ctx* c, const float* probe, void* stream) {
                                cudaMemcpyDeviceToDevice, S(stream)));
   c->has_probe = true;
   c->version++;
+  return enqueue_probe_shift(c, S(stream));
+}
+
+mpbp_status mpbp_set_scan_offsets(mpbp_ctx* c, const double* d, void* stream) {
+  if (!c) return MPBP_ERR_INVALID_ARG;
+  if (!d) {
+    c->scan_off_h.clear();
+    c->version++;
+    return MPBP_OK;
+  }
+  std::vector<float2> h(c->J);
+  for (int j = 0; j < c->J; ++j) {
+    const double a = d[2 * j], b = d[2 * j + 1];
+    if (!(std::fabs(a) <= 0.5) || !(std::fabs(b) <= 0.5))
+      return fail(c, MPBP_ERR_INVALID_ARG, "scan offsets must lie in [-1/2, 1/2]");
+    h[j] = make_float2((float)a, (float)b);
+  }
+  c->scan_off_h.swap(h);
+  c->version++;
+  return enqueue_probe_shift(c, S(stream));
+}
+
+mpbp_status mpbp_shift_probe(const float* probe, int32_t m, const double* d, int32_t n, float* out,
+                             void* stream) {
+  if (!probe || !d || !out || n < 0 || m < 1 || m > 128) return MPBP_ERR_INVALID_ARG;
+  if (n == 0) return MPBP_OK;
+  std::vector<float2> h(n);
+  for (int j = 0; j < n; ++j) {
+    if (!(std::fabs(d[2 * j]) <= 0.5) || !(std::fabs(d[2 * j + 1]) <= 0.5)) return MPBP_ERR_INVALID_ARG;
+    h[j] = make_float2((float)d[2 * j], (float)d[2 * j + 1]);
+  }
+  float2* dd = nullptr;
+  if (cudaMalloc(&dd, sizeof(float2) * n) != cudaSuccess) {
+    cudaGetLastError();
+    return MPBP_ERR_OOM;
+  }
+  cudaStream_t s = S(stream);
+  ProbeShiftArgs a{};
+  a.src = reinterpret_cast<const cf*>(probe);
+  a.out = reinterpret_cast<cf*>(out);
+  a.d = dd;
+  a.nout = n;
+  a.J = n;
+  a.m = m;
+  a.per_peak = false;
+  const bool ok = cudaMemcpyAsync(dd, h.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+                  probe_shift_prepare(m) && launch_probe_shift(a, s) == cudaSuccess &&
+                  cudaStreamSynchronize(s) == cudaSuccess;
+  cudaFree(dd);
+  if (!ok) {
+    cudaGetLastError();
+    return MPBP_ERR_CUDA;
+  }
   return MPBP_OK;
 }
 
@@ -1250,6 +1350,10 @@ mpbp_status mpbp_illumination(mpbp_ctx* c, float* out, void* stream) {
   a.n1 = c->n1;
   a.n2 = c->n2;
   a.probe_stride = c->probe_per_peak ? (long long)c->M * c->M : 0;
+  if (!c->scan_off_h.empty()) {
+    a.probe = c->probe_scan;
+    a.probe_stride = c->probe_per_peak ? kProbePerFrame : kProbePerScan;
+  }
   MPBP_CUDA(c, launch_illumination(a, c->num_sms, s));
   return MPBP_OK;
 }

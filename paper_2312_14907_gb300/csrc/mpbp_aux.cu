@@ -420,6 +420,107 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a, Re
 }
 
 // ----------------------------------------------------------------------------
+// Probes for scan positions off the pixel grid (Eq. 2's shift S_j at a real
+// position s_j = n_j + d_j): frame j keeps the integer window n_j and takes
+// P(k - d_j).  With the frequencies of each axis in [-M/2, M/2) the
+// band-limited interpolation is separable,
+//   P_d(k0, k1) = sum_{k0', k1'} D(k0 - k0' - d0) D(k1 - k1' - d1) P(k0', k1'),
+//   D(y) = (1/M) sum_q exp(2 pi i q y / M) = sin(pi y) / (M sin(pi y / M)) exp(-i pi y / M),
+// D(0) = 1 and D(n) = 0 at the other integers.  One block per output probe:
+// the probe in shared memory, one pass along k1 (a warp per row), one along
+// k0 (a warp per column), each output a length-M sum in FP32.
+// ----------------------------------------------------------------------------
+constexpr int kShiftThreads = 256;
+
+__device__ float2 interp_weight(float y, int m) {
+  if (y == 0.0f) return make_float2(1.0f, 0.0f);
+  const float a = sinpif(y) / ((float)m * sinpif(y / (float)m));
+  float sn, cs;
+  sincospif(-y / (float)m, &sn, &cs);
+  return make_float2(a * cs, a * sn);
+}
+
+__device__ __forceinline__ float2 cfma(float2 w, float2 v, float2 acc) {
+  acc.x = fmaf(w.x, v.x, fmaf(-w.y, v.y, acc.x));
+  acc.y = fmaf(w.x, v.y, fmaf(w.y, v.x, acc.y));
+  return acc;
+}
+
+__global__ void __launch_bounds__(kShiftThreads) probe_shift_kernel(ProbeShiftArgs a) {
+  extern __shared__ float2 sm[];   // w0 [2M], w1 [2M], buf [M][M + 1]
+  const int m = a.m, ld = m + 1;
+  const int i = blockIdx.x;
+  const int j = a.per_peak ? i % a.J : i;
+  const int src = a.per_peak ? i / a.J : 0;
+  float2* w0 = sm;
+  float2* w1 = sm + 2 * m;
+  float2* buf = sm + 4 * m;
+  const float2 d = a.d[j];
+  for (int t = threadIdx.x; t < 2 * m - 1; t += blockDim.x) {
+    const float x = (float)(t - (m - 1));   // k - k'
+    w0[t] = interp_weight(x - d.x, m);
+    w1[t] = interp_weight(x - d.y, m);
+  }
+  const float2* P = reinterpret_cast<const float2*>(a.src) + (size_t)src * m * m;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) buf[(e / m) * ld + e % m] = P[e];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  // along k1: warp per row, lane outputs k1 = lane + 32 u (M <= 128)
+  for (int r = warp; r < m; r += nw) {
+    float2 o[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = lane + 32 * u;
+      float2 acc = make_float2(0.0f, 0.0f);
+      if (c < m)
+        for (int cp = 0; cp < m; ++cp) acc = cfma(w1[c - cp + m - 1], buf[r * ld + cp], acc);
+      o[u] = acc;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (lane + 32 * u < m) buf[r * ld + lane + 32 * u] = o[u];
+    __syncwarp();
+  }
+  __syncthreads();
+  // along k0: warp per column
+  for (int c = warp; c < m; c += nw) {
+    float2 o[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = lane + 32 * u;
+      float2 acc = make_float2(0.0f, 0.0f);
+      if (r < m)
+        for (int rp = 0; rp < m; ++rp) acc = cfma(w0[r - rp + m - 1], buf[rp * ld + c], acc);
+      o[u] = acc;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (lane + 32 * u < m) buf[(lane + 32 * u) * ld + c] = o[u];
+    __syncwarp();
+  }
+  __syncthreads();
+  float2* out = reinterpret_cast<float2*>(a.out) + (size_t)i * m * m;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) out[e] = buf[(e / m) * ld + e % m];
+}
+
+static int probe_shift_smem(int m) { return (int)sizeof(float2) * (4 * m + m * (m + 1)); }
+
+bool probe_shift_prepare(int m) {
+  if (m < 1 || m > 128) return false;
+  return cudaFuncSetAttribute(probe_shift_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              probe_shift_smem(m)) == cudaSuccess;
+}
+
+cudaError_t launch_probe_shift(const ProbeShiftArgs& a, cudaStream_t s) {
+  if (a.m < 1 || a.m > 128 || a.nout < 0) return cudaErrorInvalidValue;
+  if (a.nout == 0) return cudaSuccess;
+  probe_shift_kernel<<<a.nout, kShiftThreads, probe_shift_smem(a.m), s>>>(a);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
 // launchers
 // ----------------------------------------------------------------------------
 static int grid_for(long long n, int threads, int cap) {

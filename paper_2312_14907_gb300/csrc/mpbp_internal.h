@@ -16,6 +16,10 @@ constexpr int kErrBounds = 1;
 constexpr int kErrNonfinite = 2;
 constexpr int kErrTimeout = 4;     // a bounded wait on the GPU ran out
 
+// FrameArgs::probe_stride codes for probes that vary with the scan position
+constexpr int kProbePerScan = -1;
+constexpr int kProbePerFrame = -2;
+
 // Arguments of the fused per-frame kernel (A2..A7 of the hot path).
 struct FrameArgs {
   const cf* O;          // [D][n1][n2] objects O_m
@@ -35,7 +39,10 @@ struct FrameArgs {
   int frame0;           // without a frame list: frames frame0 .. frame0 + nframes - 1
   int nframes_total;    // D*J (bound for frame indices)
   int n1, n2, J;
-  int probe_stride;     // M*M when one probe per peak, else 0
+  int probe_stride;     // M*M when one probe per peak, 0 when one for all;
+                        // kProbePerScan / kProbePerFrame: one per scan
+                        // position j / per frame f, M*M apart (scan
+                        // positions off the pixel grid)
   // raw-data variant of the gradient kernel (M >= 32): the measured counts
   // y (natural layout [q0][q1], frame f at yraw + f*M*M) are read instead of
   // the context's sqrt(y), and sqrt(y) is written to aT_w in the context's

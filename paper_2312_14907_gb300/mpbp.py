@@ -80,7 +80,8 @@ EXPORTS = ["mpbp_status_string", "mpbp_create", "mpbp_destroy", "mpbp_last_error
            "mpbp_set_precision", "mpbp_step_capture", "mpbp_step_replay",
            "mpbp_adam_init", "mpbp_adam_step", "mpbp_adam_get_state", "mpbp_adam_set_state",
            "mpbp_loss_grad_phases", "mpbp_unwrap_phases", "mpbp_project_displacement",
-           "mpbp_illumination", "mpbp_set_test_stall", "mpbp_loss_grad_host_counts16"]
+           "mpbp_illumination", "mpbp_set_test_stall", "mpbp_loss_grad_host_counts16",
+           "mpbp_set_scan_offsets", "mpbp_shift_probe"]
 
 PRECISION_FP32 = 0        # FFTs on the CUDA cores
 PRECISION_TC_SPLIT16 = 1  # dense DFT matrices on the tensor cores, split FP16
@@ -173,6 +174,10 @@ def load(build_if_missing=True):
     lib.mpbp_frames_timing_read.restype = st
     lib.mpbp_loss_grad_noalloc.argtypes = [P(_Problem), V, V, V, V, V, V, V, V, V, V]
     lib.mpbp_loss_grad_noalloc.restype = st
+    lib.mpbp_set_scan_offsets.argtypes = [V, V, V]
+    lib.mpbp_set_scan_offsets.restype = st
+    lib.mpbp_shift_probe.argtypes = [V, I32, V, I32, V, V]
+    lib.mpbp_shift_probe.restype = st
     _lib = lib
     return lib
 
@@ -298,6 +303,19 @@ class Problem:
         _dev(probe, torch.complex64, shape, "probe")
         self._probe = probe
         self._check(self._lib.mpbp_set_probe(self._h, _p(probe), _stream()), "mpbp_set_probe")
+
+    def set_scan_offsets(self, d):
+        """Scan positions off the pixel grid: d [J][2] (row, column) offsets in
+        [-1/2, 1/2] added to the integer scan (mpbp_set_scan_offsets), or None."""
+        if d is None:
+            self._check(self._lib.mpbp_set_scan_offsets(self._h, None, _stream()), "mpbp_set_scan_offsets")
+            return
+        d = np.ascontiguousarray(d, dtype=np.float64)
+        if d.shape != (self.nscan, 2):
+            raise MPBPError(1, "scan offsets: expected shape (%d, 2), got %s" % (self.nscan, d.shape))
+        self._offsets = d
+        self._check(self._lib.mpbp_set_scan_offsets(self._h, d.ctypes.data, _stream()),
+                    "mpbp_set_scan_offsets")
 
     def set_data(self, y, bg=None):
         _dev(y, torch.float32, self.shapes["frames"], "y")
@@ -511,6 +529,20 @@ class Problem:
         s = self._lib.mpbp_sync_status(self._h, _stream())
         if s != 0:
             raise MPBPError(s, self._lib.mpbp_last_error(self._h).decode())
+
+
+def shift_probe(probe, d):
+    """P(k - d_i) for one probe (cuda complex64 [M][M]) and offsets d [n][2]
+    in [-1/2, 1/2] (mpbp_shift_probe); returns cuda complex64 [n][M][M]."""
+    lib = load()
+    m = probe.shape[0]
+    _dev(probe, torch.complex64, (m, m), "probe")
+    d = np.ascontiguousarray(d, dtype=np.float64).reshape(-1, 2)
+    out = torch.empty((d.shape[0], m, m), dtype=torch.complex64, device=probe.device)
+    s = lib.mpbp_shift_probe(_p(probe), m, d.ctypes.data, d.shape[0], _p(out), _stream())
+    if s != 0:
+        raise MPBPError(s, "mpbp_shift_probe")
+    return out
 
 
 def loss_grad_batched(problems, states, outs=None):
