@@ -413,6 +413,37 @@ def run_gpu(args):
             "tensor_flops_per_frame": tc_flops,
             "tensor_peak_tflops": pk["bf16_tflops"], "peak_src": pk["src"] + " (dense bf16 = fp16 rate)"}
         prob.set_precision(mpbp.PRECISION_FP32)
+    # scan positions off the pixel grid (not the headline): seeded offsets in
+    # [-1/2, 1/2] per scan position, one shifted probe per position; loss and
+    # gradient evaluations on the same state, CUDA events, L2 flushed between
+    d_off = np.random.default_rng(spec.seed + 77).uniform(-0.5, 0.5, (scan.shape[0], 2))
+    torch.cuda.synchronize()
+    ts0 = time.perf_counter()
+    prob.set_scan_offsets(d_off)
+    torch.cuda.synchronize()
+    setup_ms = 1e3 * (time.perf_counter() - ts0)
+    xs = [t.clone() for t in x]
+    for _ in range(args.warmup):
+        prob.loss_grad(*xs)
+    n_sp = max(3, min(args.steps, 20))
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_sp)]
+    prob.frames_timing(True)
+    torch.cuda.synchronize()
+    for k in range(n_sp):
+        flush.zero_()
+        evs[k][0].record(stream)
+        prob.loss_grad(*xs)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    prob.frames_timing(False)
+    sk_ms, sk_n = prob.frames_timing_read()
+    prob.set_scan_offsets(None)
+    prob.sync_status()
+    sp_ms = sum(a.elapsed_time(b) for a, b in evs) / n_sp
+    line["subpixel_scan"] = {
+        "what": "loss + gradient with seeded scan offsets in [-1/2, 1/2] (one shifted probe per scan position)",
+        "ms_per_eval": sp_ms, "value": spec.nframes / (sp_ms / 1e3), "unit": UNIT,
+        "kernel_ms": sk_ms / max(sk_n, 1), "probe_setup_ms": setup_ms}
     # the unfused comparison path on the same data and state
     line["unfused_torch"] = unfused_comparison(torch, prob, spec, scan, probe, y, x, flush, stream)
     # the paper's own iteration (Alg. 1 without its projector): minibatches
