@@ -289,33 +289,49 @@ __global__ void __launch_bounds__(kUnwrapThreads) unwrap_kernel(UnwrapArgs a) {
     if (!grid_sync(a)) return;
     const bool any = *(volatile int*)&a.flags[fs] != 0;
     ++flag_it;
-    for (long long r = tid; r < n; r += stride) {
-      if (a.hook_parent[r] >= 0) {
-        P[r] = a.hook_parent[r];
-        O[r] = a.hook_off[r];
-      }
-      a.best[r] = 0ull;   // every decision that read it is behind the last barrier
-    }
-    if (!grid_sync(a)) return;
     if (!any) break;
-    // pointer jumping until every node points at its root (an acyclic
-    // forest of n nodes needs at most log2(n) + 1 passes; the cap only
-    // guards against a forest that is not)
+    // pointer jumping until every node points at its root, four hops a pass
+    // (the depth shrinks fourfold per pass; an acyclic forest of n nodes
+    // needs at most log4(n) + 1 passes, the cap only guards against a forest
+    // that is not).  The first pass reads the forest with this round's hooks
+    // applied (a hooked root's parent and offset from hook_parent/hook_off)
+    // and clears best[]: every decision that read it is behind the barrier.
     for (int jump = 0;; ++jump) {
       if (jump > 64) {
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(a.err, kErrTimeout);
         break;
       }
-      int* Pi = par[cur];
-      int* Oi = off[cur];
+      const bool first = jump == 0;
+      const int* Pi = par[cur];
+      const int* Oi = off[cur];
       int* Po = par[cur ^ 1];
       int* Oo = off[cur ^ 1];
+      auto up = [&](int x, int& o) {   // parent of x, o = x's offset to it
+        if (first) {
+          const int h = a.hook_parent[x];
+          if (h >= 0) {
+            o = a.hook_off[x];
+            return h;
+          }
+        }
+        o = Oi[x];
+        return Pi[x];
+      };
       const int fj = flag_it % 3;
       for (long long v = tid; v < n; v += stride) {
-        const int p = Pi[v], pp = Pi[p];
-        Po[v] = pp;
-        Oo[v] = Oi[v] + (pp != p ? Oi[p] : 0);
-        if (pp != p) a.flags[fj] = 1;
+        int o1, o2, o3, o4;
+        const int p1 = up((int)v, o1);
+        const int p2 = up(p1, o2);
+        const int p3 = up(p2, o3);
+        const int p4 = up(p3, o4);
+        int ov = o1;
+        if (p2 != p1) ov += o2;
+        if (p3 != p2) ov += o3;
+        if (p4 != p3) ov += o4;
+        Po[v] = p4;
+        Oo[v] = ov;
+        if (p4 != p1) a.flags[fj] = 1;
+        if (first) a.best[v] = 0ull;
       }
       next_flag();
       if (!grid_sync(a)) return;
