@@ -293,7 +293,8 @@ __global__ void __launch_bounds__(kUnwrapThreads) unwrap_kernel(UnwrapArgs a) {
     // pointer jumping until every node points at its root, four hops a pass
     // (the depth shrinks fourfold per pass; an acyclic forest of n nodes
     // needs at most log4(n) + 1 passes, the cap only guards against a forest
-    // that is not).  The first pass reads the forest with this round's hooks
+    // that is not), stopping after the pass that leaves every node under a
+    // root.  The first pass reads the forest with this round's hooks
     // applied (a hooked root's parent and offset from hook_parent/hook_off)
     // and clears best[]: every decision that read it is behind the barrier.
     for (int jump = 0;; ++jump) {
@@ -330,7 +331,9 @@ __global__ void __launch_bounds__(kUnwrapThreads) unwrap_kernel(UnwrapArgs a) {
         if (p4 != p3) ov += o4;
         Po[v] = p4;
         Oo[v] = ov;
-        if (p4 != p1) a.flags[fj] = 1;
+        // another pass only if the new parent is not a root (a root stays one)
+        int o5;
+        if (up(p4, o5) != p4) a.flags[fj] = 1;
         if (first) a.best[v] = 0ull;
       }
       next_flag();
