@@ -238,6 +238,7 @@ __global__ void __launch_bounds__(kUnwrapThreads) unwrap_kernel(UnwrapArgs a) {
   for (long long v = tid; v < n; v += stride) {
     a.rel[v] = reliability(a, v);
     a.best[v] = 0ull;
+    a.minnode[v] = INT_MAX;   // read only by the closing phase
   }
   if (!grid_sync(a)) return;
   // edge keys (0: no edge), computed once
@@ -348,8 +349,6 @@ __global__ void __launch_bounds__(kUnwrapThreads) unwrap_kernel(UnwrapArgs a) {
   // each group's lowest-numbered node keeps its wrapped value
   int* P = par[cur];
   int* O = off[cur];
-  for (long long v = tid; v < n; v += stride) a.minnode[v] = INT_MAX;
-  if (!grid_sync(a)) return;
   for (long long v = tid; v < n; v += stride) atomicMin(&a.minnode[P[v]], (int)v);
   if (!grid_sync(a)) return;
   for (long long v = tid; v < n; v += stride) {
