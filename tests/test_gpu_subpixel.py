@@ -164,3 +164,28 @@ def test_offsets_outside_half_a_pixel_are_rejected():
     d[2, 1] = np.nan
     with pytest.raises(mpbp.MPBPError):
         p.set_scan_offsets(d)
+
+
+def test_batched_problems_with_offsets():
+    """Persistent launches over several problems: each problem's frames use
+    its own shifted probes (every batch schedule)."""
+    from paper_2312_14907_gb300 import mpbp
+    cases = [Case(*custom_spec(96, 32, 5, 14, npeaks=3, offset=-2, seed=1), state="perturbed"),
+             Case(*custom_spec(160, 64, 4, 30, npeaks=2, offset=-5, seed=2), state="perturbed"),
+             Case(*custom_spec(200, 128, 2, 60, npeaks=3, offset=-10, seed=3), state="perturbed")]
+    offs = [_offsets(c.scan.shape[0], 40 + i) if i != 1 else None for i, c in enumerate(cases)]
+    refs = []
+    for c, d in zip(cases, offs):
+        if d is None:
+            refs.append(c.oracle_loss_grad())
+        else:
+            p2, Pf = _oracle_frames(c, d)
+            refs.append(p2.loss_grad(c.rho, c.u, c.alpha, Pf, c.y))
+    probs, states = zip(*[_gpu(c, d) for c, d in zip(cases, offs)])
+    for mode in (0, 1, 2, 3):
+        probs[0].set_batch_schedule(mode, 0)
+        outs = mpbp.loss_grad_batched(list(probs), list(states))
+        for o, r in zip(outs, refs):
+            _check(o, r)
+    for p in probs:
+        p.sync_status()
