@@ -150,7 +150,9 @@ mpbp_status mpbp_set_probe(mpbp_ctx *ctx, const float *probe, void *stream);
  * owned by the context) are formed on `stream` from the current probe, and
  * again by every later mpbp_set_probe; every evaluation, the forward model
  * and the illumination map use them.  MPBP_ERR_INVALID_ARG if an offset is
- * outside [-1/2, 1/2] (or not finite), MPBP_ERR_OOM if the probes do not fit. */
+ * outside [-1/2, 1/2] (or not finite); MPBP_ERR_OOM if the probes do not
+ * fit and MPBP_ERR_CUDA if they cannot be formed, after which the context
+ * is back at the integer positions. */
 mpbp_status mpbp_set_scan_offsets(mpbp_ctx *ctx, const double *d, void *stream);
 
 /* The same band-limited shift as a standalone call: out[i] = P(k - d_i) for

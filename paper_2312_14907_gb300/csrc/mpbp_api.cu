@@ -307,12 +307,7 @@ mpbp_status enqueue_probe_shift(mpbp_ctx* c, cudaStream_t s) {
       return fail(c, MPBP_ERR_OOM, "probes of the scan offsets");
     }
   }
-  if (!c->shift_ready) {
-    if (!probe_shift_prepare(c->M)) return fail(c, MPBP_ERR_CUDA, "probe shift kernel");
-    c->shift_ready = true;
-  }
-  MPBP_CUDA(c, cudaMemcpyAsync(c->scan_off, c->scan_off_h.data(), sizeof(float2) * c->J,
-                               cudaMemcpyHostToDevice, s));
+  if (!c->shift_ready) c->shift_ready = probe_shift_prepare(c->M);
   ProbeShiftArgs a{};
   a.src = c->probe;
   a.out = c->probe_scan;
@@ -321,7 +316,15 @@ mpbp_status enqueue_probe_shift(mpbp_ctx* c, cudaStream_t s) {
   a.J = c->J;
   a.m = c->M;
   a.per_peak = c->probe_per_peak != 0;
-  MPBP_CUDA(c, launch_probe_shift(a, s));
+  if (!c->shift_ready ||
+      cudaMemcpyAsync(c->scan_off, c->scan_off_h.data(), sizeof(float2) * c->J, cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      launch_probe_shift(a, s) != cudaSuccess) {
+    // no shifted probes: back to the integer positions rather than stale probes
+    cudaGetLastError();
+    c->scan_off_h.clear();
+    return fail(c, MPBP_ERR_CUDA, "shifting the probe for the scan offsets");
+  }
   return MPBP_OK;
 }
 
