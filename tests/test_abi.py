@@ -63,3 +63,25 @@ def test_invalid_geometry_is_rejected_on_the_host(lib):
                           scan.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), 0, 6.28)
     assert lib.mpbp_create(ctypes.byref(bad_d), ctypes.byref(h)) == 1      # no peaks
     assert h.value is None
+
+
+def test_probe_shift_arguments_are_checked_on_the_host(lib):
+    """mpbp_shift_probe validates sizes and offsets before any device call."""
+    import numpy as np
+    V = ctypes.c_void_p
+    lib.mpbp_shift_probe.argtypes = [V, ctypes.c_int32, V, ctypes.c_int32, V, V]
+    lib.mpbp_shift_probe.restype = ctypes.c_int
+    d = np.zeros((2, 2))
+    fake = ctypes.c_void_p(16)   # never dereferenced: every call below fails its checks first
+    assert lib.mpbp_shift_probe(None, 8, d.ctypes.data, 2, fake, None) == 1
+    assert lib.mpbp_shift_probe(fake, 0, d.ctypes.data, 2, fake, None) == 1
+    assert lib.mpbp_shift_probe(fake, 129, d.ctypes.data, 2, fake, None) == 1
+    assert lib.mpbp_shift_probe(fake, 8, d.ctypes.data, -1, fake, None) == 1
+    for bad in (0.5000001, -0.75, np.nan, np.inf):
+        d[1, 0] = bad
+        assert lib.mpbp_shift_probe(fake, 8, d.ctypes.data, 2, fake, None) == 1
+    d[1, 0] = 0.5
+    assert lib.mpbp_shift_probe(fake, 8, d.ctypes.data, 0, fake, None) == 0   # nothing to do
+    lib.mpbp_set_scan_offsets.argtypes = [V, V, V]
+    lib.mpbp_set_scan_offsets.restype = ctypes.c_int
+    assert lib.mpbp_set_scan_offsets(None, d.ctypes.data, None) == 1
