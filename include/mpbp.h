@@ -236,8 +236,11 @@ mpbp_status mpbp_step(mpbp_ctx *ctx, float *rho, float *u, float *alpha,
  * update --
  * as a CUDA graph owned by the context (replacing an earlier one), on a
  * stream of the context's own; nothing runs.  The pointers (dev) are baked
- * into the graph, and so are the kernels and schedule chosen at capture
- * (later mpbp_set_precision / mpbp_set_schedule calls need a new capture).
+ * into the graph, and so are the kernels, the schedule and the probes
+ * (scan offsets) in force at capture (later mpbp_set_precision,
+ * mpbp_set_schedule or mpbp_set_scan_offsets calls need a new capture; a new
+ * probe of the same kind is picked up, since the graph reads the context's
+ * probe buffers).
  * Frame-kernel timing (mpbp_frames_timing) must be off.  Synchronous.
  * MPBP_ERR_CUDA if capture or instantiation fails. */
 mpbp_status mpbp_step_capture(mpbp_ctx *ctx, float *rho, float *u, float *alpha,
