@@ -627,8 +627,8 @@ def run_reference(args):
 def run_drive(args):
     """Profiling driver: set up workload `--drive K` (1, 2, 3 or 5) with
     synthetic data and run `--drive-evals` loss+gradient evaluations, then
-    `--drive-steps` optimizer steps, without timing (for `ncu` captures of
-    the kernels)."""
+    `--drive-steps` optimizer steps (and `--drive-projector` calls of the
+    projector Pi_U), without timing (for `ncu` captures of the kernels)."""
     import torch
     from paper_2312_14907_gb300 import mpbp
     spec = synth.config(args.drive)
@@ -641,6 +641,11 @@ def run_drive(args):
     prob.set_precision(args.drive_precision)
     for _ in range(args.drive_evals):
         prob.loss_grad(*x)
+    if args.drive_projector:
+        mask = torch.from_numpy(synth.support_mask(spec)).cuda()
+        ud = x[1] + torch.from_numpy(synth.truth(spec)[1].astype(np.float32)).cuda() * 3.0
+        for _ in range(args.drive_projector):
+            prob.project_displacement(ud, mask)
     if args.drive_steps:
         overlap = (spec.m / spec.step) ** 2 * spec.npeaks
         t0 = 1.0 / (float(np.abs(probe).max() ** 2) * overlap)
@@ -649,7 +654,8 @@ def run_drive(args):
             prob.step(*x, state)
     torch.cuda.synchronize()
     prob.sync_status()
-    print("drove %s: %d evaluations, %d steps" % (spec.name, args.drive_evals, args.drive_steps))
+    print("drove %s: %d evaluations, %d steps, %d projector calls" % (spec.name, args.drive_evals,
+                                                                       args.drive_steps, args.drive_projector))
 
 
 def main():
@@ -665,6 +671,8 @@ def main():
                     help="profiling driver: run workload 1, 2, 3 or 5 untimed")
     ap.add_argument("--drive-evals", type=int, default=4)
     ap.add_argument("--drive-steps", type=int, default=0)
+    ap.add_argument("--drive-projector", type=int, default=0,
+                    help="profiling driver: projector calls (Pi_U on the displacement)")
     ap.add_argument("--drive-precision", type=int, default=0,
                     help="profiling driver: 0 = FP32 FFT kernels, 1 = tensor-core DFTs (M = 64)")
     args = ap.parse_args()
