@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(kUnwrapThreads) unwrap_kernel(UnwrapArgs a) {
     // (the depth shrinks fourfold per pass; an acyclic forest of n nodes
     // needs at most log4(n) + 1 passes, the cap only guards against a forest
     // that is not), stopping after the pass that leaves every node under a
-    // root.  The first pass reads the forest with this round's hooks
+    // root.  The first pass reads the forest with the Boruvka round's hooks
     // applied (a hooked root's parent and offset from hook_parent/hook_off)
     // and clears best[]: every decision that read it is behind the barrier.
     for (int jump = 0;; ++jump) {

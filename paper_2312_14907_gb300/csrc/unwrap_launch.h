@@ -14,7 +14,7 @@ struct UnwrapArgs {
   int* off;               //   multiple of 2 pi relative to the parent
   int* parent2;
   int* off2;
-  int* hook_parent;       // [nodes] this round's hooks of the roots
+  int* hook_parent;       // [nodes] the current Boruvka round's hooks of the roots
   int* hook_off;
   int* minnode;           // [nodes] lowest node of each group (at its root)
   unsigned long long* best;   // [nodes] heaviest incident edge of each root
