@@ -212,7 +212,7 @@ using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t
                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// the driver's tensor-map encoder, looked up once through the runtime
+// the CUDA driver API's tensor-map encoder, looked up once through the runtime
 EncodeTiledFn encode_tiled_fn() {
   static const EncodeTiledFn fn = [] {
     void* f = nullptr;
