@@ -160,3 +160,26 @@ def test_half_pixel_scan_of_a_flat_object(oracle_mod):
     ref = np.abs(np.fft.fft2(P)) ** 2
     for j in range(2):
         np.testing.assert_allclose(I[0, j], ref, rtol=1e-10, atol=1e-10 * ref.max())
+
+
+def test_per_peak_probes_are_shifted_per_frame(oracle_mod):
+    """With one probe per peak, frame f = m J + j takes P_m shifted by d_j."""
+    scan, G, P, offs, rho, u, alpha, y = _subpixel_problem(oracle_mod)
+    D, m, n, J = G.shape[0], P.shape[0], rho.shape[0], scan.shape[0]
+    rng = np.random.default_rng(9)
+    Pp = _rand_c(rng, (D, m, m))
+    p2 = oracle_mod.OracleProblem(n, n, 3, D, m, scan, G, probe_per_peak=2)
+    Pf = oracle_mod.frame_probes(p2, Pp, offs)
+    assert Pf.shape == (D * J, m, m)
+    for mpk in range(D):
+        for j in (0, J - 1):
+            ref = oracle_mod.probe_shift(Pp[mpk], offs[j, 0], offs[j, 1])
+            np.testing.assert_array_equal(Pf[mpk * J + j], ref)
+    # and the loss of a per-frame problem is the sum of its frames' losses,
+    # each from the one-probe model with that frame's probe
+    f_all, *_ = p2.loss_grad(rho, u, alpha, Pf, y)
+    p1 = oracle_mod.OracleProblem(n, n, 3, D, m, scan, G)
+    tot = 0.0
+    for f in range(D * J):
+        tot += p1.loss_grad(rho, u, alpha, Pf[f], y, frames=[f])[0]
+    assert abs(tot - f_all) <= 1e-12 * f_all
