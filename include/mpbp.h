@@ -189,6 +189,17 @@ mpbp_status mpbp_loss_grad(mpbp_ctx *ctx, const float *rho, const float *u,
                            double *loss, float *g_rho, float *g_u, double *g_alpha,
                            void *stream);
 
+/* Eq. 4 alone, without its gradient, over the frames listed in `frames` (as
+ * mpbp_loss_grad; NULL = all D*J frames): loss (dev, 1 double, overwritten).
+ * The fused frame kernel stops after the amplitude residual (no adjoint
+ * transform, no scatter-add); the per-frame terms are mpbp_loss_grad's (FFT
+ * kernels), summed in FP64 in another fixed order.  Always uses the FP32 FFTs, whatever
+ * mpbp_set_precision selected.  Needs probe and data.  For callers that need
+ * the loss without the gradient (a line search, or an autograd function that
+ * recomputes the gradient in its backward pass). */
+mpbp_status mpbp_loss(mpbp_ctx *ctx, const float *rho, const float *u, const float *alpha,
+                      const int32_t *frames, int32_t nframes, double *loss, void *stream);
+
 /* End-to-end variant of mpbp_loss_grad on HOST buffers: copies y (host
  * [D][J][M][M], or NULL to keep the data already set; when given it also
  * becomes the context's data for later calls), rho, u, alpha to the device,
@@ -360,19 +371,34 @@ mpbp_status mpbp_loss_grad_batched(int32_t n, mpbp_ctx *const *ctxs,
  * [Dp][M][M] complex, measured intensities y [D][J][M][M] (no background),
  * rho, u, alpha, and the outputs loss (1 double), g_rho, g_u, g_alpha [D]
  * doubles (g_alpha may be NULL).  G and the scan table stay on the host in
- * *problem.  The workspace lives in one fixed 16 MiB array inside the
- * library's device image, present on every GPU that loads the library until
- * the process exits; a problem needs about 8*(2*D*n1*n2 + nscan) +
- * 4*D*nscan*M*M bytes of it plus a few KiB, and a larger one returns
+ * *problem; the scan table is copied to the device on `stream` by
+ * cudaMemcpyAsync, so a page-locked scan array must stay valid until the
+ * stream has passed the call (a pageable one is read before the call
+ * returns).  dev_err (dev, one int32, or NULL) receives this call's device
+ * error bits, cleared first: MPBP_DEVERR_NONFINITE when the loss came out NaN
+ * or infinite, MPBP_DEVERR_TIMEOUT when a bounded wait of a kernel ran out,
+ * MPBP_DEVERR_BOUNDS for a frame index out of range (cannot happen here:
+ * every frame is evaluated); with NULL these bits are not reported.  The
+ * problem is checked as mpbp_create checks it (MPBP_ERR_INVALID_ARG,
+ * MPBP_ERR_UNSUPPORTED).  The workspace lives in one fixed 16 MiB array
+ * inside the library's device image, present on every GPU that loads the
+ * library until the process exits; a problem needs about 8*(2*D*n1*n2 +
+ * nscan) + 4*D*nscan*M*M bytes of it plus a few KiB, and a larger one returns
  * MPBP_ERR_UNSUPPORTED before anything is enqueued.  The first call on a
  * device looks up the array's device address (once per device), so make that
  * first call before capturing the stream into a graph.  All calls share the
  * array: each call clears what must start at zero, and calls whose GPU work
  * overlaps (other streams, other threads) race on it. */
+enum {
+  MPBP_DEVERR_BOUNDS = 1,     /* a frame index outside [0, npeaks*nscan)      */
+  MPBP_DEVERR_NONFINITE = 2,  /* the loss came out NaN or infinite            */
+  MPBP_DEVERR_TIMEOUT = 4     /* a bounded wait on the GPU ran out            */
+};
 mpbp_status mpbp_loss_grad_noalloc(const mpbp_problem *problem, const float *probe,
                                    const float *y, const float *rho, const float *u,
                                    const float *alpha, double *loss, float *g_rho,
-                                   float *g_u, double *g_alpha, void *stream);
+                                   float *g_u, double *g_alpha, int32_t *dev_err,
+                                   void *stream);
 
 /* Overrides the fused frame kernel's schedule: resident blocks per SM used to
  * size its persistent grid (0 = occupancy maximum).  Host-side only. */

@@ -62,5 +62,8 @@ int finish_grid(long long npix, int num_sms);
 // gradient assembly, then (last block to finish) the reductions and decision;
 // with r.step set (and r.st), also the optimizer update of mpbp_step
 cudaError_t launch_finish(const FinishArgs& a, const ReduceArgs& r, int grid, cudaStream_t s);
+// loss = fixed-order sum of n per-block loss partials (one warp); err gets
+// the non-finite bit
+cudaError_t launch_loss_reduce(const double* part, long long n, double* loss, int* err, cudaStream_t s);
 
 }  // namespace mpbp

@@ -13,6 +13,11 @@ cudaError_t frames_launch_m16(const FrameArgs&, int, bool, cudaStream_t, const T
 cudaError_t frames_launch_m32(const FrameArgs&, int, bool, cudaStream_t, const TmaMap*);
 cudaError_t frames_launch_m64(const FrameArgs&, int, bool, cudaStream_t, const TmaMap*);
 cudaError_t frames_launch_m128(const FrameArgs&, int, bool, cudaStream_t, const TmaMap*);
+cudaError_t frames_launch_loss_m8(const FrameArgs&, int, cudaStream_t, const TmaMap*);
+cudaError_t frames_launch_loss_m16(const FrameArgs&, int, cudaStream_t, const TmaMap*);
+cudaError_t frames_launch_loss_m32(const FrameArgs&, int, cudaStream_t, const TmaMap*);
+cudaError_t frames_launch_loss_m64(const FrameArgs&, int, cudaStream_t, const TmaMap*);
+cudaError_t frames_launch_loss_m128(const FrameArgs&, int, cudaStream_t, const TmaMap*);
 cudaError_t frames_launch_raw_m32(const FrameArgs&, int, cudaStream_t, const TmaMap*, bool);
 cudaError_t frames_launch_raw_m64(const FrameArgs&, int, cudaStream_t, const TmaMap*, bool);
 cudaError_t frames_launch_raw_m128(const FrameArgs&, int, cudaStream_t, const TmaMap*, bool);
@@ -35,6 +40,17 @@ cudaError_t frames_launch(int m, const FrameArgs& a, int grid, bool forward, cud
     case 32: return frames_launch_m32(a, grid, forward, s, tm);
     case 64: return frames_launch_m64(a, grid, forward, s, tm);
     case 128: return frames_launch_m128(a, grid, forward, s, tm);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t frames_launch_loss(int m, const FrameArgs& a, int grid, cudaStream_t s, const TmaMap* tm) {
+  switch (m) {
+    case 8: return frames_launch_loss_m8(a, grid, s, tm);
+    case 16: return frames_launch_loss_m16(a, grid, s, tm);
+    case 32: return frames_launch_loss_m32(a, grid, s, tm);
+    case 64: return frames_launch_loss_m64(a, grid, s, tm);
+    case 128: return frames_launch_loss_m128(a, grid, s, tm);
     default: return cudaErrorInvalidValue;
   }
 }

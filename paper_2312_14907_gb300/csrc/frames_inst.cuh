@@ -45,6 +45,7 @@ struct FramesKernel<M, false> {
   static constexpr int kTileGrad = 0, kTileFwd = 0;
   static KernelShape grad(bool) { return {frames_t1<M, false>, C::T, C::SMEM}; }
   static KernelShape fwd(bool) { return {frames_t1<M, true>, C::T, C::SMEM}; }
+  static KernelShape loss(bool) { return {frames_t1<M, false, true>, C::T, C::SMEM}; }
   static constexpr bool kRaw = false;
   static constexpr bool kRaw16 = false;
   static KernelShape raw(bool, bool = false) { return grad(false); }
@@ -71,6 +72,17 @@ struct FramesKernel<M, true> {
     return tma ? KernelShape{frames_t2<M, true, false, true>, C::T, C::SMEM_TMA}
                : KernelShape{frames_t2<M, true>, C::T, C::SMEM};
   }
+  // the loss alone, in the gradient kernel's layout (same tile width)
+  static KernelShape loss(bool tma) {
+    if constexpr (kQuads) {
+      return {tma ? frames_t4<M, true, true> : frames_t4<M, false, true>, T4Cfg<M>::T, T4Cfg<M>::SMEM};
+    } else if constexpr (C::SWZ) {
+      return {frames_t2<M, false, false, false, false, true>, C::T, C::SMEM};
+    } else {
+      return tma ? KernelShape{frames_t2<M, false, false, true, false, true>, C::T, C::SMEM_TMA}
+                 : KernelShape{frames_t2<M, false, false, false, false, true>, C::T, C::SMEM};
+    }
+  }
   static constexpr bool kRaw = true;
   static constexpr bool kRaw16 = M >= 64;   // 16-bit counts by tile copies
   static KernelShape raw(bool tma, bool y16 = false) {
@@ -90,7 +102,8 @@ template <int M>
 bool frames_prepare_impl(FrameKernelInfo* info) {
   using K = FramesKernel<M>;
   bool ok = true;
-  for (int t = 0; t < 2; ++t) ok = set_smem(K::grad(t != 0)) && set_smem(K::fwd(t != 0)) && ok;
+  for (int t = 0; t < 2; ++t)
+    ok = set_smem(K::grad(t != 0)) && set_smem(K::fwd(t != 0)) && set_smem(K::loss(t != 0)) && ok;
   if (K::kRaw) ok = set_smem(K::raw(false)) && set_smem(K::raw(true)) && ok;
   if (K::kRaw16) ok = set_smem(K::raw(true, true)) && ok;
   if (!ok) return false;
@@ -121,6 +134,17 @@ cudaError_t frames_launch_impl(const FrameArgs& a, int grid, bool forward, cudaS
   return cudaGetLastError();
 }
 
+// the loss alone (no adjoint, no scatter-add)
+template <int M>
+cudaError_t frames_launch_loss_impl(const FrameArgs& a, int grid, cudaStream_t s, const TmaMap* tm) {
+  using K = FramesKernel<M>;
+  static const TmaMap kNone{};
+  const bool tile = tm != nullptr && K::kTileGrad > 0;
+  const KernelShape k = K::loss(tile);
+  k.fn<<<grid, k.threads, k.smem, s>>>(a, tile ? *tm : kNone);
+  return cudaGetLastError();
+}
+
 // the raw-data gradient kernel (FrameArgs::yraw); thread-pair sides only
 template <int M>
 cudaError_t frames_launch_raw_impl(const FrameArgs& a, int grid, cudaStream_t s, const TmaMap* tm, bool y16) {
@@ -144,5 +168,9 @@ cudaError_t frames_launch_raw_impl(const FrameArgs& a, int grid, cudaStream_t s,
   cudaError_t frames_launch_raw_m##M(const FrameArgs& a, int grid, cudaStream_t s,        \
                                      const TmaMap* tm, bool y16) {                         \
     return frames_launch_raw_impl<M>(a, grid, s, tm, y16);                                 \
+  }                                                                                        \
+  cudaError_t frames_launch_loss_m##M(const FrameArgs& a, int grid, cudaStream_t s,       \
+                                      const TmaMap* tm) {                                  \
+    return frames_launch_loss_impl<M>(a, grid, s, tm);                                     \
   }                                                                                        \
   }

@@ -62,6 +62,10 @@ bool frames_prepare(int m, FrameKernelInfo* info);
 cudaError_t frames_launch(int m, const FrameArgs& a, int grid, bool forward, cudaStream_t s,
                           const TmaMap* tm = nullptr);
 
+// The loss alone (Eq. 4 over the frames of a, no adjoint and no scatter-add):
+// per-block partials in a.loss_part.  tm as for the gradient kernel.
+cudaError_t frames_launch_loss(int m, const FrameArgs& a, int grid, cudaStream_t s, const TmaMap* tm = nullptr);
+
 // Raw-data gradient kernel (a.yraw: counts in their natural layout, device
 // memory; sqrt(y) written to a.aT_w).  Frame sides 32, 64, 128.
 bool frames_raw_supported(int m);

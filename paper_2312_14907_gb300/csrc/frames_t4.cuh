@@ -138,7 +138,7 @@ MPBP_DI void t4_fetch(const FrameArgs& p, const T4Group<M>& g, const FrameRef& r
 // One frame's loss and gradient (inputs in flight); fetches the next frame's
 // inputs as soon as their buffers are free.  TMA: a wait that runs out clears
 // bs.ok and returns at once.
-template <int M, bool TMA, typename AddLoss>
+template <int M, bool TMA, bool LOSS, typename AddLoss>
 MPBP_DI void t4_frame(const FrameArgs& p, const T4Group<M>& g, const FrameRef& cur, const FrameRef& nxt,
                       AddLoss&& add_loss, BulkState& bs, const TmaMap* tm) {
   using C = T4Cfg<M>;
@@ -194,6 +194,13 @@ MPBP_DI void t4_frame(const FrameArgs& p, const T4Group<M>& g, const FrameRef& c
     v[i] = residual(v[i], g.abuf[t4_amp<M>(q1, ln)], bv, fl);
   });
   add_loss(cur.valid ? 0.5f * fl : 0.0f);
+  if constexpr (LOSS) {
+    // loss only: the buffers are free once every thread is past its residual
+    __syncthreads();
+    t4_fetch<M, TMA>(p, g, nxt, bs, tm);
+    if constexpr (!TMA) cp_async_commit();
+    return;
+  }
 
   // A5: rows (blk4 -> dec4), transpose, columns; the exchange buffer's last
   // reads (the transposed row input above) are behind this barrier
@@ -238,10 +245,10 @@ MPBP_DI void t4_frame(const FrameArgs& p, const T4Group<M>& g, const FrameRef& c
   });
 }
 
-// loss and gradient: one frame per block, frames round-robin over a
-// persistent grid; TMA: inputs by tile and bulk copies (tm: the objects'
-// tensor map), else by cp.async
-template <int M, bool TMA>
+// loss and gradient (LOSS: loss only): one frame per block, frames
+// round-robin over a persistent grid; TMA: inputs by tile and bulk copies
+// (tm: the objects' tensor map), else by cp.async
+template <int M, bool TMA, bool LOSS = false>
 __global__ void __launch_bounds__(T4Cfg<M>::T, T4Cfg<M>::MINB)
     frames_t4(const FrameArgs p, const __grid_constant__ TmaMap tm) {
   using C = T4Cfg<M>;
@@ -263,7 +270,7 @@ __global__ void __launch_bounds__(T4Cfg<M>::T, T4Cfg<M>::MINB)
   if constexpr (!TMA) cp_async_commit();
   for (; it < p.nframes; it += gridDim.x) {
     const FrameRef nxt = frame_ref(p, it + gridDim.x);
-    t4_frame<M, TMA>(p, g, cur, nxt, [&](float fl) { lsum += (double)fl; }, bs, &tm);
+    t4_frame<M, TMA, LOSS>(p, g, cur, nxt, [&](float fl) { lsum += (double)fl; }, bs, &tm);
     if (TMA && !bs.ok) {
       if (threadIdx.x == 0) atomicOr(p.err, kErrTimeout);
       break;

@@ -427,16 +427,8 @@ const char* mpbp_last_error(const mpbp_ctx* ctx) { return ctx ? ctx->last_error.
 mpbp_status mpbp_create(const mpbp_problem* pr, mpbp_ctx** out) {
   if (!out) return MPBP_ERR_INVALID_ARG;
   *out = nullptr;
-  if (!pr || !pr->G || !pr->scan) return MPBP_ERR_INVALID_ARG;
-  if (pr->n1 < 1 || pr->n2 < 1 || pr->ncomp < 1 || pr->ncomp > kMaxComp || pr->npeaks < 1 ||
-      pr->npeaks > kMaxPeaks || pr->nscan < 1 || !std::isfinite(pr->phase_scale))
-    return MPBP_ERR_INVALID_ARG;
-  if ((long long)pr->n1 * pr->n2 > (1LL << 31) / 16) return MPBP_ERR_INVALID_ARG;
-  if ((long long)pr->npeaks * pr->nscan > (1LL << 31) - 1) return MPBP_ERR_INVALID_ARG;
-  if (pr->m != 8 && pr->m != 16 && pr->m != 32 && pr->m != 64 && pr->m != 128)
-    return MPBP_ERR_UNSUPPORTED;
-  for (int i = 0; i < pr->npeaks * pr->ncomp; ++i)
-    if (!std::isfinite(pr->G[i])) return MPBP_ERR_INVALID_ARG;
+  const mpbp_status vs = validate_problem(pr);
+  if (vs != MPBP_OK) return vs;
 
   mpbp_ctx* c = new (std::nothrow) mpbp_ctx();
   if (!c) return MPBP_ERR_OOM;
@@ -747,6 +739,29 @@ mpbp_status mpbp_loss_grad(mpbp_ctx* c, const float* rho, const float* u, const 
   if (!c->has_probe || !c->has_data) return fail(c, MPBP_ERR_NO_DATA, "probe or data not set");
   return enqueue_loss_grad(c, rho, u, alpha, frames, nframes, loss, g_rho ? g_rho : c->g_rho_ws,
                            g_u ? g_u : c->g_u_ws, g_alpha, nullptr, S(stream));
+}
+
+mpbp_status mpbp_loss(mpbp_ctx* c, const float* rho, const float* u, const float* alpha,
+                      const int32_t* frames, int32_t nframes, double* loss, void* stream) {
+  if (!c || !rho || !u || !alpha || !loss) return fail(c, MPBP_ERR_INVALID_ARG, "null argument");
+  if (frames && nframes < 0) return fail(c, MPBP_ERR_INVALID_ARG, "nframes < 0");
+  if (!c->has_probe || !c->has_data) return fail(c, MPBP_ERR_NO_DATA, "probe or data not set");
+  cudaStream_t s = S(stream);
+  mpbp_status r = enqueue_object_build(c, rho, u, alpha, c->O, s);
+  if (r != MPBP_OK) return r;
+  const int nf = frames ? nframes : (int)c->nframes;
+  FrameArgs fa = frame_args(c, frames, nf);
+  fa.arrivals = nullptr;   // no gradient assembly follows
+  const int grid = frames_grid_fft(c, nf);
+  if (c->tile_grad) {
+    TmaMap tm = c->tm_grad;
+    tm.tx_extra = c->test_tx_extra;
+    MPBP_CUDA(c, frames_launch_loss(c->M, fa, grid, s, &tm));
+  } else {
+    MPBP_CUDA(c, frames_launch_loss(c->M, fa, grid, s, nullptr));
+  }
+  MPBP_CUDA(c, launch_loss_reduce(c->loss_part, grid, loss, c->err, s));
+  return MPBP_OK;
 }
 
 }  // extern "C"

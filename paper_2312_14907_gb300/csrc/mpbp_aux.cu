@@ -419,6 +419,20 @@ __global__ void __launch_bounds__(kFinishThreads) finish_kernel(FinishArgs a, Re
   final_reduce<kFinishThreads, STEP>(ra, STEP ? s_loss : 0.0);
 }
 
+// The loss alone (mpbp_loss): one warp sums the frame kernel's per-block
+// partials in a fixed order (the same bits as the gradient assembly's
+// sum of them) and flags a non-finite result.
+__global__ void loss_reduce_kernel(const double* __restrict__ part, long long n, double* loss, int* err) {
+  const int lane = threadIdx.x & 31;
+  double v = warp_slice_sum(part, n, 1, lane);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) {
+    *loss = v;
+    if (!isfinite(v)) atomicOr(err, kErrNonfinite);
+  }
+}
+
 // ----------------------------------------------------------------------------
 // Probes for scan positions off the pixel grid (Eq. 2's shift S_j at a real
 // position s_j = n_j + d_j): frame j keeps the integer window n_j and takes
@@ -557,6 +571,11 @@ cudaError_t launch_frame_transpose(const float* in, float* out, long long nframe
 int finish_grid(long long npix, int num_sms) {
   return grid_for((npix + kFinishPixelsPerThread - 1) / kFinishPixelsPerThread, kFinishThreads,
                   num_sms * 4);
+}
+
+cudaError_t launch_loss_reduce(const double* part, long long n, double* loss, int* err, cudaStream_t s) {
+  loss_reduce_kernel<<<1, 32, 0, s>>>(part, n, loss, err);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_finish(const FinishArgs& a, const ReduceArgs& r, int grid, cudaStream_t s) {

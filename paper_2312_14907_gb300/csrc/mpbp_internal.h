@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include "fft_reg.cuh"
 #include "mpbp.h"
 
@@ -11,14 +13,31 @@ namespace mpbp {
 constexpr int kMaxPeaks = 16;
 constexpr int kMaxComp = 3;
 
-// device error word bits
-constexpr int kErrBounds = 1;
-constexpr int kErrNonfinite = 2;
-constexpr int kErrTimeout = 4;     // a bounded wait on the GPU ran out
+// device error word bits (the same values as the MPBP_DEVERR_* of mpbp.h)
+constexpr int kErrBounds = MPBP_DEVERR_BOUNDS;
+constexpr int kErrNonfinite = MPBP_DEVERR_NONFINITE;
+constexpr int kErrTimeout = MPBP_DEVERR_TIMEOUT;   // a bounded wait on the GPU ran out
 
 // FrameArgs::probe_stride codes for probes that vary with the scan position
 constexpr int kProbePerScan = -1;
 constexpr int kProbePerFrame = -2;
+
+// Checks of a problem's geometry, shared by every entry point that takes an
+// mpbp_problem: sizes in range, G and phase_scale finite, the pixel and frame
+// counts within the kernels' 32-bit indexing.  MPBP_ERR_UNSUPPORTED for a
+// frame side the kernels do not cover.
+inline mpbp_status validate_problem(const mpbp_problem* pr) {
+  if (!pr || !pr->G || !pr->scan) return MPBP_ERR_INVALID_ARG;
+  if (pr->n1 < 1 || pr->n2 < 1 || pr->ncomp < 1 || pr->ncomp > kMaxComp || pr->npeaks < 1 ||
+      pr->npeaks > kMaxPeaks || pr->nscan < 1 || !std::isfinite(pr->phase_scale))
+    return MPBP_ERR_INVALID_ARG;
+  if ((long long)pr->n1 * pr->n2 > (1LL << 31) / 16) return MPBP_ERR_INVALID_ARG;
+  if ((long long)pr->npeaks * pr->nscan > (1LL << 31) - 1) return MPBP_ERR_INVALID_ARG;
+  for (int i = 0; i < pr->npeaks * pr->ncomp; ++i)
+    if (!std::isfinite(pr->G[i])) return MPBP_ERR_INVALID_ARG;
+  if (pr->m != 8 && pr->m != 16 && pr->m != 32 && pr->m != 64 && pr->m != 128) return MPBP_ERR_UNSUPPORTED;
+  return MPBP_OK;
+}
 
 // Arguments of the fused per-frame kernel (A2..A7 of the hot path).
 struct FrameArgs {

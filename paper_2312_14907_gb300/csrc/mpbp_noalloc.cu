@@ -57,14 +57,11 @@ mpbp_status device_setup(int dev, DeviceSetup** out) {
 extern "C" mpbp_status mpbp_loss_grad_noalloc(const mpbp_problem* pr, const float* probe,
                                               const float* y, const float* rho, const float* u,
                                               const float* alpha, double* loss, float* g_rho,
-                                              float* g_u, double* g_alpha, void* stream) {
-  if (!pr || !pr->G || !pr->scan || !probe || !y || !rho || !u || !alpha || !loss || !g_rho || !g_u)
-    return MPBP_ERR_INVALID_ARG;
-  if (pr->n1 < 1 || pr->n2 < 1 || pr->ncomp < 1 || pr->ncomp > kMaxComp || pr->npeaks < 1 ||
-      pr->npeaks > kMaxPeaks || pr->nscan < 1)
-    return MPBP_ERR_INVALID_ARG;
-  if (pr->m != 8 && pr->m != 16 && pr->m != 32 && pr->m != 64 && pr->m != 128)
-    return MPBP_ERR_UNSUPPORTED;
+                                              float* g_u, double* g_alpha, int32_t* dev_err,
+                                              void* stream) {
+  if (!probe || !y || !rho || !u || !alpha || !loss || !g_rho || !g_u) return MPBP_ERR_INVALID_ARG;
+  const mpbp_status vs = validate_problem(pr);
+  if (vs != MPBP_OK) return vs;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return MPBP_ERR_CUDA;
   DeviceSetup* ds = nullptr;
@@ -95,7 +92,7 @@ extern "C" mpbp_status mpbp_loss_grad_noalloc(const mpbp_problem* pr, const floa
   const size_t oA = take(sizeof(float) * nframes * mm);
   const size_t oLP = take(sizeof(double) * (fgrid > 0 ? fgrid : 1));
   const size_t oPart = take(sizeof(double) * pgrid * (pr->npeaks + 3));
-  const size_t oErr = take(sizeof(int));
+  const size_t oErr = take(sizeof(int));   // used when the caller passes no error word
   const size_t oArr = take(sizeof(unsigned));
   if (off > kScratchBytes) return MPBP_ERR_UNSUPPORTED;
   char* b = static_cast<char*>(ds->scratch);
@@ -105,7 +102,8 @@ extern "C" mpbp_status mpbp_loss_grad_noalloc(const mpbp_problem* pr, const floa
   float* aT = reinterpret_cast<float*>(b + oA);
   double* loss_part = reinterpret_cast<double*>(b + oLP);
   double* part = reinterpret_cast<double*>(b + oPart);
-  int* err = reinterpret_cast<int*>(b + oErr);
+  // the device error bits of this call go to the caller's word when given
+  int* err = dev_err ? reinterpret_cast<int*>(dev_err) : reinterpret_cast<int*>(b + oErr);
   unsigned* arrivals = reinterpret_cast<unsigned*>(b + oArr);
 
   PhaseCoef pc{};
@@ -117,7 +115,9 @@ extern "C" mpbp_status mpbp_loss_grad_noalloc(const mpbp_problem* pr, const floa
     }
 
   // the array keeps the previous call's contents: clear what must start at 0
-  // and load this call's scan table
+  // (the accumulator, the error word; the arrival counter is cleared by the
+  // frame kernel) and load this call's scan table, copied from the caller's
+  // host array on the stream
   if (cudaMemcpyAsync(scan, pr->scan, sizeof(int2) * pr->nscan, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemsetAsync(acc, 0, sizeof(cf) * npix * pr->npeaks, s) != cudaSuccess ||
       cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess)

@@ -81,7 +81,7 @@ EXPORTS = ["mpbp_status_string", "mpbp_create", "mpbp_destroy", "mpbp_last_error
            "mpbp_adam_init", "mpbp_adam_step", "mpbp_adam_get_state", "mpbp_adam_set_state",
            "mpbp_loss_grad_phases", "mpbp_unwrap_phases", "mpbp_project_displacement",
            "mpbp_illumination", "mpbp_set_test_stall", "mpbp_loss_grad_host_counts16",
-           "mpbp_set_scan_offsets", "mpbp_shift_probe"]
+           "mpbp_set_scan_offsets", "mpbp_shift_probe", "mpbp_loss"]
 
 PRECISION_FP32 = 0        # FFTs on the CUDA cores
 PRECISION_TC_SPLIT16 = 1  # dense DFT matrices on the tensor cores, split FP16
@@ -124,6 +124,8 @@ def load(build_if_missing=True):
     lib.mpbp_forward.restype = st
     lib.mpbp_loss_grad.argtypes = [V, V, V, V, V, I32, V, V, V, V, V]
     lib.mpbp_loss_grad.restype = st
+    lib.mpbp_loss.argtypes = [V, V, V, V, V, I32, V, V]
+    lib.mpbp_loss.restype = st
     lib.mpbp_loss_grad_host.argtypes = [V, V, V, V, V, V, V, V, V, V]
     lib.mpbp_loss_grad_host.restype = st
     lib.mpbp_loss_grad_host_counts16.argtypes = [V, V, V, V, V, V, V, V, V, V]
@@ -172,7 +174,7 @@ def load(build_if_missing=True):
     lib.mpbp_set_test_stall.restype = st
     lib.mpbp_frames_timing_read.argtypes = [V, P(D), P(I32)]
     lib.mpbp_frames_timing_read.restype = st
-    lib.mpbp_loss_grad_noalloc.argtypes = [P(_Problem), V, V, V, V, V, V, V, V, V, V]
+    lib.mpbp_loss_grad_noalloc.argtypes = [P(_Problem), V, V, V, V, V, V, V, V, V, V, V]
     lib.mpbp_loss_grad_noalloc.restype = st
     lib.mpbp_set_scan_offsets.argtypes = [V, V, V]
     lib.mpbp_set_scan_offsets.restype = st
@@ -362,6 +364,16 @@ class Problem:
                                              _p(loss), _p(g_rho), _p(g_u), _p(g_alpha), _stream()),
                     "mpbp_loss_grad")
         return loss, g_rho, g_u, g_alpha
+
+    def loss(self, rho, u, alpha, frames=None, out=None):
+        """Eq. 4 alone (mpbp_loss): returns loss [1] float64 on the device."""
+        self._state(rho, u, alpha)
+        if out is None:
+            out = torch.empty(1, dtype=torch.float64, device=rho.device)
+        frames, nfr = self._frames_arg(frames, rho.device)
+        self._check(self._lib.mpbp_loss(self._h, _p(rho), _p(u), _p(alpha), _p(frames), nfr, _p(out),
+                                        _stream()), "mpbp_loss")
+        return out
 
     def _frames_arg(self, frames, dev):
         nfr = 0
@@ -571,24 +583,58 @@ def loss_grad_batched(problems, states, outs=None):
     return outs
 
 
-def loss_grad_noalloc(spec_problem, probe, y, rho, u, alpha, out):
+DEVERR_BOUNDS, DEVERR_NONFINITE, DEVERR_TIMEOUT = 1, 2, 4   # device error bits (MPBP_DEVERR_*)
+
+
+def loss_grad_noalloc(spec_problem, probe, y, rho, u, alpha, out, dev_err=None):
     """mpbp_loss_grad_noalloc: the loss and gradient computed in the library's
     fixed device scratch array, for callers that cannot allocate device
     memory.  `spec_problem` is a Problem (only its geometry is used); every
     tensor, including the outputs in `out` = (loss [1] float64, g_rho, g_u,
-    g_alpha [D] float64), must already be on the device."""
+    g_alpha [D] float64) and the optional error word `dev_err` ([1] int32,
+    read it with noalloc_check), must already be on the current device.
+    Shapes, dtypes, contiguity and the device are checked here, so that no
+    wrong pointer reaches the kernels."""
     lib = load()
     p = spec_problem
+    sh = p.shapes
+    dev = torch.cuda.current_device()
+    probe_shape = (p.npeaks, p.m, p.m) if p.probe_per_peak else (p.m, p.m)
+    loss, g_rho, g_u, g_alpha = out
+    checks = [(probe, torch.complex64, probe_shape, "probe"), (y, torch.float32, sh["frames"], "y"),
+              (rho, torch.float32, sh["rho"], "rho"), (u, torch.float32, sh["u"], "u"),
+              (alpha, torch.float32, sh["alpha"], "alpha"), (loss, torch.float64, (1,), "loss"),
+              (g_rho, torch.float32, sh["rho"], "g_rho"), (g_u, torch.float32, sh["u"], "g_u")]
+    if g_alpha is not None:
+        checks.append((g_alpha, torch.float64, (p.npeaks,), "g_alpha"))
+    if dev_err is not None:
+        checks.append((dev_err, torch.int32, (1,), "dev_err"))
+    for t, dtype, shape, name in checks:
+        _dev(t, dtype, shape, name)
+        if t.device.index != dev:
+            raise ValueError("%s is on cuda:%d, the current device is cuda:%d" % (name, t.device.index, dev))
     pr = _Problem(p.n1, p.n2, p.ncomp, p.npeaks, p.m, p.nscan,
                   p._G.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                   p._scan.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                   int(p.probe_per_peak), p.phase_scale)
-    loss, g_rho, g_u, g_alpha = out
     s = lib.mpbp_loss_grad_noalloc(ctypes.byref(pr), _p(probe), _p(y), _p(rho), _p(u), _p(alpha),
-                                   _p(loss), _p(g_rho), _p(g_u), _p(g_alpha), _stream())
+                                   _p(loss), _p(g_rho), _p(g_u), _p(g_alpha), _p(dev_err), _stream())
     if s != 0:
         raise MPBPError(s, "mpbp_loss_grad_noalloc")
     return out
+
+
+def noalloc_check(dev_err):
+    """Waits for the current stream, then raises MPBPError for the device
+    error bits a loss_grad_noalloc call left in `dev_err` (no-op if 0)."""
+    torch.cuda.current_stream().synchronize()
+    bits = int(dev_err.item())
+    if bits & DEVERR_TIMEOUT:
+        raise MPBPError(5, "a bounded wait on the GPU ran out")
+    if bits & DEVERR_BOUNDS:
+        raise MPBPError(6, "a frame index out of range")
+    if bits & DEVERR_NONFINITE:
+        raise MPBPError(4, "the loss is not finite")
 
 
 def autotune_batched(problems, states, cache_path=None):
@@ -609,24 +655,35 @@ def autotune_batched(problems, states, cache_path=None):
 class MPBPLoss(torch.autograd.Function):
     """f(rho, u, alpha) of Eq. 4 with the hand-written adjoint as its backward.
 
-    forward runs the fused loss+gradient pass once and keeps only the
-    object-sized gradients; backward scales them by the incoming gradient.
-    Exit waves are never stored."""
+    Default: forward runs the fused loss+gradient pass once and keeps only
+    the object-sized gradients; backward scales them by the incoming
+    gradient.  recompute=True: forward runs the loss alone (no adjoint, no
+    scatter) and keeps only the inputs; backward reruns the fused pass, which
+    recomputes the exit waves and far fields on chip.  Exit waves are never
+    stored either way."""
 
     @staticmethod
-    def forward(ctx, rho, u, alpha, problem):
-        loss, g_rho, g_u, g_alpha = problem.loss_grad(rho.detach().contiguous(),
-                                                      u.detach().contiguous(),
-                                                      alpha.detach().contiguous())
-        ctx.save_for_backward(g_rho, g_u, g_alpha)
+    def forward(ctx, rho, u, alpha, problem, recompute=False):
+        x = (rho.detach().contiguous(), u.detach().contiguous(), alpha.detach().contiguous())
+        ctx.problem = problem
+        ctx.recompute = bool(recompute)
+        if recompute:
+            loss = problem.loss(*x)
+            ctx.save_for_backward(*x)
+        else:
+            loss, g_rho, g_u, g_alpha = problem.loss_grad(*x)
+            ctx.save_for_backward(g_rho, g_u, g_alpha)
         return loss[0]
 
     @staticmethod
     def backward(ctx, grad_out):
-        g_rho, g_u, g_alpha = ctx.saved_tensors
+        if ctx.recompute:
+            _, g_rho, g_u, g_alpha = ctx.problem.loss_grad(*ctx.saved_tensors)
+        else:
+            g_rho, g_u, g_alpha = ctx.saved_tensors
         go = grad_out.to(torch.float32)
-        return go * g_rho, go * g_u, (grad_out * g_alpha).to(torch.float32), None
+        return go * g_rho, go * g_u, (grad_out * g_alpha).to(torch.float32), None, None
 
 
-def mpbp_loss(rho, u, alpha, problem):
-    return MPBPLoss.apply(rho, u, alpha, problem)
+def mpbp_loss(rho, u, alpha, problem, recompute=False):
+    return MPBPLoss.apply(rho, u, alpha, problem, recompute)

@@ -240,12 +240,13 @@ def poisson_counts(I, seed):
     return rng.poisson(np.maximum(I, 0.0)).astype(np.float32)
 
 
-def template_counts(spec, seed):
+def template_counts(spec, seed, scan_index=None):
     """Count-like data [D][J][M][M] without any forward model: per peak a fixed
     speckle template (a few Gaussian spots on a weak floor, DC at [0][0]) times
     a seeded per-frame level, rounded.  For tests that only need some data of
     the right shape and range (the loss and gradient are compared for the same
-    y on both sides)."""
+    y on both sides).  scan_index: only those scan positions ([D][len][M][M],
+    the same values as the full array's)."""
     rng = np.random.default_rng(seed)
     m = spec.m
     q = np.fft.fftfreq(m) * m
@@ -259,6 +260,8 @@ def template_counts(spec, seed):
             t += rng.uniform(5, 60) * np.exp(-((q0 - c0) ** 2 + (q1 - c1) ** 2) / (2 * w * w))
         tmpl[d] = t
     level = rng.uniform(0.2, 1.5, (spec.npeaks, spec.nscan)).astype(np.float32)
+    if scan_index is not None:
+        level = level[:, np.asarray(scan_index)]
     return np.rint(level[:, :, None, None] * tmpl[:, None, :, :]).astype(np.float32)
 
 

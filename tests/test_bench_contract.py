@@ -10,7 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_reference_arm_prints_one_json_line():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                          "--steps", "1", "--warmup", "3", "--ref-frames", "24"],
+                          "--steps", "1", "--warmup", "3", "--ref-frames", "12"],
                          cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.strip().startswith("{")]
@@ -21,7 +21,7 @@ def test_reference_arm_prints_one_json_line():
               "higher_is_better", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert k in d, k
     assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1
-    assert d["config"]["workload"] == "mpbp-256-m64-d3"
+    assert d["config"]["workload"] == "mpbp-1024-m128-d6"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     e = d["e2e"]

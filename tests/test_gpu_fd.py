@@ -6,7 +6,7 @@ The loss of Eq. 4 at a perturbed state is differenced in rho at each pixel
 (the other frames do not depend on it), with the FP64 oracle, so that the
 difference quotient is limited only by its O(h^2) truncation.  Both precision
 modes of the GPU gradient (FP32 FFTs; split-FP16 tensor-core DFTs) are
-compared with it.
+compared with it at 1e-4 relative L2 over the sampled pixels.
 """
 import numpy as np
 import pytest
@@ -78,5 +78,5 @@ def test_gradient_matches_central_differences_at_64_pixels(fd_case, precision):
     for got, fd in ((got_rho, fd_rho), (got_u, fd_u)):
         assert np.abs(fd).max() > 0
         rel = np.linalg.norm(got - fd) / np.linalg.norm(fd)
-        assert rel <= 1e-3, rel
-        assert np.abs(got - fd).max() <= 1e-2 * np.abs(fd).max()
+        assert rel <= 1e-4, rel
+        assert np.abs(got - fd).max() <= 1e-3 * np.abs(fd).max()

@@ -122,6 +122,28 @@ def test_tile_and_plain_copies_match_oracle(m):
         q.sync_status()
 
 
+@pytest.mark.parametrize("n2,tiles", [(256, 3), (255, 0)])
+def test_m128_steady_state_matches_oracle(n2, tiles):
+    """The M = 128 gradient kernel runs one block per SM, so a block takes a
+    second frame only when a launch has more than one frame per SM.  338
+    frames (13 x 13 scan, 2 peaks) give every block of the 152-block grid two
+    or three frames: each prefetches the next frame's inputs while it
+    transforms the current one, reuses its buffers and flips its barrier
+    phase at least twice.  Element by element against the oracle, through
+    the tile-copy path (even n2) and the cp.async path (odd n2), with the
+    scan overhanging the grid; the same again through a frame list."""
+    spec, scan = custom_spec(256, 128, 13, 10, npeaks=2, offset=-6, n2=n2)
+    case = Case(spec, scan=scan, state="perturbed")
+    p, x = _gpu(case)
+    info = p.info()
+    assert info["tile_copies"] == tiles, info
+    assert spec.nframes > 2 * info["frames_grid"], (spec.nframes, info)
+    _check_loss_grad(case, p.loss_grad(*x))
+    frames = np.random.default_rng(128).permutation(spec.nframes)[:320].astype(np.int32)
+    _check_loss_grad(case, p.loss_grad(*x, frames=torch.from_numpy(frames).cuda()), frames=frames)
+    p.sync_status()
+
+
 def test_frame_subset_matches_oracle():
     spec, scan = custom_spec(64, 32, 6, 6, npeaks=3, offset=0)
     case = Case(spec, scan=scan, state="perturbed")

@@ -404,3 +404,61 @@ def test_step_decreases_loss_with_armijo(oracle_mod):
     assert all(b <= a for a, b in zip(accepted, accepted[1:]))
     assert accepted[-1] < accepted[0] / 10
     assert alpha[0] == 1.0
+
+
+def test_step_bookkeeping_matches_a_replay_of_the_rule(oracle_mod):
+    """The lagged-Armijo stepper against a replay of its stated rule, written
+    here with the (separately pinned) loss and gradient: on each call
+    evaluate f, g at the current point; accept on the first call, or when f
+    <= f_prev - c t gn2_prev; on acceptance the point and its gradient become
+    the base and t grows (not on the first call), on rejection t shrinks;
+    the next point is base - t w g_base with alpha_0 held.  A first step
+    length far too long forces rejections, and the rejected trials must lie
+    on the line from the base point along the base gradient, each at
+    `shrink` times the previous distance."""
+    spec = synth.tiny(npeaks=3, n=16, m=8, side=4, step=2)
+    scan = synth.scan_positions(spec)
+    p = oracle_mod.OracleProblem.from_spec(spec, scan)
+    P = synth.probe(spec)
+    rho_t, u_t = synth.truth(spec)
+    y = p.forward(rho_t, u_t, np.array([1.0, 0.8, 1.3]), P)
+    rho, u, alpha = synth.init_state(spec)
+    c, grow, shrink, t0, w = 1e-4, 1.25, 0.5, 0.2, (1.0, 0.5, 0.25)
+    st = oracle_mod.OracleStepper(p, P, y, c_armijo=c, grow=grow, shrink=shrink, t0=t0,
+                                  w_rho=w[0], w_u=w[1], w_alpha=w[2])
+    # the replay's own state
+    x = [rho.copy(), u.copy(), alpha.copy()]
+    base, gbase, f_prev, gn2_prev, t = None, None, None, None, t0
+    flags, ts = [], []
+    for k in range(16):
+        f, gr, gu, ga = p.loss_grad(x[0], x[1], x[2], P, y)
+        accept = np.isfinite(f) if k == 0 else (np.isfinite(f) and f <= f_prev - c * t * gn2_prev)
+        if accept:
+            if k > 0:
+                t *= grow
+            base = [a.copy() for a in x]
+            gbase = [gr.copy(), gu.copy(), ga.copy()]
+            f_prev = f
+            gn2_prev = w[0] * np.sum(gr * gr) + w[1] * np.sum(gu * gu) + w[2] * np.sum(ga[1:] ** 2)
+        else:
+            t *= shrink
+        prev_trial = [a.copy() for a in x]
+        x = [base[0] - t * w[0] * gbase[0], base[1] - t * w[1] * gbase[1],
+             np.concatenate([[base[2][0]], base[2][1:] - t * w[2] * gbase[2][1:]])]
+        f_lib = st.step(rho, u, alpha)
+        assert abs(f_lib - f) <= 1e-12 * abs(f), k
+        assert bool(st.state.accepted) == bool(accept), k
+        assert abs(st.state.t - t) <= 1e-15 * t, k
+        for got, want in zip((rho, u, alpha), x):
+            np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * max(1.0, np.abs(want).max()))
+        if not accept and k > 0:
+            # the rejected trial and the new one lie on one ray from the base point
+            for got, old, b in zip((rho, u, alpha), prev_trial, base):
+                np.testing.assert_allclose(got - b, shrink * (old - b), rtol=0,
+                                           atol=1e-12 * max(1.0, np.abs(old - b).max()))
+        flags.append(bool(accept))
+        ts.append(st.state.t)
+    assert flags[0] and not flags[1], flags           # t0 far too long: the first trial fails
+    assert any(flags[2:]) and sum(flags[1:]) >= 3, flags
+    assert st.state.n_accept == sum(flags) and st.state.n_reject == len(flags) - sum(flags)
+    assert alpha[0] == 1.0
