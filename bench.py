@@ -426,13 +426,13 @@ def run_gpu(args):
         "data": "synthetic (seeded truth object, Gaussian probe with quadratic phase, CUDA forward "
                 "model, Poisson counts at 1e4 photons in the brightest frame drawn on the device)",
         "config": dict(workload_config(spec), **{
-            "step": "object synthesis + fused frame kernel + gradient assembly + FP64 "
-                    "reductions + lagged-Armijo update, replayed as the context's CUDA graph "
-                    "(mpbp_step_capture / mpbp_step_replay)",
-            "eager_ms_per_step": eager_ms,
             "l2": "flushed between timed steps (256 MB write, outside the timed region); the "
                   "step's 5.76 GB of amplitudes exceed L2 as well",
             "parallelism": "replicas" if world > 1 else "single"}),
+        "step": {"what": "object synthesis + fused frame kernel + gradient assembly + FP64 "
+                         "reductions + lagged-Armijo update, replayed as the context's CUDA graph "
+                         "(mpbp_step_capture / mpbp_step_replay)",
+                 "eager_ms_per_step": eager_ms},
         "iterations_per_s": args.steps * world / (tot_ms / 1e3),
         "hbm_roofline": {"bytes_per_frame": bpf, "achieved_gbs": value * bpf / 1e9 / world,
                          "peak_gbs": pk["hbm_gbs"], "frac": value * bpf / 1e9 / world / pk["hbm_gbs"],
@@ -717,7 +717,7 @@ def run_reference(args):
         p.loss_grad(rho0, u0, a0, probe, y, frames=fr)
         t += time.perf_counter() - t1
     value = nsample * args.steps / t
-    cfg = dict(workload_config(spec), parallelism="single")
+    cfg = dict(workload_config(spec), l2="host cores: no GPU cache involved", parallelism="single")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
