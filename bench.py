@@ -498,8 +498,9 @@ def secondary_block(torch, mpbp, args, flush, stream, pk):
     the projector."""
     spec, scan, prob, probe, yd, x, t0 = setup_problem(torch, mpbp, SECONDARY)
     steps = max(5, min(args.steps, 20))
-    step_ms, eager_ms, kavg_ms, _ = time_steps(torch, prob, [t.clone() for t in x], t0, steps, args.warmup,
-                                               flush, stream)
+    # (the steps move x away from the flat start, where the gradient is ill
+    # conditioned, before the unfused comparison below)
+    step_ms, eager_ms, kavg_ms, _ = time_steps(torch, prob, x, t0, steps, args.warmup, flush, stream)
     ms = sum(step_ms) / len(step_ms)
     achieved = flops_per_frame(spec.m) * spec.nframes / (kavg_ms / 1e3) / 1e12
     rev = kernel_revision(spec.m)
@@ -742,9 +743,10 @@ def run_drive(args):
     spec = synth.config(args.drive)
     scan = synth.scan_positions(spec)
     prob = mpbp.Problem.from_spec(spec, scan)
-    probe, y = make_inputs(spec, scan, prob, torch)
+    probe, yd = make_inputs(spec, scan, prob, torch)
     prob.set_probe(torch.from_numpy(probe).cuda())
-    prob.set_data(torch.from_numpy(y).cuda())
+    prob.set_data(yd)
+    del yd
     x = [torch.from_numpy(a.astype(np.float32)).cuda() for a in synth.init_state(spec)]
     prob.set_precision(args.drive_precision)
     for _ in range(args.drive_evals):
