@@ -43,9 +43,9 @@ struct FramesKernel<M, false> {
   using C = T1Cfg<M>;
   static constexpr int NG = C::NG;
   static constexpr int kTileGrad = 0, kTileFwd = 0;
-  static KernelShape grad(bool) { return {frames_t1<M, false>, C::T, C::SMEM}; }
+  static KernelShape grad(bool, bool = false) { return {frames_t1<M, false>, C::T, C::SMEM}; }
   static KernelShape fwd(bool) { return {frames_t1<M, true>, C::T, C::SMEM}; }
-  static KernelShape loss(bool) { return {frames_t1<M, false, true>, C::T, C::SMEM}; }
+  static KernelShape loss(bool, bool = false) { return {frames_t1<M, false, true>, C::T, C::SMEM}; }
   static constexpr bool kRaw = false;
   static constexpr bool kRaw16 = false;
   static KernelShape raw(bool, bool = false) { return grad(false); }
@@ -58,8 +58,12 @@ struct FramesKernel<M, true> {
   static constexpr int NG = 1;
   static constexpr int kTileFwd = C::PW;
   static constexpr int kTileGrad = kQuads ? T4Cfg<M>::PW : (C::SWZ ? 0 : C::PW);
-  static KernelShape grad(bool tma) {
+  // tpr: the probe stays in tensor memory (four threads per line; probes
+  // shared by the frames of a peak)
+  static KernelShape grad(bool tma, bool tpr = false) {
     if constexpr (kQuads) {
+      if (tpr)
+        return {tma ? frames_t4<M, true, false, true> : frames_t4<M, false, false, true>, T4Cfg<M>::T, T4Cfg<M>::SMEM};
       return {tma ? frames_t4<M, true> : frames_t4<M, false>, T4Cfg<M>::T, T4Cfg<M>::SMEM};
     } else if constexpr (C::SWZ) {
       return {frames_t2<M, false>, C::T, C::SMEM};
@@ -73,8 +77,10 @@ struct FramesKernel<M, true> {
                : KernelShape{frames_t2<M, true>, C::T, C::SMEM};
   }
   // the loss alone, in the gradient kernel's layout (same tile width)
-  static KernelShape loss(bool tma) {
+  static KernelShape loss(bool tma, bool tpr = false) {
     if constexpr (kQuads) {
+      if (tpr)
+        return {tma ? frames_t4<M, true, true, true> : frames_t4<M, false, true, true>, T4Cfg<M>::T, T4Cfg<M>::SMEM};
       return {tma ? frames_t4<M, true, true> : frames_t4<M, false, true>, T4Cfg<M>::T, T4Cfg<M>::SMEM};
     } else if constexpr (C::SWZ) {
       return {frames_t2<M, false, false, false, false, true>, C::T, C::SMEM};
@@ -102,8 +108,8 @@ template <int M>
 bool frames_prepare_impl(FrameKernelInfo* info) {
   using K = FramesKernel<M>;
   bool ok = true;
-  for (int t = 0; t < 2; ++t)
-    ok = set_smem(K::grad(t != 0)) && set_smem(K::fwd(t != 0)) && set_smem(K::loss(t != 0)) && ok;
+  for (int t = 0; t < 4; ++t)
+    ok = set_smem(K::grad(t & 1, t >> 1)) && set_smem(K::fwd(t & 1)) && set_smem(K::loss(t & 1, t >> 1)) && ok;
   if (K::kRaw) ok = set_smem(K::raw(false)) && set_smem(K::raw(true)) && ok;
   if (K::kRaw16) ok = set_smem(K::raw(true, true)) && ok;
   if (!ok) return false;
@@ -129,7 +135,7 @@ cudaError_t frames_launch_impl(const FrameArgs& a, int grid, bool forward, cudaS
   using K = FramesKernel<M>;
   static const TmaMap kNone{};
   const bool tile = tm != nullptr && (forward ? K::kTileFwd : K::kTileGrad) > 0;
-  const KernelShape k = forward ? K::fwd(tile) : K::grad(tile);
+  const KernelShape k = forward ? K::fwd(tile) : K::grad(tile, a.probe_stride >= 0);
   k.fn<<<grid, k.threads, k.smem, s>>>(a, tile ? *tm : kNone);
   return cudaGetLastError();
 }
@@ -140,7 +146,7 @@ cudaError_t frames_launch_loss_impl(const FrameArgs& a, int grid, cudaStream_t s
   using K = FramesKernel<M>;
   static const TmaMap kNone{};
   const bool tile = tm != nullptr && K::kTileGrad > 0;
-  const KernelShape k = K::loss(tile);
+  const KernelShape k = K::loss(tile, a.probe_stride >= 0);
   k.fn<<<grid, k.threads, k.smem, s>>>(a, tile ? *tm : kNone);
   return cudaGetLastError();
 }

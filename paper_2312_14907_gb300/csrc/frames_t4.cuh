@@ -17,9 +17,20 @@
 //   sqrt(y)   [q1][M] + 8 (q1 / Q) floats: the four rows Q g + t a warp reads
 //             at eight consecutive q0 fall in different bank octets; 16-row
 //             bands of M floats, one bulk copy each.
+//
+// The probe (TPR): the 32 probe values a thread multiplies, P(4n + h, ln)
+// for n = 0 .. 31, are the same in A2 and A6 and for every frame of the
+// block's peak, so they are kept in tensor memory, in 64 columns of the
+// thread's own TMEM lane (warps w, w + 4, w + 8, w + 12 share a lane quarter
+// and take columns 64 (w / 4) on), and read with tcgen05.ld instead of twice
+// per frame from L2 (128 KB per probe does not fit in L1 beside the shared
+// buffers).  They are reloaded when the frame's probe changes (a new peak with
+// one probe per peak).  Probes that change with every scan position take the
+// global loads (TPR = false).
 #pragma once
 #include "fft_quad.cuh"
 #include "frames.cuh"
+#include "tmem.cuh"
 
 namespace mpbp {
 
@@ -138,9 +149,31 @@ MPBP_DI void t4_fetch(const FrameArgs& p, const T4Group<M>& g, const FrameRef& r
 // One frame's loss and gradient (inputs in flight); fetches the next frame's
 // inputs as soon as their buffers are free.  TMA: a wait that runs out clears
 // bs.ok and returns at once.
-template <int M, bool TMA, bool LOSS, typename AddLoss>
+// TMEM columns of the resident probe: 32 complex values a thread, four
+// threads (warps w, w + 4, w + 8, w + 12) per lane
+constexpr uint32_t kT4ProbeCols = 256;
+
+// the thread's 32 probe values P(4n + h, ln) of probe P into its TMEM words
+template <int M>
+MPBP_DI void t4_probe_to_tmem(const cf* P, const T4Group<M>& g, uint32_t tp) {
+  static_assert(T4Cfg<M>::H == 32, "the resident probe holds 32 values a thread");
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    uint32_t w[16];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const cf v = ldg_cf(P + (4 * (8 * c + j) + g.h) * M + g.ln);
+      w[2 * j] = __float_as_uint(v.x);
+      w[2 * j + 1] = __float_as_uint(v.y);
+    }
+    tmem_st16(tp + 16 * c, w);
+  }
+  tmem_wait_st();
+}
+
+template <int M, bool TMA, bool LOSS, bool TPR, typename AddLoss>
 MPBP_DI void t4_frame(const FrameArgs& p, const T4Group<M>& g, const FrameRef& cur, const FrameRef& nxt,
-                      AddLoss&& add_loss, BulkState& bs, const TmaMap* tm) {
+                      AddLoss&& add_loss, BulkState& bs, const TmaMap* tm, uint32_t tp) {
   using C = T4Cfg<M>;
   constexpr int H = C::H, PW = C::PW;
   cf* buf = g.buf;
@@ -162,11 +195,23 @@ MPBP_DI void t4_frame(const FrameArgs& p, const T4Group<M>& g, const FrameRef& c
 
   // A2: column ln, rows 4n + h
   cf v[H];
-  sfor<0, H>([&](auto n_) {
-    constexpr int n = decltype(n_)::value;
-    const int k0 = 4 * n + h;
-    v[n] = cmul(ldg_cf(P + k0 * M + ln), buf[k0 * PW + ln + dlt]);
-  });
+  if constexpr (TPR) {
+    uint32_t w[4][16];
+    sfor<0, 4>([&](auto c_) { tmem_ld16(tp + 16 * decltype(c_)::value, w[decltype(c_)::value]); });
+    tmem_wait_ld();
+    sfor<0, H>([&](auto n_) {
+      constexpr int n = decltype(n_)::value;
+      const int k0 = 4 * n + h;
+      const cf pv = cf{__uint_as_float(w[n / 8][2 * (n % 8)]), __uint_as_float(w[n / 8][2 * (n % 8) + 1])};
+      v[n] = cmul(pv, buf[k0 * PW + ln + dlt]);
+    });
+  } else {
+    sfor<0, H>([&](auto n_) {
+      constexpr int n = decltype(n_)::value;
+      const int k0 = 4 * n + h;
+      v[n] = cmul(ldg_cf(P + k0 * M + ln), buf[k0 * PW + ln + dlt]);
+    });
+  }
 
   // A3: columns, transpose, rows; the barrier orders the patch reads above
   // before the transpose writes of other threads
@@ -236,33 +281,69 @@ MPBP_DI void t4_frame(const FrameArgs& p, const T4Group<M>& g, const FrameRef& c
   cf* a = p.acc + cur.mpk * p.obj_stride + (long long)row * p.n2 + col;
   const long long step = 4LL * p.n2;
   const unsigned n1 = (unsigned)p.n1;
-  sfor<0, H>([&](auto k_) {
-    constexpr int k = decltype(k_)::value;
-    const cf w = cmul(ldg_cf(P + (4 * k + h) * M + ln), v[ct::brev<H>(k)]);
-    if (cok && (unsigned)row < n1) red_add_v2(a, w);
-    a += step;
-    row += 4;
-  });
+  if constexpr (TPR) {
+    // probe values by chunks of eight, the next chunk's load in flight while
+    // the current one is used
+    uint32_t w[2][16];
+    tmem_ld16(tp, w[0]);
+    tmem_wait_ld();
+    sfor<0, 4>([&](auto c_) {
+      constexpr int c = decltype(c_)::value;
+      if constexpr (c + 1 < 4) tmem_ld16(tp + 16 * (c + 1), w[(c + 1) & 1]);
+      sfor<0, 8>([&](auto j_) {
+        constexpr int j = decltype(j_)::value, k = 8 * c + j;
+        const cf pv = cf{__uint_as_float(w[c & 1][2 * j]), __uint_as_float(w[c & 1][2 * j + 1])};
+        const cf wv = cmul(pv, v[ct::brev<H>(k)]);
+        if (cok && (unsigned)row < n1) red_add_v2(a, wv);
+        a += step;
+        row += 4;
+      });
+      if constexpr (c + 1 < 4) tmem_wait_ld();
+    });
+  } else {
+    sfor<0, H>([&](auto k_) {
+      constexpr int k = decltype(k_)::value;
+      const cf w = cmul(ldg_cf(P + (4 * k + h) * M + ln), v[ct::brev<H>(k)]);
+      if (cok && (unsigned)row < n1) red_add_v2(a, w);
+      a += step;
+      row += 4;
+    });
+  }
 }
 
 // loss and gradient (LOSS: loss only): one frame per block, frames
 // round-robin over a persistent grid; TMA: inputs by tile and bulk copies
 // (tm: the objects' tensor map), else by cp.async
-template <int M, bool TMA, bool LOSS = false>
+// TPR: the probe resident in tensor memory (probes shared by all frames of a
+// peak: FrameArgs::probe_stride >= 0)
+template <int M, bool TMA, bool LOSS = false, bool TPR = false>
 __global__ void __launch_bounds__(T4Cfg<M>::T, T4Cfg<M>::MINB)
     frames_t4(const FrameArgs p, const __grid_constant__ TmaMap tm) {
   using C = T4Cfg<M>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[C::T / 32];
   __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
   if (blockIdx.x == 0 && threadIdx.x == 0 && p.arrivals) *p.arrivals = 0u;
   unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
   const T4Group<M> g = T4Group<M>::make(threadIdx.x, smem);
   BulkState bs{smem_addr(&mbar), 0u, true};
+  const int warp = threadIdx.x >> 5;
+  if constexpr (TPR) {
+    if (warp == 0) tmem_alloc(smem_addr(&tmem_base), kT4ProbeCols);
+  }
   if constexpr (TMA) {
     if (threadIdx.x == 0) mbar_init(bs.bar, 1);
-    __syncthreads();
   }
+  if constexpr (TMA || TPR) {
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+  }
+  // this thread's 64 probe columns: lane 32 (warp mod 4) + lane id, columns
+  // 64 (warp / 4) on
+  const uint32_t tp = TPR ? tmem_addr(tmem_base, 32u * (warp & 3), 64u * (warp >> 2)) : 0u;
+  const cf* tp_src = nullptr;   // the probe held in tensor memory (block-uniform)
   double lsum = 0.0;
   int it = blockIdx.x;
   FrameRef cur = frame_ref(p, it);
@@ -270,7 +351,14 @@ __global__ void __launch_bounds__(T4Cfg<M>::T, T4Cfg<M>::MINB)
   if constexpr (!TMA) cp_async_commit();
   for (; it < p.nframes; it += gridDim.x) {
     const FrameRef nxt = frame_ref(p, it + gridDim.x);
-    t4_frame<M, TMA, LOSS>(p, g, cur, nxt, [&](float fl) { lsum += (double)fl; }, bs, &tm);
+    if constexpr (TPR) {
+      const cf* P = frame_probe(p, cur, M * M);
+      if (P != tp_src) {
+        t4_probe_to_tmem<M>(P, g, tp);
+        tp_src = P;
+      }
+    }
+    t4_frame<M, TMA, LOSS, TPR>(p, g, cur, nxt, [&](float fl) { lsum += (double)fl; }, bs, &tm, tp);
     if (TMA && !bs.ok) {
       if (threadIdx.x == 0) atomicOr(p.err, kErrTimeout);
       break;
@@ -280,6 +368,11 @@ __global__ void __launch_bounds__(T4Cfg<M>::T, T4Cfg<M>::MINB)
   cp_async_wait_all();
   const double tot = block_sum_d<C::T>(lsum, red);
   if (threadIdx.x == 0) p.loss_part[blockIdx.x] = tot;
+  if constexpr (TPR) {
+    tmem_fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem_base, kT4ProbeCols);
+  }
 }
 
 }  // namespace mpbp
