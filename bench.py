@@ -437,8 +437,11 @@ def run_gpu(args):
         "hbm_roofline": {"bytes_per_frame": bpf, "achieved_gbs": value * bpf / 1e9 / world,
                          "peak_gbs": pk["hbm_gbs"], "frac": value * bpf / 1e9 / world / pk["hbm_gbs"],
                          "peak_src": pk["src"]},
-        "roofline": {"bound": "alu", "kernel": "frames_t4<128, tile copies> (fused per-frame kernel, "
-                                               "four threads per line)",
+        "roofline": {"bound": "alu", "kernel": ("frames_x3<tile copies, probe in TMEM> (fused per-frame kernel, "
+                                                "shared-memory exchange FFT schedule)"
+                                                if info["fft_schedule"] == mpbp.FFT_EXCHANGE else
+                                                "frames_t4<128, tile copies, probe in TMEM> (fused per-frame "
+                                                "kernel, shuffle FFT schedule)"),
                      "achieved": achieved_tf, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
                      "frac": achieved_tf / pk["fp32_tflops"], "traffic": traffic,
                      "traffic_src": (tr or {}).get("src"),
@@ -458,6 +461,19 @@ def run_gpu(args):
         "clocks": clk.summary(),
         "wall_s": wall,
     }
+    # the two FFT schedules of the M = 128 kernel on the same state (loss and
+    # gradient evaluations, CUDA events, L2 flushed between)
+    sched = {}
+    for name, sc in (("exchange", mpbp.FFT_EXCHANGE), ("shuffle", mpbp.FFT_SHUFFLE)):
+        prob.set_fft_schedule(sc)
+        e_ms, k_ms = time_evals(torch, prob, [t.clone() for t in x], max(3, min(args.steps, 10)), flush, stream)
+        sched[name] = {"ms_per_eval": e_ms, "kernel_ms": k_ms,
+                       "kernel_frac_fp32": fl / (k_ms / 1e3) / 1e12 / pk["fp32_tflops"]}
+    prob.set_fft_schedule(info["fft_schedule"])
+    line["fft_schedules"] = dict(sched, timed_step=("exchange" if info["fft_schedule"] == mpbp.FFT_EXCHANGE
+                                                    else "shuffle"),
+                                 what="columns 32 x 4 and rows 8 x 16 through shared-memory exchanges, or "
+                                      "radix-2 stages across threads by warp shuffles")
     # scan positions off the pixel grid (not the headline): seeded offsets in
     # [-1/2, 1/2] per scan position, one shifted probe per position; loss and
     # gradient evaluations on the same state, CUDA events, L2 flushed between
@@ -612,8 +628,8 @@ def alg1_block(torch, prob, spec, x, flush, stream):
 KERNEL_SOURCES = {
     64: ("frames.cuh", "bulk.cuh", "frames_inst.cuh", "fft_reg.cuh", "fft_pair.cuh", "frames_m64.cu",
          "mpbp_internal.h"),
-    128: ("frames.cuh", "frames_t4.cuh", "bulk.cuh", "frames_inst.cuh", "fft_reg.cuh", "fft_pair.cuh",
-          "fft_quad.cuh", "frames_m128.cu", "mpbp_internal.h"),
+    128: ("frames.cuh", "frames_t4.cuh", "frames_x3.cuh", "tmem.cuh", "bulk.cuh", "frames_inst.cuh",
+          "fft_reg.cuh", "fft_pair.cuh", "fft_quad.cuh", "frames_m128.cu", "mpbp_internal.h"),
 }
 
 

@@ -108,7 +108,18 @@ typedef struct {
                                  bulk copies: bit 0 the gradient kernel, bit 1 the
                                  forward kernel (none when a row of O is not a
                                  multiple of 16 bytes, i.e. odd n2: cp.async)  */
+  int32_t fft_schedule;       /* MPBP_FFT_* in use (frame side 128)            */
 } mpbp_info;
+
+/* How the 128-point lines of the frame side M = 128 are split over the four
+ * threads that hold one (mpbp_set_fft_schedule). */
+enum {
+  MPBP_FFT_SHUFFLE = 0,   /* 32-point FFTs in registers and the last two radix-2
+                             stages across the threads by warp shuffles      */
+  MPBP_FFT_EXCHANGE = 1   /* columns as 32 x 4 and rows as 8 x 16 transforms in
+                             three register layouts joined by two shared-memory
+                             exchanges per 2-D transform (default)           */
+};
 
 /* Arithmetic of the 2-D DFTs (F of Eq. 2 and its adjoint in the gradient). */
 enum {
@@ -400,6 +411,12 @@ mpbp_status mpbp_loss_grad_noalloc(const mpbp_problem *problem, const float *pro
                                    float *g_u, double *g_alpha, int32_t *dev_err,
                                    void *stream);
 
+/* Selects the FFT schedule (MPBP_FFT_*) of this context's FP32 loss-and-
+ * gradient kernel for frame side 128 (both compute the same transforms of
+ * Eq. 2; other frame sides ignore it).  Host-side only; a captured step keeps
+ * the schedule of its capture.  MPBP_ERR_INVALID_ARG for an unknown value. */
+mpbp_status mpbp_set_fft_schedule(mpbp_ctx *ctx, int32_t schedule);
+
 /* Overrides the fused frame kernel's schedule: resident blocks per SM used to
  * size its persistent grid (0 = occupancy maximum).  Host-side only. */
 mpbp_status mpbp_set_schedule(mpbp_ctx *ctx, int32_t blocks_per_sm);
@@ -453,7 +470,9 @@ mpbp_status mpbp_set_batch_schedule(mpbp_ctx *ctx, int32_t mode, int32_t order);
 
 /* Autotuner for one context: times mpbp_loss_grad at rho, u, alpha (dev)
  * with every schedule from 1 to the occupancy limit of resident frame-kernel
- * blocks per SM and keeps the fastest (mpbp_set_schedule).  loss, g_rho and
+ * blocks per SM -- for frame side 128 in FP32 precision, under both FFT
+ * schedules (mpbp_set_fft_schedule) -- and keeps the fastest
+ * (mpbp_set_schedule, mpbp_set_fft_schedule).  loss, g_rho and
  * g_u (dev) receive the evaluations.  With cache_path != NULL (host string)
  * the choice is first looked up in that JSON-lines file under a key made of
  * the GPU name, M, D, n1 x n2 and the frame count, and appended to it after

@@ -8,16 +8,16 @@ bool frames_prepare_m16(FrameKernelInfo*);
 bool frames_prepare_m32(FrameKernelInfo*);
 bool frames_prepare_m64(FrameKernelInfo*);
 bool frames_prepare_m128(FrameKernelInfo*);
-cudaError_t frames_launch_m8(const FrameArgs&, int, bool, cudaStream_t, const TmaMap*);
-cudaError_t frames_launch_m16(const FrameArgs&, int, bool, cudaStream_t, const TmaMap*);
-cudaError_t frames_launch_m32(const FrameArgs&, int, bool, cudaStream_t, const TmaMap*);
-cudaError_t frames_launch_m64(const FrameArgs&, int, bool, cudaStream_t, const TmaMap*);
-cudaError_t frames_launch_m128(const FrameArgs&, int, bool, cudaStream_t, const TmaMap*);
-cudaError_t frames_launch_loss_m8(const FrameArgs&, int, cudaStream_t, const TmaMap*);
-cudaError_t frames_launch_loss_m16(const FrameArgs&, int, cudaStream_t, const TmaMap*);
-cudaError_t frames_launch_loss_m32(const FrameArgs&, int, cudaStream_t, const TmaMap*);
-cudaError_t frames_launch_loss_m64(const FrameArgs&, int, cudaStream_t, const TmaMap*);
-cudaError_t frames_launch_loss_m128(const FrameArgs&, int, cudaStream_t, const TmaMap*);
+cudaError_t frames_launch_m8(const FrameArgs&, int, bool, cudaStream_t, const TmaMap*, int);
+cudaError_t frames_launch_m16(const FrameArgs&, int, bool, cudaStream_t, const TmaMap*, int);
+cudaError_t frames_launch_m32(const FrameArgs&, int, bool, cudaStream_t, const TmaMap*, int);
+cudaError_t frames_launch_m64(const FrameArgs&, int, bool, cudaStream_t, const TmaMap*, int);
+cudaError_t frames_launch_m128(const FrameArgs&, int, bool, cudaStream_t, const TmaMap*, int);
+cudaError_t frames_launch_loss_m8(const FrameArgs&, int, cudaStream_t, const TmaMap*, int);
+cudaError_t frames_launch_loss_m16(const FrameArgs&, int, cudaStream_t, const TmaMap*, int);
+cudaError_t frames_launch_loss_m32(const FrameArgs&, int, cudaStream_t, const TmaMap*, int);
+cudaError_t frames_launch_loss_m64(const FrameArgs&, int, cudaStream_t, const TmaMap*, int);
+cudaError_t frames_launch_loss_m128(const FrameArgs&, int, cudaStream_t, const TmaMap*, int);
 cudaError_t frames_launch_raw_m32(const FrameArgs&, int, cudaStream_t, const TmaMap*, bool);
 cudaError_t frames_launch_raw_m64(const FrameArgs&, int, cudaStream_t, const TmaMap*, bool);
 cudaError_t frames_launch_raw_m128(const FrameArgs&, int, cudaStream_t, const TmaMap*, bool);
@@ -33,24 +33,25 @@ bool frames_prepare(int m, FrameKernelInfo* info) {
   }
 }
 
-cudaError_t frames_launch(int m, const FrameArgs& a, int grid, bool forward, cudaStream_t s, const TmaMap* tm) {
+cudaError_t frames_launch(int m, const FrameArgs& a, int grid, bool forward, cudaStream_t s, const TmaMap* tm,
+                          int layout) {
   switch (m) {
-    case 8: return frames_launch_m8(a, grid, forward, s, tm);
-    case 16: return frames_launch_m16(a, grid, forward, s, tm);
-    case 32: return frames_launch_m32(a, grid, forward, s, tm);
-    case 64: return frames_launch_m64(a, grid, forward, s, tm);
-    case 128: return frames_launch_m128(a, grid, forward, s, tm);
+    case 8: return frames_launch_m8(a, grid, forward, s, tm, layout);
+    case 16: return frames_launch_m16(a, grid, forward, s, tm, layout);
+    case 32: return frames_launch_m32(a, grid, forward, s, tm, layout);
+    case 64: return frames_launch_m64(a, grid, forward, s, tm, layout);
+    case 128: return frames_launch_m128(a, grid, forward, s, tm, layout);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t frames_launch_loss(int m, const FrameArgs& a, int grid, cudaStream_t s, const TmaMap* tm) {
+cudaError_t frames_launch_loss(int m, const FrameArgs& a, int grid, cudaStream_t s, const TmaMap* tm, int layout) {
   switch (m) {
-    case 8: return frames_launch_loss_m8(a, grid, s, tm);
-    case 16: return frames_launch_loss_m16(a, grid, s, tm);
-    case 32: return frames_launch_loss_m32(a, grid, s, tm);
-    case 64: return frames_launch_loss_m64(a, grid, s, tm);
-    case 128: return frames_launch_loss_m128(a, grid, s, tm);
+    case 8: return frames_launch_loss_m8(a, grid, s, tm, layout);
+    case 16: return frames_launch_loss_m16(a, grid, s, tm, layout);
+    case 32: return frames_launch_loss_m32(a, grid, s, tm, layout);
+    case 64: return frames_launch_loss_m64(a, grid, s, tm, layout);
+    case 128: return frames_launch_loss_m128(a, grid, s, tm, layout);
     default: return cudaErrorInvalidValue;
   }
 }

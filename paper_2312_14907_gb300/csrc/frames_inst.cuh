@@ -9,6 +9,7 @@
 #include "frames.cuh"
 #include "frames_launch.h"
 #include "frames_t4.cuh"
+#include "frames_x3.cuh"
 
 namespace mpbp {
 
@@ -38,14 +39,17 @@ struct KernelShape {
   int smem;
 };
 
+// M = 128 loss-and-gradient layouts (FrameLayout): radix-2 stages across
+// threads by shuffles (frames_t4) or three register layouts joined by
+// shared-memory exchanges (frames_x3)
 template <int M>
 struct FramesKernel<M, false> {
   using C = T1Cfg<M>;
   static constexpr int NG = C::NG;
   static constexpr int kTileGrad = 0, kTileFwd = 0;
-  static KernelShape grad(bool, bool = false) { return {frames_t1<M, false>, C::T, C::SMEM}; }
+  static KernelShape grad(bool, bool = false, int = 0) { return {frames_t1<M, false>, C::T, C::SMEM}; }
   static KernelShape fwd(bool) { return {frames_t1<M, true>, C::T, C::SMEM}; }
-  static KernelShape loss(bool, bool = false) { return {frames_t1<M, false, true>, C::T, C::SMEM}; }
+  static KernelShape loss(bool, bool = false, int = 0) { return {frames_t1<M, false, true>, C::T, C::SMEM}; }
   static constexpr bool kRaw = false;
   static constexpr bool kRaw16 = false;
   static KernelShape raw(bool, bool = false) { return grad(false); }
@@ -60,8 +64,12 @@ struct FramesKernel<M, true> {
   static constexpr int kTileGrad = kQuads ? T4Cfg<M>::PW : (C::SWZ ? 0 : C::PW);
   // tpr: the probe stays in tensor memory (four threads per line; probes
   // shared by the frames of a peak)
-  static KernelShape grad(bool tma, bool tpr = false) {
+  static KernelShape grad(bool tma, bool tpr = false, int layout = kLayoutDefault) {
     if constexpr (kQuads) {
+      if (layout == kLayoutExchange) {
+        if (tpr) return {tma ? frames_x3<true, false, true> : frames_x3<false, false, true>, X3Cfg::T, X3Cfg::SMEM};
+        return {tma ? frames_x3<true> : frames_x3<false>, X3Cfg::T, X3Cfg::SMEM};
+      }
       if (tpr)
         return {tma ? frames_t4<M, true, false, true> : frames_t4<M, false, false, true>, T4Cfg<M>::T, T4Cfg<M>::SMEM};
       return {tma ? frames_t4<M, true> : frames_t4<M, false>, T4Cfg<M>::T, T4Cfg<M>::SMEM};
@@ -77,8 +85,12 @@ struct FramesKernel<M, true> {
                : KernelShape{frames_t2<M, true>, C::T, C::SMEM};
   }
   // the loss alone, in the gradient kernel's layout (same tile width)
-  static KernelShape loss(bool tma, bool tpr = false) {
+  static KernelShape loss(bool tma, bool tpr = false, int layout = kLayoutDefault) {
     if constexpr (kQuads) {
+      if (layout == kLayoutExchange) {
+        if (tpr) return {tma ? frames_x3<true, true, true> : frames_x3<false, true, true>, X3Cfg::T, X3Cfg::SMEM};
+        return {tma ? frames_x3<true, true> : frames_x3<false, true>, X3Cfg::T, X3Cfg::SMEM};
+      }
       if (tpr)
         return {tma ? frames_t4<M, true, true, true> : frames_t4<M, false, true, true>, T4Cfg<M>::T, T4Cfg<M>::SMEM};
       return {tma ? frames_t4<M, true, true> : frames_t4<M, false, true>, T4Cfg<M>::T, T4Cfg<M>::SMEM};
@@ -108,8 +120,9 @@ template <int M>
 bool frames_prepare_impl(FrameKernelInfo* info) {
   using K = FramesKernel<M>;
   bool ok = true;
-  for (int t = 0; t < 4; ++t)
-    ok = set_smem(K::grad(t & 1, t >> 1)) && set_smem(K::fwd(t & 1)) && set_smem(K::loss(t & 1, t >> 1)) && ok;
+  for (int t = 0; t < 8; ++t)
+    ok = set_smem(K::grad(t & 1, (t >> 1) & 1, t >> 2)) && set_smem(K::fwd(t & 1)) &&
+         set_smem(K::loss(t & 1, (t >> 1) & 1, t >> 2)) && ok;
   if (K::kRaw) ok = set_smem(K::raw(false)) && set_smem(K::raw(true)) && ok;
   if (K::kRaw16) ok = set_smem(K::raw(true, true)) && ok;
   if (!ok) return false;
@@ -118,10 +131,10 @@ bool frames_prepare_impl(FrameKernelInfo* info) {
   info->frames_per_block = K::NG;
   info->tile_w_grad = K::kTileGrad;
   info->tile_w_fwd = K::kTileFwd;
-  // the schedule's blocks per SM must hold for both copy variants
+  // the schedule's blocks per SM must hold for both copy variants and layouts
   int nb = 1 << 20;
-  for (int t = 0; t < 2; ++t) {
-    const KernelShape k = K::grad(t != 0);
+  for (int t = 0; t < 4; ++t) {
+    const KernelShape k = K::grad(t & 1, false, t >> 1);
     int b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k.fn, k.threads, k.smem) != cudaSuccess) return false;
     nb = b < nb ? b : nb;
@@ -131,22 +144,23 @@ bool frames_prepare_impl(FrameKernelInfo* info) {
 }
 
 template <int M>
-cudaError_t frames_launch_impl(const FrameArgs& a, int grid, bool forward, cudaStream_t s, const TmaMap* tm) {
+cudaError_t frames_launch_impl(const FrameArgs& a, int grid, bool forward, cudaStream_t s, const TmaMap* tm,
+                               int layout) {
   using K = FramesKernel<M>;
   static const TmaMap kNone{};
   const bool tile = tm != nullptr && (forward ? K::kTileFwd : K::kTileGrad) > 0;
-  const KernelShape k = forward ? K::fwd(tile) : K::grad(tile, a.probe_stride >= 0);
+  const KernelShape k = forward ? K::fwd(tile) : K::grad(tile, a.probe_stride >= 0, layout);
   k.fn<<<grid, k.threads, k.smem, s>>>(a, tile ? *tm : kNone);
   return cudaGetLastError();
 }
 
 // the loss alone (no adjoint, no scatter-add)
 template <int M>
-cudaError_t frames_launch_loss_impl(const FrameArgs& a, int grid, cudaStream_t s, const TmaMap* tm) {
+cudaError_t frames_launch_loss_impl(const FrameArgs& a, int grid, cudaStream_t s, const TmaMap* tm, int layout) {
   using K = FramesKernel<M>;
   static const TmaMap kNone{};
   const bool tile = tm != nullptr && K::kTileGrad > 0;
-  const KernelShape k = K::loss(tile, a.probe_stride >= 0);
+  const KernelShape k = K::loss(tile, a.probe_stride >= 0, layout);
   k.fn<<<grid, k.threads, k.smem, s>>>(a, tile ? *tm : kNone);
   return cudaGetLastError();
 }
@@ -168,15 +182,15 @@ cudaError_t frames_launch_raw_impl(const FrameArgs& a, int grid, cudaStream_t s,
   namespace mpbp {                                                                         \
   bool frames_prepare_m##M(FrameKernelInfo* info) { return frames_prepare_impl<M>(info); } \
   cudaError_t frames_launch_m##M(const FrameArgs& a, int grid, bool forward, cudaStream_t s, \
-                                 const TmaMap* tm) {                                       \
-    return frames_launch_impl<M>(a, grid, forward, s, tm);                                 \
+                                 const TmaMap* tm, int layout) {                           \
+    return frames_launch_impl<M>(a, grid, forward, s, tm, layout);                         \
   }                                                                                        \
   cudaError_t frames_launch_raw_m##M(const FrameArgs& a, int grid, cudaStream_t s,        \
                                      const TmaMap* tm, bool y16) {                         \
     return frames_launch_raw_impl<M>(a, grid, s, tm, y16);                                 \
   }                                                                                        \
   cudaError_t frames_launch_loss_m##M(const FrameArgs& a, int grid, cudaStream_t s,       \
-                                      const TmaMap* tm) {                                  \
-    return frames_launch_loss_impl<M>(a, grid, s, tm);                                     \
+                                      const TmaMap* tm, int layout) {                      \
+    return frames_launch_loss_impl<M>(a, grid, s, tm, layout);                             \
   }                                                                                        \
   }

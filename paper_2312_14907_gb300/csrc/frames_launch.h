@@ -51,6 +51,13 @@ cudaError_t batched_launch(const BatchArgs& b, int grid, cudaStream_t s);
 bool batched_m_prepare(int m, int* blocks_per_sm);
 cudaError_t batched_m_launch(int m, const BatchArgs& b, int grid, cudaStream_t s);
 
+// Layout of the M = 128 loss-and-gradient kernel (ignored for other sides):
+// radix-2 stages of each 128-point line across four threads by shuffles
+// (frames_t4.cuh), or 32 x 4 column and 8 x 16 row factorisations in three
+// register layouts joined by shared-memory exchanges (frames_x3.cuh).
+enum FrameLayout { kLayoutShuffle = MPBP_FFT_SHUFFLE, kLayoutExchange = MPBP_FFT_EXCHANGE };
+constexpr int kLayoutDefault = kLayoutExchange;
+
 // Prepares the kernels of frame side m on the current device (shared-memory
 // carve-out) and reports their launch shape.  Returns false for unsupported m.
 bool frames_prepare(int m, FrameKernelInfo* info);
@@ -60,11 +67,12 @@ bool frames_prepare(int m, FrameKernelInfo* info);
 // tensor map with the box width the kernel reports (tile_w_*), or nullptr
 // for the cp.async copies.
 cudaError_t frames_launch(int m, const FrameArgs& a, int grid, bool forward, cudaStream_t s,
-                          const TmaMap* tm = nullptr);
+                          const TmaMap* tm = nullptr, int layout = kLayoutDefault);
 
 // The loss alone (Eq. 4 over the frames of a, no adjoint and no scatter-add):
 // per-block partials in a.loss_part.  tm as for the gradient kernel.
-cudaError_t frames_launch_loss(int m, const FrameArgs& a, int grid, cudaStream_t s, const TmaMap* tm = nullptr);
+cudaError_t frames_launch_loss(int m, const FrameArgs& a, int grid, cudaStream_t s, const TmaMap* tm = nullptr,
+                               int layout = kLayoutDefault);
 
 // Raw-data gradient kernel (a.yraw: counts in their natural layout, device
 // memory; sqrt(y) written to a.aT_w).  Frame sides 32, 64, 128.

@@ -1,0 +1,458 @@
+// frames_x3.cuh -- the fused frame kernel for M = 128 (A2-A7 of frames.cuh)
+// with each 2-D transform computed in three register layouts joined by two
+// shared-memory exchanges, in place of the radix-2 stages across threads
+// (warp shuffles and selects) of frames_t4.cuh.
+//
+// Index split (W = exp(-2 pi i / 128); 512 threads, 32 values each):
+//   rows    r = 4 n + h,          q0 = k' + 32 k''   (n, k' < 32; h, k'' < 4)
+//   columns c = c_r + 16 c_a,     q1 = m' + 8 m''    (c_r, m'' < 16; c_a, m' < 8)
+// and the forward transform Psi = F psi of Eq. 2 as
+//   X1(q0, c)  = sum_h  W4^(k'' h) W^(k' h) [sum_n W32^(n k') psi(4n + h, c)]
+//   Psi(q0,q1) = sum_c_r W16^(m'' c_r) W^(m' c_r) [sum_c_a W8^(m' c_a) X1(q0, c_r + 16 c_a)]
+// Layouts (register index -> thread index):
+//   L1  n (32)                    | c, h        lane = 8 h + (c mod 8), warp = c / 8
+//   L2  h or k'' (4) x c_a or m'  | k', c_r     lane = c_r + 16 (k' mod 2), warp = k' / 2
+//   L3  c_r or m'' (16) x m_r (2) | q0, m_t     lane = k', warp = 4 k'' + m_t;  m' = m_t + 4 m_r
+// L1: the 32-point transforms over n.  L2: twiddle W^(k' h), 4-point
+// transforms over h, 8-point over c_a, twiddle W^(m' c_r).  L3: 16-point
+// transforms over c_r; the residual (A4) reads sqrt(y)[q1][q0] with 32
+// consecutive q0 per warp.  The adjoint Z = F conj(chi) (A5) runs the same
+// factorisation backwards (16-point over m'' in L3, twiddle W^(m' c_r) and
+// 8-point over m' in L2, 4-point over k'' and twiddle W^(k' h) in L2, 32-point
+// over k' in L1) and ends in L1, the columns layout of the scatter (A6, A7).
+// The per-thread twiddles W^(h k'), h = 1..3, and W^(m' c_r), m' = 1..7, are
+// formed once per block and kept in tensor memory (20 words a thread).
+//
+// Shared layouts (complex values), every 16-lane half-warp on 16 distinct
+// 8-byte banks:
+//   A  [h][k'][c ^ 8 (h mod 2)]       (L1 <-> L2), 16,384 values
+//   B  [m'][q0][17] (c_r or m'')      (L2 <-> L3), 17,408 values
+//   the patch tile [k0][M + 8] as in frames_t4.cuh, and sqrt(y) [q1][q0].
+#pragma once
+#include "frames_t4.cuh"
+#include "tmem.cuh"
+
+namespace mpbp {
+
+struct X3Cfg {
+  static constexpr int M = 128;
+  static constexpr int T = 512;
+  static constexpr int PW = M + 8;                               // patch row (the tile copy's box width)
+  static constexpr int A_VALS = 4 * 32 * 128;                    // layout A
+  static constexpr int B_VALS = 8 * 128 * 17;                    // layout B
+  static constexpr int PATCH_VALS = M * PW;
+  static constexpr int BUF = (B_VALS > PATCH_VALS ? B_VALS : PATCH_VALS) * (int)sizeof(cf);
+  static constexpr int ABUF = M * M * (int)sizeof(float);       // sqrt(y) [q1][q0]
+  static constexpr int SMEM = BUF + ABUF + 128;                  // + alignment of the tile destination
+  static constexpr uint32_t TMEM_COLS = 512;                     // probe (0..255), twiddles (256..)
+  static_assert(A_VALS <= B_VALS && BUF % 16 == 0, "layouts");
+};
+
+// a thread's indices in the three layouts
+struct X3Roles {
+  int tid;
+  // L1
+  int c, h;
+  // L2
+  int kp, cr;
+  // L3
+  int q0, mt;
+  MPBP_DI static X3Roles make(int tid) {
+    X3Roles r;
+    r.tid = tid;
+    const int w = tid >> 5, l = tid & 31;
+    r.c = 8 * w + (l & 7);
+    r.h = l >> 3;
+    r.kp = 2 * w + (l >> 4);
+    r.cr = l & 15;
+    r.q0 = l + 32 * (w >> 2);
+    r.mt = w & 3;
+    return r;
+  }
+};
+
+MPBP_DI int x3_a(int h, int kp, int c) { return (h * 32 + kp) * 128 + (c ^ ((h & 1) << 3)); }
+MPBP_DI int x3_b(int mp, int q0, int i) { return (mp * 128 + q0) * 17 + i; }
+
+// W^j = exp(-2 pi i j / 128)
+MPBP_DI cf x3_w128(int j) {
+  float s, c;
+  sincospif((float)(j & 127) / 64.0f, &s, &c);
+  return cf{c, -s};
+}
+
+// The thread's 20 twiddle words into tensor memory: W^(h k'), h = 1..3, then
+// W^(m' c_r), m' = 1..7 (words 6..19)
+MPBP_DI void x3_twiddles_to_tmem(const X3Roles& r, uint32_t tt) {
+  uint32_t w[16], w4[16];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const cf t = i < 3 ? x3_w128((i + 1) * r.kp) : x3_w128((i - 2) * r.cr);
+    const int k = 2 * i;
+    if (k < 16) {
+      w[k] = __float_as_uint(t.x);
+      w[k + 1] = __float_as_uint(t.y);
+    } else {
+      w4[k - 16] = __float_as_uint(t.x);
+      w4[k - 15] = __float_as_uint(t.y);
+    }
+  }
+#pragma unroll
+  for (int k = 4; k < 16; ++k) w4[k] = 0u;
+  tmem_st16(tt, w);
+  tmem_st16(tt + 16, w4);
+  tmem_wait_st();
+}
+
+struct X3Tw {
+  cf th[4];   // th[h] = W^(h k'), th[0] unused
+  cf um[8];   // um[m'] = W^(m' c_r), um[0] unused
+};
+
+MPBP_DI void x3_load_twiddles(uint32_t tt, X3Tw& t) {
+  uint32_t w[16], w4[16];
+  tmem_ld16(tt, w);
+  tmem_ld16(tt + 16, w4);
+  tmem_wait_ld();
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const int k = 2 * i;
+    const cf v = k < 16 ? cf{__uint_as_float(w[k]), __uint_as_float(w[k + 1])}
+                        : cf{__uint_as_float(w4[k - 16]), __uint_as_float(w4[k - 15])};
+    if (i < 3) t.th[i + 1] = v;
+    else t.um[i - 2] = v;
+  }
+}
+
+// inputs of frame fr: the patch tile and sqrt(y) [q1][q0] (64 KB); TMA: one
+// thread issues a tile load and one bulk copy on the block's mbarrier, after
+// the barrier that freed the buffers; else cp.async by every thread
+template <bool TMA>
+MPBP_DI void x3_fetch(const FrameArgs& p, const X3Roles& r, const FrameRef& fr, cf* buf, float* abuf,
+                      const BulkState& bs, const TmaMap* tm) {
+  using C = X3Cfg;
+  constexpr int M = C::M;
+  if constexpr (TMA) {
+    if (r.tid == 0) {
+      constexpr uint32_t kPatch = M * C::PW * (uint32_t)sizeof(cf);
+      constexpr uint32_t kAmp = M * M * (uint32_t)sizeof(float);
+      fence_async_smem();
+      mbar_arrive_tx(bs.bar, (fr.valid ? kPatch + kAmp : 0u) + tm->tx_extra);
+      if (fr.valid) {
+        tile_load_3d(smem_addr(buf), &tm->map, fr.s.y - (fr.s.y & 1), fr.s.x, fr.mpk, bs.bar);
+        bulk_load(smem_addr(abuf), p.aT + (long long)fr.f * M * M, kAmp, bs.bar);
+      }
+    }
+  } else {
+    const PatchSrc q = patch_src<M>(p, fr);
+#pragma unroll 2
+    for (int n = 0; n < 32; ++n) {
+      const int k0 = 4 * n + r.h;
+      fetch_patch_elem(q, k0, r.c, buf + k0 * C::PW + r.c);
+    }
+    if (q.amp) {
+#pragma unroll
+      for (int i = 0; i < M * M / 4 / C::T; ++i) {
+        const int ch = r.tid + i * C::T;
+        cp_async16(abuf + 4 * ch, q.amp + 4 * ch);
+      }
+    }
+  }
+}
+
+// One frame's loss and gradient (inputs in flight); fetches the next frame's
+// inputs as soon as their buffers are free.  TMA: a wait that runs out clears
+// bs.ok and returns at once.
+template <bool TMA, bool LOSS, bool TPR, typename AddLoss>
+MPBP_DI void x3_frame(const FrameArgs& p, const X3Roles& r, const FrameRef& cur, const FrameRef& nxt,
+                      AddLoss&& add_loss, BulkState& bs, const TmaMap* tm, cf* buf, float* abuf, uint32_t tp,
+                      uint32_t tt) {
+  using C = X3Cfg;
+  constexpr int M = C::M, PW = C::PW;
+  const cf* P = frame_probe(p, cur, M * M);
+  if constexpr (TMA) {
+    bs.ok = bulk_wait(bs.bar, bs.parity);
+    bs.parity ^= 1u;
+    if (!bs.ok) return;
+  } else {
+    cp_async_wait_all();
+    __syncthreads();
+  }
+  const int dlt = TMA ? (cur.s.y & 1) : 0;   // a tile starts at an even column
+
+  // ---- A2 + the 32-point transforms over n (L1)
+  cf v[32];
+  if constexpr (TPR) {
+    uint32_t w[4][16];
+    sfor<0, 4>([&](auto c_) { tmem_ld16(tp + 16 * decltype(c_)::value, w[decltype(c_)::value]); });
+    tmem_wait_ld();
+    sfor<0, 32>([&](auto n_) {
+      constexpr int n = decltype(n_)::value;
+      const cf pv = cf{__uint_as_float(w[n / 8][2 * (n % 8)]), __uint_as_float(w[n / 8][2 * (n % 8) + 1])};
+      v[n] = cmul(pv, buf[(4 * n + r.h) * PW + r.c + dlt]);
+    });
+  } else {
+    sfor<0, 32>([&](auto n_) {
+      constexpr int n = decltype(n_)::value;
+      const int k0 = 4 * n + r.h;
+      v[n] = cmul(ldg_cf(P + k0 * M + r.c), buf[k0 * PW + r.c + dlt]);
+    });
+  }
+  fft_line<32>(v);   // Y(h, k', c) in slot brev(k')
+  __syncthreads();   // the patch reads are done
+  sfor<0, 32>([&](auto k_) {
+    constexpr int k = decltype(k_)::value;
+    buf[x3_a(r.h, k, r.c)] = v[ct::brev<32>(k)];
+  });
+  __syncthreads();
+
+  // ---- L2: twiddle, 4-point over h, 8-point over c_a, twiddle
+  cf x[32];
+  {
+  X3Tw tw;
+  x3_load_twiddles(tt, tw);   // x[4 h + .. ] layouts as named below
+  sfor<0, 4>([&](auto h_) {
+    constexpr int hh = decltype(h_)::value;
+    sfor<0, 8>([&](auto a_) {
+      constexpr int ca = decltype(a_)::value;
+      x[hh * 8 + ca] = buf[x3_a(hh, r.kp, r.cr + 16 * ca)];
+    });
+  });
+  sfor<0, 8>([&](auto a_) {
+    constexpr int ca = decltype(a_)::value;
+    cf t4[4];
+    t4[0] = x[ca];
+    sfor<1, 4>([&](auto h_) {
+      constexpr int hh = decltype(h_)::value;
+      t4[hh] = cmul(x[hh * 8 + ca], tw.th[hh]);
+    });
+    fft_line<4>(t4);
+    sfor<0, 4>([&](auto k_) {
+      constexpr int kk = decltype(k_)::value;
+      x[kk * 8 + ca] = t4[ct::brev<4>(kk)];   // x[8 k'' + c_a]
+    });
+  });
+  sfor<0, 4>([&](auto k_) {
+    constexpr int kk = decltype(k_)::value;
+    cf t8[8];
+    sfor<0, 8>([&](auto a_) { t8[decltype(a_)::value] = x[kk * 8 + decltype(a_)::value]; });
+    fft_line<8>(t8);
+    x[kk * 8] = t8[0];
+    sfor<1, 8>([&](auto m_) {
+      constexpr int mp = decltype(m_)::value;
+      x[kk * 8 + mp] = cmul(t8[ct::brev<8>(mp)], tw.um[mp]);   // x[8 k'' + m']
+    });
+  });
+  }
+  __syncthreads();   // every layout-A read is done
+  sfor<0, 4>([&](auto k_) {
+    constexpr int kk = decltype(k_)::value;
+    sfor<0, 8>([&](auto m_) {
+      constexpr int mp = decltype(m_)::value;
+      buf[x3_b(mp, r.kp + 32 * kk, r.cr)] = x[kk * 8 + mp];
+    });
+  });
+  __syncthreads();
+
+  // ---- L3: 16-point over c_r; A4 on row q0
+  sfor<0, 2>([&](auto m_) {
+    constexpr int mr = decltype(m_)::value;
+    sfor<0, 16>([&](auto i_) {
+      constexpr int i = decltype(i_)::value;
+      v[mr * 16 + i] = buf[x3_b(r.mt + 4 * mr, r.q0, i)];
+    });
+  });
+  sfor<0, 2>([&](auto m_) {
+    constexpr int mr = decltype(m_)::value;
+    cf t16[16];
+    sfor<0, 16>([&](auto i_) { t16[decltype(i_)::value] = v[mr * 16 + decltype(i_)::value]; });
+    fft_line<16>(t16);
+    sfor<0, 16>([&](auto i_) {
+      constexpr int mm = decltype(i_)::value;
+      v[mr * 16 + mm] = t16[ct::brev<16>(mm)];   // Psi(q0, m' + 8 m'') at v[16 m_r + m'']
+    });
+  });
+  const float* bg = p.bgT ? p.bgT + (long long)cur.f * M * M : nullptr;
+  float fl = 0.0f;
+  sfor<0, 2>([&](auto m_) {
+    constexpr int mr = decltype(m_)::value;
+    sfor<0, 16>([&](auto i_) {
+      constexpr int mm = decltype(i_)::value;
+      const int q1 = r.mt + 4 * mr + 8 * mm;
+      const float bv = bg ? bg[q1 * M + r.q0] : 0.0f;
+      v[mr * 16 + mm] = residual(v[mr * 16 + mm], abuf[q1 * M + r.q0], bv, fl);
+    });
+  });
+  add_loss(cur.valid ? 0.5f * fl : 0.0f);
+  if constexpr (LOSS) {
+    __syncthreads();   // every read of the buffers is done
+    x3_fetch<TMA>(p, r, nxt, buf, abuf, bs, tm);
+    if constexpr (!TMA) cp_async_commit();
+    return;
+  }
+
+  // ---- A5: Z = F conj(chi), L3: 16-point over m''
+  sfor<0, 2>([&](auto m_) {
+    constexpr int mr = decltype(m_)::value;
+    cf t16[16];
+    sfor<0, 16>([&](auto i_) { t16[decltype(i_)::value] = v[mr * 16 + decltype(i_)::value]; });
+    fft_line<16>(t16);   // T(m', kr) in slot brev(kr)
+    sfor<0, 16>([&](auto i_) {
+      constexpr int kr = decltype(i_)::value;
+      v[mr * 16 + kr] = t16[ct::brev<16>(kr)];
+    });
+  });
+  __syncthreads();   // every layout-B read is done
+  sfor<0, 2>([&](auto m_) {
+    constexpr int mr = decltype(m_)::value;
+    sfor<0, 16>([&](auto i_) {
+      constexpr int kr = decltype(i_)::value;
+      buf[x3_b(r.mt + 4 * mr, r.q0, kr)] = v[mr * 16 + kr];
+    });
+  });
+  __syncthreads();
+
+  // ---- L2: twiddle, 8-point over m', 4-point over k'', twiddle
+  X3Tw tw;
+  x3_load_twiddles(tt, tw);
+  sfor<0, 4>([&](auto k_) {
+    constexpr int kk = decltype(k_)::value;
+    cf t8[8];
+    t8[0] = buf[x3_b(0, r.kp + 32 * kk, r.cr)];
+    sfor<1, 8>([&](auto m_) {
+      constexpr int mp = decltype(m_)::value;
+      t8[mp] = cmul(buf[x3_b(mp, r.kp + 32 * kk, r.cr)], tw.um[mp]);
+    });
+    fft_line<8>(t8);
+    sfor<0, 8>([&](auto a_) {
+      constexpr int ka = decltype(a_)::value;
+      x[kk * 8 + ka] = t8[ct::brev<8>(ka)];   // x[8 k'' + k_a]
+    });
+  });
+  sfor<0, 8>([&](auto a_) {
+    constexpr int ka = decltype(a_)::value;
+    cf t4[4];
+    sfor<0, 4>([&](auto k_) { t4[decltype(k_)::value] = x[decltype(k_)::value * 8 + ka]; });
+    fft_line<4>(t4);
+    x[ka] = t4[0];
+    sfor<1, 4>([&](auto h_) {
+      constexpr int hh = decltype(h_)::value;
+      x[hh * 8 + ka] = cmul(t4[ct::brev<4>(hh)], tw.th[hh]);   // x[8 h' + k_a]
+    });
+  });
+  __syncthreads();   // every layout-B read is done
+  sfor<0, 4>([&](auto h_) {
+    constexpr int hh = decltype(h_)::value;
+    sfor<0, 8>([&](auto a_) {
+      constexpr int ka = decltype(a_)::value;
+      buf[x3_a(hh, r.kp, r.cr + 16 * ka)] = x[hh * 8 + ka];
+    });
+  });
+  __syncthreads();
+
+  // ---- L1: 32-point over k'; A6 + A7
+  sfor<0, 32>([&](auto k_) {
+    constexpr int k = decltype(k_)::value;
+    v[k] = buf[x3_a(r.h, k, r.c)];
+  });
+  __syncthreads();   // both buffers are free
+  x3_fetch<TMA>(p, r, nxt, buf, abuf, bs, tm);
+  if constexpr (!TMA) cp_async_commit();
+  fft_line<32>(v);   // Z(4 n + h, c) in slot brev(n)
+
+  const int col = cur.s.y + r.c;
+  const bool cok = cur.valid && col >= 0 && col < p.n2;
+  int row = cur.s.x + r.h;
+  cf* a = p.acc + cur.mpk * p.obj_stride + (long long)row * p.n2 + col;
+  const long long step = 4LL * p.n2;
+  const unsigned n1 = (unsigned)p.n1;
+  if constexpr (TPR) {
+    uint32_t w[2][16];
+    tmem_ld16(tp, w[0]);
+    tmem_wait_ld();
+    sfor<0, 4>([&](auto c_) {
+      constexpr int c = decltype(c_)::value;
+      if constexpr (c + 1 < 4) tmem_ld16(tp + 16 * (c + 1), w[(c + 1) & 1]);
+      sfor<0, 8>([&](auto j_) {
+        constexpr int j = decltype(j_)::value, n = 8 * c + j;
+        const cf pv = cf{__uint_as_float(w[c & 1][2 * j]), __uint_as_float(w[c & 1][2 * j + 1])};
+        const cf wv = cmul(pv, v[ct::brev<32>(n)]);
+        if (cok && (unsigned)row < n1) red_add_v2(a, wv);
+        a += step;
+        row += 4;
+      });
+      if constexpr (c + 1 < 4) tmem_wait_ld();
+    });
+  } else {
+    sfor<0, 32>([&](auto n_) {
+      constexpr int n = decltype(n_)::value;
+      const cf wv = cmul(ldg_cf(P + (4 * n + r.h) * M + r.c), v[ct::brev<32>(n)]);
+      if (cok && (unsigned)row < n1) red_add_v2(a, wv);
+      a += step;
+      row += 4;
+    });
+  }
+}
+
+// loss and gradient (LOSS: loss only): one frame per block, frames
+// round-robin over a persistent grid; TMA: inputs by tile and bulk copies
+// (tm: the objects' tensor map), else by cp.async; TPR: the probe resident
+// in tensor memory (probes shared by all frames of a peak)
+template <bool TMA, bool LOSS = false, bool TPR = false>
+__global__ void __launch_bounds__(X3Cfg::T, 1) frames_x3(const FrameArgs p, const __grid_constant__ TmaMap tm) {
+  using C = X3Cfg;
+  constexpr int M = C::M;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[C::T / 32];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && p.arrivals) *p.arrivals = 0u;
+  unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+  cf* buf = reinterpret_cast<cf*>(smem);
+  float* abuf = reinterpret_cast<float*>(smem + C::BUF);
+  const X3Roles r = X3Roles::make(threadIdx.x);
+  BulkState bs{smem_addr(&mbar), 0u, true};
+  const int warp = threadIdx.x >> 5;
+  if (warp == 0) tmem_alloc(smem_addr(&tmem_base), C::TMEM_COLS);
+  if (TMA && threadIdx.x == 0) mbar_init(bs.bar, 1);
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  // this thread's words: lane 32 (warp mod 4) + lane id; the probe in columns
+  // 64 (warp / 4) .. + 63, the twiddles in 256 + 32 (warp / 4) .. + 19
+  const uint32_t tp = tmem_addr(tmem_base, 32u * (warp & 3), 64u * (warp >> 2));
+  const uint32_t tt = tmem_addr(tmem_base, 32u * (warp & 3), 256u + 32u * (warp >> 2));
+  x3_twiddles_to_tmem(r, tt);
+  const cf* tp_src = nullptr;   // the probe held in tensor memory (block-uniform)
+  double lsum = 0.0;
+  int it = blockIdx.x;
+  FrameRef cur = frame_ref(p, it);
+  x3_fetch<TMA>(p, r, cur, buf, abuf, bs, &tm);
+  if constexpr (!TMA) cp_async_commit();
+  for (; it < p.nframes; it += gridDim.x) {
+    const FrameRef nxt = frame_ref(p, it + gridDim.x);
+    if constexpr (TPR) {
+      const cf* P = frame_probe(p, cur, M * M);
+      if (P != tp_src) {
+        // the probe values of this thread's L1 role: P(4 n + h, c)
+        T4Group<M> g4 = T4Group<M>::make(threadIdx.x, smem);
+        t4_probe_to_tmem<M>(P, g4, tp);
+        tp_src = P;
+      }
+    }
+    x3_frame<TMA, LOSS, TPR>(p, r, cur, nxt, [&](float fl) { lsum += (double)fl; }, bs, &tm, buf, abuf, tp, tt);
+    if (TMA && !bs.ok) {
+      if (threadIdx.x == 0) atomicOr(p.err, kErrTimeout);
+      break;
+    }
+    cur = nxt;
+  }
+  cp_async_wait_all();
+  const double tot = block_sum_d<C::T>(lsum, red);
+  if (threadIdx.x == 0) p.loss_part[blockIdx.x] = tot;
+  tmem_fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem_base, C::TMEM_COLS);
+}
+
+}  // namespace mpbp

@@ -47,6 +47,7 @@ struct mpbp_ctx {
   CUtensorMap ymap16[kStageSlots];
   long long ymap16_per = 0;
   int precision = MPBP_PRECISION_FP32;
+  int fft_schedule = kLayoutDefault;   // M = 128: FrameLayout of the gradient kernel
   void* tc_w = nullptr;       // split DFT matrix of the tensor-core kernel
   int blocks_per_sm = 0;  // schedule in use
   int frames_grid_cap = 0;
@@ -202,10 +203,10 @@ int frames_grid_fft(const mpbp_ctx* c, long long nframes) {
 // the gradient-mode frame kernel of the context's precision
 cudaError_t launch_frames(const mpbp_ctx* c, const FrameArgs& fa, int grid, cudaStream_t s) {
   if (c->precision == MPBP_PRECISION_TC_SPLIT16) return tc_launch(fa, c->tc_w, grid, s);
-  if (!c->tile_grad || fa.O != c->O) return frames_launch(c->M, fa, grid, false, s, nullptr);
+  if (!c->tile_grad || fa.O != c->O) return frames_launch(c->M, fa, grid, false, s, nullptr, c->fft_schedule);
   TmaMap tm = c->tm_grad;
   tm.tx_extra = c->test_tx_extra;
-  return frames_launch(c->M, fa, grid, false, s, &tm);
+  return frames_launch(c->M, fa, grid, false, s, &tm, c->fft_schedule);
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -576,6 +577,15 @@ mpbp_status mpbp_get_info(const mpbp_ctx* c, mpbp_info* info) {
   info->launches_step = 3;       // the same; the assembly also applies the update
   info->precision = c->precision;
   info->tile_copies = (c->tile_grad ? 1 : 0) | (c->tile_fwd ? 2 : 0);
+  info->fft_schedule = c->fft_schedule;
+  return MPBP_OK;
+}
+
+mpbp_status mpbp_set_fft_schedule(mpbp_ctx* c, int32_t schedule) {
+  if (!c) return MPBP_ERR_INVALID_ARG;
+  if (schedule != MPBP_FFT_SHUFFLE && schedule != MPBP_FFT_EXCHANGE)
+    return fail(c, MPBP_ERR_INVALID_ARG, "unknown FFT schedule");
+  c->fft_schedule = schedule;
   return MPBP_OK;
 }
 
@@ -756,9 +766,9 @@ mpbp_status mpbp_loss(mpbp_ctx* c, const float* rho, const float* u, const float
   if (c->tile_grad) {
     TmaMap tm = c->tm_grad;
     tm.tx_extra = c->test_tx_extra;
-    MPBP_CUDA(c, frames_launch_loss(c->M, fa, grid, s, &tm));
+    MPBP_CUDA(c, frames_launch_loss(c->M, fa, grid, s, &tm, c->fft_schedule));
   } else {
-    MPBP_CUDA(c, frames_launch_loss(c->M, fa, grid, s, nullptr));
+    MPBP_CUDA(c, frames_launch_loss(c->M, fa, grid, s, nullptr, c->fft_schedule));
   }
   MPBP_CUDA(c, launch_loss_reduce(c->loss_part, grid, loss, c->err, s));
   return MPBP_OK;
@@ -1715,25 +1725,36 @@ mpbp_status mpbp_autotune(mpbp_ctx* c, const float* rho, const float* u, const f
   k << gpu_name(c->device) << "|single|m" << c->M << "|p" << c->precision << "|d" << c->D << "|n" << c->n1 << "x" << c->n2
     << "|f" << c->nframes;
   const double cached = cache_lookup(cache_path, k.str(), "blocks_per_sm");
-  if (cached >= 1.0) return mpbp_set_schedule(c, (int32_t)cached);
+  if (cached >= 1.0) {
+    const double sched = cache_lookup(cache_path, k.str(), "fft_schedule");
+    if (sched >= 0.0) c->fft_schedule = (int)sched;
+    return mpbp_set_schedule(c, (int32_t)cached);
+  }
   cudaStream_t s = S(stream);
-  int best = c->fk.blocks_per_sm;
+  // candidates: resident blocks per SM x (M = 128, FP32 FFTs) the FFT schedule
+  const int nsched = (c->M == 128 && c->precision == MPBP_PRECISION_FP32) ? 2 : 1;
+  int best = c->fk.blocks_per_sm, best_sched = c->fft_schedule;
   double best_ms = 1e30;
-  for (int b = 1; b <= c->fk.blocks_per_sm; ++b) {
-    mpbp_set_schedule(c, b);
-    mpbp_status st = MPBP_OK;
-    const double ms = time_ms(s, 3, [&]() {
-      return mpbp_loss_grad(c, rho, u, alpha, nullptr, 0, loss, g_rho, g_u, nullptr, stream);
-    }, &st);
-    if (st != MPBP_OK) return st;
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = b;
+  for (int sc = 0; sc < nsched; ++sc) {
+    if (nsched > 1) c->fft_schedule = sc;
+    for (int b = 1; b <= c->fk.blocks_per_sm; ++b) {
+      mpbp_set_schedule(c, b);
+      mpbp_status st = MPBP_OK;
+      const double ms = time_ms(s, 3, [&]() {
+        return mpbp_loss_grad(c, rho, u, alpha, nullptr, 0, loss, g_rho, g_u, nullptr, stream);
+      }, &st);
+      if (st != MPBP_OK) return st;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = b;
+        best_sched = c->fft_schedule;
+      }
     }
   }
+  c->fft_schedule = best_sched;
   mpbp_set_schedule(c, best);
   std::ostringstream f;
-  f << "\"blocks_per_sm\": " << best << ", \"ms\": " << best_ms;
+  f << "\"blocks_per_sm\": " << best << ", \"fft_schedule\": " << best_sched << ", \"ms\": " << best_ms;
   cache_store(cache_path, k.str(), f.str());
   return MPBP_OK;
 }

@@ -68,7 +68,8 @@ class Info(ctypes.Structure):
                 ("frames_block", ctypes.c_int32), ("frames_smem", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("num_sms", ctypes.c_int32),
                 ("launches_loss_grad", ctypes.c_int32), ("launches_step", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("tile_copies", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("tile_copies", ctypes.c_int32),
+                ("fft_schedule", ctypes.c_int32)]
 
 
 EXPORTS = ["mpbp_status_string", "mpbp_create", "mpbp_destroy", "mpbp_last_error",
@@ -81,8 +82,10 @@ EXPORTS = ["mpbp_status_string", "mpbp_create", "mpbp_destroy", "mpbp_last_error
            "mpbp_adam_init", "mpbp_adam_step", "mpbp_adam_get_state", "mpbp_adam_set_state",
            "mpbp_loss_grad_phases", "mpbp_unwrap_phases", "mpbp_project_displacement",
            "mpbp_illumination", "mpbp_set_test_stall", "mpbp_loss_grad_host_counts16",
-           "mpbp_set_scan_offsets", "mpbp_shift_probe", "mpbp_loss"]
+           "mpbp_set_scan_offsets", "mpbp_shift_probe", "mpbp_loss", "mpbp_set_fft_schedule"]
 
+FFT_SHUFFLE = 0           # M = 128: radix-2 stages across threads by warp shuffles
+FFT_EXCHANGE = 1          # M = 128: three register layouts joined by shared-memory exchanges
 PRECISION_FP32 = 0        # FFTs on the CUDA cores
 PRECISION_TC_SPLIT16 = 1  # dense DFT matrices on the tensor cores, split FP16
 
@@ -138,6 +141,8 @@ def load(build_if_missing=True):
     lib.mpbp_loss_grad_batched.restype = st
     lib.mpbp_set_schedule.argtypes = [V, I32]
     lib.mpbp_set_schedule.restype = st
+    lib.mpbp_set_fft_schedule.argtypes = [V, I32]
+    lib.mpbp_set_fft_schedule.restype = st
     lib.mpbp_set_precision.argtypes = [V, I32]
     lib.mpbp_set_precision.restype = st
     lib.mpbp_adam_init.argtypes = [V, P(AdamParams), V, V]
@@ -282,6 +287,10 @@ class Problem:
         """DFT arithmetic of the gradient evaluations: PRECISION_FP32 (FFTs) or
         PRECISION_TC_SPLIT16 (tensor cores, frame side 64 only)."""
         self._check(self._lib.mpbp_set_precision(self._h, int(mode)), "mpbp_set_precision")
+
+    def set_fft_schedule(self, schedule):
+        """FFT schedule of the M = 128 gradient kernel: FFT_SHUFFLE or FFT_EXCHANGE."""
+        self._check(self._lib.mpbp_set_fft_schedule(self._h, int(schedule)), "mpbp_set_fft_schedule")
 
     def set_schedule(self, blocks_per_sm):
         self._check(self._lib.mpbp_set_schedule(self._h, int(blocks_per_sm)), "mpbp_set_schedule")

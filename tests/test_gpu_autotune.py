@@ -43,6 +43,26 @@ def test_single_problem_autotune_and_cache(tmp_path):
     p.sync_status()
 
 
+def test_m128_autotune_covers_both_fft_schedules(tmp_path):
+    """At frame side 128 the autotuner also chooses between the two FFT
+    schedules (shuffles across threads; shared-memory exchanges) and caches
+    the choice; the chosen schedule still computes the oracle's result."""
+    spec, scan = custom_spec(256, 128, 6, 24, npeaks=2, offset=-4)
+    case = Case(spec, scan=scan, state="perturbed")
+    p, x = _gpu(case)
+    cache = tmp_path / "tune.jsonl"
+    p.autotune(*x, cache_path=str(cache))
+    line = json.loads(cache.read_text().splitlines()[0])
+    assert line["fft_schedule"] in (0, 1) and line["blocks_per_sm"] >= 1
+    assert p.info()["fft_schedule"] == line["fft_schedule"]
+    _check(case, p.loss_grad(*x))
+    p2, x2 = _gpu(case)
+    p2.set_fft_schedule(1 - line["fft_schedule"])
+    p2.autotune(*x2, cache_path=str(cache))          # from the cache
+    assert p2.info()["fft_schedule"] == line["fft_schedule"]
+    p.sync_status()
+
+
 def test_batched_autotune_picks_a_working_schedule(tmp_path):
     from paper_2312_14907_gb300 import mpbp
     cases = [Case(*custom_spec(96, 32, 5, 14, npeaks=3, offset=-2, seed=1), state="perturbed"),

@@ -77,16 +77,18 @@ def test_forward_and_objects_match_oracle(m):
             assert rel_l2(I[d, j], I_ref[d, j]) <= 1e-5, (d, j)
 
 
-@pytest.mark.parametrize("m", [16, 64, 128])
-def test_random_probe_per_peak_and_background(m):
-    """Unstructured per-peak probes catch transposed or mis-indexed operands;
-    the background enters the intensity of Eq. 2."""
+@pytest.mark.parametrize("m,schedule", [(16, 1), (64, 1), (128, 0), (128, 1)])
+def test_random_probe_per_peak_and_background(m, schedule):
+    """Unstructured per-peak probes catch transposed or mis-indexed operands
+    (and, at M = 128, the reload of the probe held in tensor memory when the
+    peak changes); the background enters the intensity of Eq. 2."""
     n = 2 * m + 8
     spec, scan = custom_spec(n, m, 3, m // 2 + 1, npeaks=3, offset=-3, probe_per_peak=True)
     rng = np.random.default_rng(100 + m)
     probe = (rng.standard_normal((3, m, m)) + 1j * rng.standard_normal((3, m, m))).astype(np.complex64)
     case = Case(spec, scan=scan, probe=probe, state="perturbed", bg=True)
     p, x = _gpu(case)
+    p.set_fft_schedule(schedule)
     _check_loss_grad(case, p.loss_grad(*x))
     I = p.forward(*x).cpu().numpy()
     I_ref = case.oracle.forward(case.rho, case.u, case.alpha, case.probe, bg=case.bg)
@@ -122,8 +124,9 @@ def test_tile_and_plain_copies_match_oracle(m):
         q.sync_status()
 
 
+@pytest.mark.parametrize("schedule", [0, 1])
 @pytest.mark.parametrize("n2,tiles", [(256, 3), (255, 0)])
-def test_m128_steady_state_matches_oracle(n2, tiles):
+def test_m128_steady_state_matches_oracle(n2, tiles, schedule):
     """The M = 128 gradient kernel runs one block per SM, so a block takes a
     second frame only when a launch has more than one frame per SM.  338
     frames (13 x 13 scan, 2 peaks) give every block of the 152-block grid two
@@ -131,10 +134,14 @@ def test_m128_steady_state_matches_oracle(n2, tiles):
     transforms the current one, reuses its buffers and flips its barrier
     phase at least twice.  Element by element against the oracle, through
     the tile-copy path (even n2) and the cp.async path (odd n2), with the
-    scan overhanging the grid; the same again through a frame list."""
+    scan overhanging the grid, under both FFT schedules (radix-2 stages
+    across threads by shuffles; three register layouts joined by shared-
+    memory exchanges); the same again through a frame list."""
     spec, scan = custom_spec(256, 128, 13, 10, npeaks=2, offset=-6, n2=n2)
     case = Case(spec, scan=scan, state="perturbed")
     p, x = _gpu(case)
+    p.set_fft_schedule(schedule)
+    assert p.info()["fft_schedule"] == schedule
     info = p.info()
     assert info["tile_copies"] == tiles, info
     assert spec.nframes > 2 * info["frames_grid"], (spec.nframes, info)
@@ -330,8 +337,8 @@ def test_batched_matches_single_problems():
         p.sync_status()
 
 
-@pytest.mark.parametrize("m", [64, 128])
-def test_tile_copy_wait_runs_out_and_reports(m):
+@pytest.mark.parametrize("m,schedule", [(64, 1), (128, 0), (128, 1)])
+def test_tile_copy_wait_runs_out_and_reports(m, schedule):
     """The frame kernels' waits for their tile copies are bounded: with the
     barrier told to expect bytes that never arrive, each block gives up
     after its time limit, the call reports MPBP_ERR_TIMEOUT, and the context
@@ -341,6 +348,7 @@ def test_tile_copy_wait_runs_out_and_reports(m):
     spec, scan = custom_spec(2 * m + 8, m, 3, m // 2, npeaks=2, offset=-2)
     case = Case(spec, scan=scan, state="perturbed")
     p, x = _gpu(case)
+    p.set_fft_schedule(schedule)
     assert p.info()["tile_copies"] == 3
     p.set_test_stall(True)
     t0 = time.time()
