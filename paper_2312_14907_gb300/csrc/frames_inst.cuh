@@ -66,10 +66,8 @@ struct FramesKernel<M, true> {
   // shared by the frames of a peak)
   static KernelShape grad(bool tma, bool tpr = false, int layout = kLayoutDefault) {
     if constexpr (kQuads) {
-      if (layout == kLayoutExchange) {
-        if (tpr) return {tma ? frames_x3<true, false, true> : frames_x3<false, false, true>, X3Cfg::T, X3Cfg::SMEM};
+      if (layout == kLayoutExchange)   // the probe always in tensor memory
         return {tma ? frames_x3<true> : frames_x3<false>, X3Cfg::T, X3Cfg::SMEM};
-      }
       if (tpr)
         return {tma ? frames_t4<M, true, false, true> : frames_t4<M, false, false, true>, T4Cfg<M>::T, T4Cfg<M>::SMEM};
       return {tma ? frames_t4<M, true> : frames_t4<M, false>, T4Cfg<M>::T, T4Cfg<M>::SMEM};
@@ -87,10 +85,8 @@ struct FramesKernel<M, true> {
   // the loss alone, in the gradient kernel's layout (same tile width)
   static KernelShape loss(bool tma, bool tpr = false, int layout = kLayoutDefault) {
     if constexpr (kQuads) {
-      if (layout == kLayoutExchange) {
-        if (tpr) return {tma ? frames_x3<true, true, true> : frames_x3<false, true, true>, X3Cfg::T, X3Cfg::SMEM};
+      if (layout == kLayoutExchange)
         return {tma ? frames_x3<true, true> : frames_x3<false, true>, X3Cfg::T, X3Cfg::SMEM};
-      }
       if (tpr)
         return {tma ? frames_t4<M, true, true, true> : frames_t4<M, false, true, true>, T4Cfg<M>::T, T4Cfg<M>::SMEM};
       return {tma ? frames_t4<M, true, true> : frames_t4<M, false, true>, T4Cfg<M>::T, T4Cfg<M>::SMEM};

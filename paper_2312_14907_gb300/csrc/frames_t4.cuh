@@ -294,7 +294,7 @@ MPBP_DI void t4_frame(const FrameArgs& p, const T4Group<M>& g, const FrameRef& c
         constexpr int j = decltype(j_)::value, k = 8 * c + j;
         const cf pv = cf{__uint_as_float(w[c & 1][2 * j]), __uint_as_float(w[c & 1][2 * j + 1])};
         const cf wv = cmul(pv, v[ct::brev<H>(k)]);
-        if (cok && (unsigned)row < n1) red_add_v2(a, wv);
+        red_add_v2_if(a, wv, cok && (unsigned)row < n1);
         a += step;
         row += 4;
       });

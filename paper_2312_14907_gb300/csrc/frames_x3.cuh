@@ -109,11 +109,20 @@ struct X3Tw {
   cf um[8];   // um[m'] = W^(m' c_r), um[0] unused
 };
 
-MPBP_DI void x3_load_twiddles(uint32_t tt, X3Tw& t) {
+// the twiddle words in flight (issued before a barrier, used after it)
+struct X3TwRaw {
   uint32_t w[16], w4[16];
-  tmem_ld16(tt, w);
-  tmem_ld16(tt + 16, w4);
+};
+
+MPBP_DI void x3_issue_twiddles(uint32_t tt, X3TwRaw& raw) {
+  tmem_ld16(tt, raw.w);
+  tmem_ld16(tt + 16, raw.w4);
+}
+
+MPBP_DI void x3_finish_twiddles(const X3TwRaw& raw, X3Tw& t) {
   tmem_wait_ld();
+  const uint32_t(&w)[16] = raw.w;
+  const uint32_t(&w4)[16] = raw.w4;
 #pragma unroll
   for (int i = 0; i < 10; ++i) {
     const int k = 2 * i;
@@ -163,17 +172,22 @@ MPBP_DI void x3_fetch(const FrameArgs& p, const X3Roles& r, const FrameRef& fr, 
 // One frame's loss and gradient (inputs in flight); fetches the next frame's
 // inputs as soon as their buffers are free.  TMA: a wait that runs out clears
 // bs.ok and returns at once.
-template <bool TMA, bool LOSS, bool TPR, typename AddLoss>
+template <bool TMA, bool LOSS, typename AddLoss>
 MPBP_DI void x3_frame(const FrameArgs& p, const X3Roles& r, const FrameRef& cur, const FrameRef& nxt,
                       AddLoss&& add_loss, BulkState& bs, const TmaMap* tm, cf* buf, float* abuf, uint32_t tp,
                       uint32_t tt) {
   using C = X3Cfg;
   constexpr int M = C::M, PW = C::PW;
-  const cf* P = frame_probe(p, cur, M * M);
+  // the probe values of A2 load from tensor memory while the inputs land
+  uint32_t w[4][16];
+  sfor<0, 4>([&](auto c_) { tmem_ld16(tp + 16 * decltype(c_)::value, w[decltype(c_)::value]); });
   if constexpr (TMA) {
     bs.ok = bulk_wait(bs.bar, bs.parity);
     bs.parity ^= 1u;
-    if (!bs.ok) return;
+    if (!bs.ok) {
+      tmem_wait_ld();
+      return;
+    }
   } else {
     cp_async_wait_all();
     __syncthreads();
@@ -182,35 +196,27 @@ MPBP_DI void x3_frame(const FrameArgs& p, const X3Roles& r, const FrameRef& cur,
 
   // ---- A2 + the 32-point transforms over n (L1)
   cf v[32];
-  if constexpr (TPR) {
-    uint32_t w[4][16];
-    sfor<0, 4>([&](auto c_) { tmem_ld16(tp + 16 * decltype(c_)::value, w[decltype(c_)::value]); });
-    tmem_wait_ld();
-    sfor<0, 32>([&](auto n_) {
-      constexpr int n = decltype(n_)::value;
-      const cf pv = cf{__uint_as_float(w[n / 8][2 * (n % 8)]), __uint_as_float(w[n / 8][2 * (n % 8) + 1])};
-      v[n] = cmul(pv, buf[(4 * n + r.h) * PW + r.c + dlt]);
-    });
-  } else {
-    sfor<0, 32>([&](auto n_) {
-      constexpr int n = decltype(n_)::value;
-      const int k0 = 4 * n + r.h;
-      v[n] = cmul(ldg_cf(P + k0 * M + r.c), buf[k0 * PW + r.c + dlt]);
-    });
-  }
+  tmem_wait_ld();
+  sfor<0, 32>([&](auto n_) {
+    constexpr int n = decltype(n_)::value;
+    const cf pv = cf{__uint_as_float(w[n / 8][2 * (n % 8)]), __uint_as_float(w[n / 8][2 * (n % 8) + 1])};
+    v[n] = cmul(pv, buf[(4 * n + r.h) * PW + r.c + dlt]);
+  });
   fft_line<32>(v);   // Y(h, k', c) in slot brev(k')
   __syncthreads();   // the patch reads are done
   sfor<0, 32>([&](auto k_) {
     constexpr int k = decltype(k_)::value;
     buf[x3_a(r.h, k, r.c)] = v[ct::brev<32>(k)];
   });
+  X3TwRaw twr;
+  x3_issue_twiddles(tt, twr);   // in flight across the barrier
   __syncthreads();
 
   // ---- L2: twiddle, 4-point over h, 8-point over c_a, twiddle
   cf x[32];
   {
   X3Tw tw;
-  x3_load_twiddles(tt, tw);   // x[4 h + .. ] layouts as named below
+  x3_finish_twiddles(twr, tw);   // x[4 h + .. ] layouts as named below
   sfor<0, 4>([&](auto h_) {
     constexpr int hh = decltype(h_)::value;
     sfor<0, 8>([&](auto a_) {
@@ -310,11 +316,13 @@ MPBP_DI void x3_frame(const FrameArgs& p, const X3Roles& r, const FrameRef& cur,
       buf[x3_b(r.mt + 4 * mr, r.q0, kr)] = v[mr * 16 + kr];
     });
   });
+  X3TwRaw twr2;
+  x3_issue_twiddles(tt, twr2);   // in flight across the barrier
   __syncthreads();
 
   // ---- L2: twiddle, 8-point over m', 4-point over k'', twiddle
   X3Tw tw;
-  x3_load_twiddles(tt, tw);
+  x3_finish_twiddles(twr2, tw);
   sfor<0, 4>([&](auto k_) {
     constexpr int kk = decltype(k_)::value;
     cf t8[8];
@@ -366,39 +374,33 @@ MPBP_DI void x3_frame(const FrameArgs& p, const X3Roles& r, const FrameRef& cur,
   cf* a = p.acc + cur.mpk * p.obj_stride + (long long)row * p.n2 + col;
   const long long step = 4LL * p.n2;
   const unsigned n1 = (unsigned)p.n1;
-  if constexpr (TPR) {
-    uint32_t w[2][16];
-    tmem_ld16(tp, w[0]);
+  {
+    uint32_t w2[2][16];
+    tmem_ld16(tp, w2[0]);
     tmem_wait_ld();
     sfor<0, 4>([&](auto c_) {
       constexpr int c = decltype(c_)::value;
-      if constexpr (c + 1 < 4) tmem_ld16(tp + 16 * (c + 1), w[(c + 1) & 1]);
+      if constexpr (c + 1 < 4) tmem_ld16(tp + 16 * (c + 1), w2[(c + 1) & 1]);
       sfor<0, 8>([&](auto j_) {
         constexpr int j = decltype(j_)::value, n = 8 * c + j;
-        const cf pv = cf{__uint_as_float(w[c & 1][2 * j]), __uint_as_float(w[c & 1][2 * j + 1])};
+        const cf pv = cf{__uint_as_float(w2[c & 1][2 * j]), __uint_as_float(w2[c & 1][2 * j + 1])};
         const cf wv = cmul(pv, v[ct::brev<32>(n)]);
-        if (cok && (unsigned)row < n1) red_add_v2(a, wv);
+        red_add_v2_if(a, wv, cok && (unsigned)row < n1);
         a += step;
         row += 4;
       });
       if constexpr (c + 1 < 4) tmem_wait_ld();
-    });
-  } else {
-    sfor<0, 32>([&](auto n_) {
-      constexpr int n = decltype(n_)::value;
-      const cf wv = cmul(ldg_cf(P + (4 * n + r.h) * M + r.c), v[ct::brev<32>(n)]);
-      if (cok && (unsigned)row < n1) red_add_v2(a, wv);
-      a += step;
-      row += 4;
     });
   }
 }
 
 // loss and gradient (LOSS: loss only): one frame per block, frames
 // round-robin over a persistent grid; TMA: inputs by tile and bulk copies
-// (tm: the objects' tensor map), else by cp.async; TPR: the probe resident
-// in tensor memory (probes shared by all frames of a peak)
-template <bool TMA, bool LOSS = false, bool TPR = false>
+// (tm: the objects' tensor map), else by cp.async.  The probe values of a
+// thread sit in tensor memory and are reloaded when the frame's probe
+// changes: once per block for one probe, per peak for one probe per peak,
+// per frame for probes shifted per scan position.
+template <bool TMA, bool LOSS = false>
 __global__ void __launch_bounds__(X3Cfg::T, 1) frames_x3(const FrameArgs p, const __grid_constant__ TmaMap tm) {
   using C = X3Cfg;
   constexpr int M = C::M;
@@ -431,7 +433,7 @@ __global__ void __launch_bounds__(X3Cfg::T, 1) frames_x3(const FrameArgs p, cons
   if constexpr (!TMA) cp_async_commit();
   for (; it < p.nframes; it += gridDim.x) {
     const FrameRef nxt = frame_ref(p, it + gridDim.x);
-    if constexpr (TPR) {
+    {
       const cf* P = frame_probe(p, cur, M * M);
       if (P != tp_src) {
         // the probe values of this thread's L1 role: P(4 n + h, c)
@@ -440,7 +442,7 @@ __global__ void __launch_bounds__(X3Cfg::T, 1) frames_x3(const FrameArgs p, cons
         tp_src = P;
       }
     }
-    x3_frame<TMA, LOSS, TPR>(p, r, cur, nxt, [&](float fl) { lsum += (double)fl; }, bs, &tm, buf, abuf, tp, tt);
+    x3_frame<TMA, LOSS>(p, r, cur, nxt, [&](float fl) { lsum += (double)fl; }, bs, &tm, buf, abuf, tp, tt);
     if (TMA && !bs.ok) {
       if (threadIdx.x == 0) atomicOr(p.err, kErrTimeout);
       break;
