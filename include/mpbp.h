@@ -227,9 +227,9 @@ mpbp_status mpbp_loss_grad_host(mpbp_ctx *ctx, const float *y, const float *rho,
 /* mpbp_loss_grad_host with the measured data as 16-bit photon counts: y is
  * host uint16 [D][J][M][M] (natural layout, each count exact; counts above
  * 65535 cannot be given this way), half the bytes of the float call across
- * the host link.  On frame sides 64 and 128 (FP32 precision, even n2) the
- * frame kernel reads the staged 16-bit counts itself; otherwise they are
- * widened to floats on the device first.  Everything else as
+ * the host link.  On frame side 64 (FP32 precision, even n2) the frame
+ * kernel reads the staged 16-bit counts itself; otherwise they are widened
+ * to floats on the device first.  Everything else as
  * mpbp_loss_grad_host; y must not be NULL. */
 mpbp_status mpbp_loss_grad_host_counts16(mpbp_ctx *ctx, const uint16_t *y, const float *rho,
                                          const float *u, const float *alpha, double *loss,

@@ -56,9 +56,12 @@ cudaError_t frames_launch_loss(int m, const FrameArgs& a, int grid, cudaStream_t
   }
 }
 
-bool frames_raw_supported(int m) { return m == 32 || m == 64 || m == 128; }
+// M = 128 takes the staged counts through the transpose kernel and the
+// four-threads-per-line kernels (faster than the pair layout's raw-data
+// variant, whose 64 values a thread spill)
+bool frames_raw_supported(int m) { return m == 32 || m == 64; }
 
-bool frames_raw16_supported(int m) { return m == 64 || m == 128; }
+bool frames_raw16_supported(int m) { return m == 64; }
 
 cudaError_t frames_launch_raw(int m, const FrameArgs& a, int grid, cudaStream_t s, const TmaMap* tm,
                               bool y16) {

@@ -97,14 +97,20 @@ struct FramesKernel<M, true> {
                  : KernelShape{frames_t2<M, false, false, false, false, true>, C::T, C::SMEM};
     }
   }
-  static constexpr bool kRaw = true;
-  static constexpr bool kRaw16 = M >= 64;   // 16-bit counts by tile copies
+  // raw-data variants for M = 32, 64 (M = 128 host chunks go through the
+  // transpose kernel and the four-threads-per-line kernels)
+  static constexpr bool kRaw = M < 128;
+  static constexpr bool kRaw16 = M == 64;   // 16-bit counts by tile copies
   static KernelShape raw(bool tma, bool y16 = false) {
-    if constexpr (kRaw16) {
-      if (y16) return {frames_t2<M, false, true, true, true>, C::T, C::SMEM_RAW_TMA};
+    if constexpr (!kRaw) {
+      return grad(tma);
+    } else {
+      if constexpr (kRaw16) {
+        if (y16) return {frames_t2<M, false, true, true, true>, C::T, C::SMEM_RAW_TMA};
+      }
+      return tma ? KernelShape{frames_t2<M, false, true, true>, C::T, C::SMEM_RAW_TMA}
+                 : KernelShape{frames_t2<M, false, true>, C::T, C::SMEM};
     }
-    return tma ? KernelShape{frames_t2<M, false, true, true>, C::T, C::SMEM_RAW_TMA}
-               : KernelShape{frames_t2<M, false, true>, C::T, C::SMEM};
   }
 };
 

@@ -1,0 +1,73 @@
+"""The 512^2, M = 128, 4-peak problem at full size: optimizer iterations
+replayed from one captured CUDA graph, and the FP64 oracle replayed at the
+GPU's own iterates (the trajectory is the GPU's; at each kept iterate the
+loss and gradient must match the oracle's at that same state).
+
+The oracle evaluates a seeded 1/16 of the scan positions (every peak at
+each), as a problem of its own, with the same count data on both sides; the
+full-size context's step records the loss it evaluated, which must equal a
+plain evaluation at the same state."""
+import numpy as np
+import pytest
+
+from helpers import rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+KEEP = (0, 1, 10)
+
+
+def test_graph_trajectory_replayed_on_the_oracle():
+    import oracle
+    from paper_2312_14907_gb300 import mpbp, synth
+    spec = synth.config(3)
+    scan = synth.scan_positions(spec)
+    probe = (synth.probe(spec) * 3.0).astype(np.complex64)
+    p = mpbp.Problem.from_spec(spec, scan)
+    p.set_probe(torch.from_numpy(probe).cuda())
+    yd = torch.from_numpy(synth.template_counts(spec, spec.seed + 80)).cuda()
+    p.set_data(yd)
+    del yd
+    xs = synth.perturbed_state(spec, np.random.default_rng(spec.seed + 81), 0.05)
+    x = [torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda() for a in xs]
+    overlap = (spec.m / spec.step) ** 2 * spec.npeaks
+    state = p.step_init(1.0 / (float(np.abs(probe).max() ** 2) * overlap), w_u=1e-3, w_alpha=1e-3)
+    p.step_capture(*x, state)
+    snaps, f_rec = {}, {}
+    for k in range(max(KEEP) + 1):
+        if k in KEEP:
+            snaps[k] = [t.cpu().numpy().copy() for t in x]
+        p.step_replay()
+        torch.cuda.synchronize()
+        if k in KEEP:
+            f_rec[k] = mpbp.Problem.read_state(state).f_last
+    p.sync_status()
+    st = mpbp.Problem.read_state(state)
+    assert st.n_accept >= 1 and st.k == max(KEEP) + 1
+    # the recorded loss of each kept step is the plain evaluation at its state
+    q_full = mpbp.Problem.from_spec(spec, scan)
+    q_full.set_probe(torch.from_numpy(probe).cuda())
+    q_full.set_data(torch.from_numpy(synth.template_counts(spec, spec.seed + 80)).cuda())
+    for k, a in snaps.items():
+        f = q_full.loss(*[torch.from_numpy(v).cuda() for v in a]).item()
+        assert abs(f - f_rec[k]) <= 1e-9 * abs(f), (k, f, f_rec[k])
+    q_full.close()
+    # the oracle at the GPU's iterates, on a seeded 1/16 of the scan positions
+    js = np.sort(np.random.default_rng(spec.seed + 82).choice(scan.shape[0], scan.shape[0] // 16, replace=False))
+    sub = np.ascontiguousarray(scan[js])
+    y = synth.template_counts(spec, spec.seed + 80, scan_index=js)
+    orc = oracle.OracleProblem.from_spec(spec, sub)
+    q = mpbp.Problem(spec.n1, spec.n2, spec.ncomp, spec.npeaks, spec.m, sub, spec.G, spec.phase_scale)
+    q.set_probe(torch.from_numpy(probe).cuda())
+    q.set_data(torch.from_numpy(y).cuda())
+    for k, a in snaps.items():
+        got = [t.cpu().numpy() for t in q.loss_grad(*[torch.from_numpy(v).cuda() for v in a])]
+        f, gr, gu, ga = orc.loss_grad(*a, probe, y)
+        assert abs(got[0][0] - f) <= 1e-5 * abs(f), (k, got[0][0], f)
+        assert rel_l2(got[1], gr) <= 1e-4, (k, rel_l2(got[1], gr))
+        for c in range(3):
+            if np.abs(gu[c]).max() > 0:
+                assert rel_l2(got[2][c], gu[c]) <= 1e-4, (k, c)
+        assert rel_l2(got[3], ga) <= 1e-4, k
+    q.sync_status()
