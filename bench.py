@@ -229,8 +229,8 @@ def event_pairs(torch, n):
 
 
 def setup_problem(torch, mpbp, k):
-    """Context, data and starting state of workload k, with the lagged-Armijo
-    optimizer state (first step ~ 1 / (max|P|^2 x frames covering a pixel))."""
+    """Context, data and starting state of workload k, and the lagged-Armijo
+    first step length."""
     spec = synth.config(k)
     scan = synth.scan_positions(spec)
     prob = mpbp.Problem.from_spec(spec, scan)
@@ -239,8 +239,11 @@ def setup_problem(torch, mpbp, k):
     prob.set_data(yd)
     rho0, u0, a0 = synth.init_state(spec)
     x = [torch.from_numpy(a.astype(np.float32)).cuda() for a in (rho0, u0, a0)]
+    # first step length: the inverse of the Gauss-Newton curvature bound of a
+    # pixel's density, M^2 (the unnormalised DFT, Parseval) x max|P|^2 x the
+    # frames of all peaks that cover a pixel
     overlap = (spec.m / spec.step) ** 2 * spec.npeaks
-    t0 = 1.0 / (float(np.abs(probe).max() ** 2) * overlap)
+    t0 = 1.0 / (spec.m ** 2 * float(np.abs(probe).max() ** 2) * overlap)
     return spec, scan, prob, probe, yd, x, t0
 
 
@@ -867,7 +870,7 @@ def run_drive(args):
             prob.project_displacement(ud, mask)
     if args.drive_steps:
         overlap = (spec.m / spec.step) ** 2 * spec.npeaks
-        t0 = 1.0 / (float(np.abs(probe).max() ** 2) * overlap)
+        t0 = 1.0 / (spec.m ** 2 * float(np.abs(probe).max() ** 2) * overlap)
         state = prob.step_init(t0, w_rho=1.0, w_u=1e-3, w_alpha=1e-3)
         for _ in range(args.drive_steps):
             prob.step(*x, state)

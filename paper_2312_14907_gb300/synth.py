@@ -261,8 +261,8 @@ def template_counts(spec, seed, scan_index=None):
         tmpl[d] = t
     level = rng.uniform(0.2, 1.5, (spec.npeaks, spec.nscan)).astype(np.float32)
     if scan_index is not None:
-        level = level[:, np.asarray(scan_index)]
-    return np.rint(level[:, :, None, None] * tmpl[:, None, :, :]).astype(np.float32)
+        level = np.ascontiguousarray(level[:, np.asarray(scan_index)])
+    return np.ascontiguousarray(np.rint(level[:, :, None, None] * tmpl[:, None, :, :]).astype(np.float32))
 
 
 def perturbed_state(spec, rng, scale=0.05):

@@ -32,7 +32,10 @@ def test_graph_trajectory_replayed_on_the_oracle():
     xs = synth.perturbed_state(spec, np.random.default_rng(spec.seed + 81), 0.05)
     x = [torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda() for a in xs]
     overlap = (spec.m / spec.step) ** 2 * spec.npeaks
-    state = p.step_init(1.0 / (float(np.abs(probe).max() ** 2) * overlap), w_u=1e-3, w_alpha=1e-3)
+    # first step: the inverse Gauss-Newton curvature bound of a density pixel
+    # (M^2 max|P|^2 x the frames covering it)
+    state = p.step_init(1.0 / (spec.m ** 2 * float(np.abs(probe).max() ** 2) * overlap), w_u=1e-3,
+                        w_alpha=1e-3)
     p.step_capture(*x, state)
     snaps, f_rec = {}, {}
     for k in range(max(KEEP) + 1):
