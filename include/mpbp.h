@@ -440,13 +440,17 @@ mpbp_status mpbp_set_schedule(mpbp_ctx *ctx, int32_t blocks_per_sm);
  * wait of that kernel is reported by mpbp_sync_status as MPBP_ERR_TIMEOUT. */
 mpbp_status mpbp_set_precision(mpbp_ctx *ctx, int32_t mode);
 
-/* Test hook for the timeout path (on != 0): the FFT gradient kernels' tile-copy
- * barriers are told to expect 16 bytes more than the copies deliver, so each
- * block's bounded wait (0.2 s) runs out; the kernel records the event and
- * leaves with no copy in flight, and the next mpbp_sync_status returns
- * MPBP_ERR_TIMEOUT.  Results of calls made while it is on are meaningless.
- * No effect on contexts whose frame kernels use cp.async copies (odd n2,
- * M <= 16) or tensor cores.  Off by default. */
+/* Test hook for the timeout paths (on != 0): every bounded wait on the GPU
+ * is made to run out without a fault.  The FFT gradient kernels' tile-copy
+ * barriers are told to expect 16 bytes more than the copies deliver (each
+ * block's wait, 0.2 s, runs out and the block leaves with no copy in flight);
+ * the tensor-core kernel issues no MMA and no completion signal (its 0.2 s
+ * wait runs out; no MMA is in flight when it frees its tensor memory); block
+ * 0 of the phase unwrapper (mpbp_unwrap_phases, mpbp_project_displacement)
+ * never arrives at a grid barrier (the others' 0.1 s waits run out).  The
+ * next mpbp_sync_status returns MPBP_ERR_TIMEOUT.  Results of calls made
+ * while it is on are meaningless.  No effect on contexts whose frame kernels
+ * use cp.async copies (odd n2, M <= 16).  Off by default. */
 mpbp_status mpbp_set_test_stall(mpbp_ctx *ctx, int32_t on);
 
 /* Turns on (enable != 0) or off the recording of CUDA events around every

@@ -95,7 +95,9 @@ constexpr size_t kTcSplitBytes = 2 * 128 * 128 * 2;   // W hi + lo, FP16
 void tc_split_dft64(uint32_t* out);
 // Prepares the kernel on the current device: shared memory, occupancy.
 bool tc_prepare(int* blocks_per_sm, int* smem_bytes);
-// wsplit: device copy of tc_split_dft64's table (16-byte aligned)
-cudaError_t tc_launch(const FrameArgs& a, const void* wsplit, int grid, cudaStream_t s);
+// wsplit: device copy of tc_split_dft64's table (16-byte aligned).
+// test_stall: no MMA is issued and none is committed, so the bounded wait for
+// its completion runs out (test of the timeout path; results meaningless).
+cudaError_t tc_launch(const FrameArgs& a, const void* wsplit, int grid, cudaStream_t s, bool test_stall = false);
 
 }  // namespace mpbp

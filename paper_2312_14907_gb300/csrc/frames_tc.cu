@@ -246,12 +246,12 @@ MPBP_DI void fetch_at(const FrameArgs& p, const TcGroup& G, const FrameRef& r) {
 
 // D = Wh Xh + Wh Xl + Wl Xh from the group's operand tiles, then wait
 // (bounded) until the accumulator holds it
-MPBP_DI void tc_pass(TcGroup& G, int* err) {
+MPBP_DI void tc_pass(TcGroup& G, int* err, bool stall) {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // operand stores -> tensor core
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   G.ok = group_bar_and(G.id, G.ok);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (G.t == 0 && G.ok) {
+  if (G.t == 0 && G.ok && !stall) {
     const uint32_t bh = smem_u32(G.bh), bl = smem_u32(G.bl);
 #pragma unroll
     for (int prod = 0; prod < 3; ++prod) {
@@ -286,7 +286,9 @@ MPBP_DI void tc_wait(TcGroup& G, int* err) {
 
 }  // namespace
 
-__global__ void __launch_bounds__(TC_THREADS, 1) frames_tc64(const FrameArgs p, const uint32_t* __restrict__ wsplit) {
+// stall != 0: no MMA is issued (test of the bounded completion waits)
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    frames_tc64(const FrameArgs p, const uint32_t* __restrict__ wsplit, int stall) {
   extern __shared__ __align__(16) unsigned char smem_tc[];
   __shared__ uint32_t taddr_holder;
   __shared__ __align__(8) uint64_t mbar[NGROUPS];
@@ -390,7 +392,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) frames_tc64(const FrameArgs p, 
         split_store8(G.bh, G.bl, rq, 64 + 32 * po + 8 * c, cim + 8 * c, s);
       }
     }
-    tc_pass(G, p.err);   // [(q0, po)][k1] = 2^e1 F_0 psi
+    tc_pass(G, p.err, stall);   // [(q0, po)][k1] = 2^e1 F_0 psi
     if (has_next) fetch_patch(p, G, nxt);   // every thread is past its patch reads
     tc_wait(G, p.err);
 
@@ -398,7 +400,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) frames_tc64(const FrameArgs p, 
     if (G.ok) tmem_row64(dlane, d);
 #pragma unroll
     for (int c = 0; c < 8; ++c) split_store8(G.bh, G.bl, rq, 64 * po + 8 * c, d + 8 * c, pow2f(-6));
-    tc_pass(G, p.err);   // [(q1, po)][q0] = 2^(e1 - 6) Psi
+    tc_pass(G, p.err, stall);   // [(q1, po)][q0] = 2^(e1 - 6) Psi
     tc_wait(G, p.err);
 
     // A4: row q1 = rq of Psi; after the pairing this thread has q0 = 32 po + j
@@ -435,14 +437,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) frames_tc64(const FrameArgs p, 
         split_store8(G.bh, G.bl, rq, 64 + 32 * po + 8 * c, cim + 8 * c, s);
       }
     }
-    tc_pass(G, p.err);   // [(k0, po)][q1] = 2^e3 F_0 conj(chi)
+    tc_pass(G, p.err, stall);   // [(k0, po)][q1] = 2^e3 F_0 conj(chi)
     if (has_next) fetch_at(p, G, nxt);   // every thread is past its sqrt(y) reads
     tc_wait(G, p.err);
 
     if (G.ok) tmem_row64(dlane, d);
 #pragma unroll
     for (int c = 0; c < 8; ++c) split_store8(G.bh, G.bl, rq, 64 * po + 8 * c, d + 8 * c, pow2f(-6));
-    tc_pass(G, p.err);   // [(k1, po)][k0] = 2^(e3 - 6) Z
+    tc_pass(G, p.err, stall);   // [(k1, po)][k0] = 2^(e3 - 6) Z
     // the probe values of the scatter load while the pass runs
     cf pv[32];
 #pragma unroll
@@ -514,8 +516,8 @@ bool tc_prepare(int* blocks_per_sm, int* smem_bytes) {
   return *blocks_per_sm > 0;
 }
 
-cudaError_t tc_launch(const FrameArgs& a, const void* wsplit, int grid, cudaStream_t s) {
-  frames_tc64<<<grid, TC_THREADS, TC_SMEM, s>>>(a, static_cast<const uint32_t*>(wsplit));
+cudaError_t tc_launch(const FrameArgs& a, const void* wsplit, int grid, cudaStream_t s, bool test_stall) {
+  frames_tc64<<<grid, TC_THREADS, TC_SMEM, s>>>(a, static_cast<const uint32_t*>(wsplit), test_stall ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -202,7 +202,7 @@ int frames_grid_fft(const mpbp_ctx* c, long long nframes) {
 
 // the gradient-mode frame kernel of the context's precision
 cudaError_t launch_frames(const mpbp_ctx* c, const FrameArgs& fa, int grid, cudaStream_t s) {
-  if (c->precision == MPBP_PRECISION_TC_SPLIT16) return tc_launch(fa, c->tc_w, grid, s);
+  if (c->precision == MPBP_PRECISION_TC_SPLIT16) return tc_launch(fa, c->tc_w, grid, s, c->test_tx_extra != 0);
   if (!c->tile_grad || fa.O != c->O) return frames_launch(c->M, fa, grid, false, s, nullptr, c->fft_schedule);
   TmaMap tm = c->tm_grad;
   tm.tx_extra = c->test_tx_extra;
@@ -1283,6 +1283,7 @@ mpbp_status enqueue_unwrap(mpbp_ctx* c, const float* wrapped, const float* mask,
   a.wrapped = wrapped;
   a.mask = mask;
   a.out = out;
+  a.test_stall = c->test_tx_extra != 0 ? 1 : 0;
   MPBP_CUDA(c, cudaMemsetAsync(a.flags, 0, sizeof(int) * 3, s));
   MPBP_CUDA(c, cudaMemsetAsync(a.bar_count, 0, sizeof(unsigned) * 2, s));
   MPBP_CUDA(c, unwrap_launch(a, c->uw_grid, s));

@@ -48,6 +48,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // Sense by generation: the last block to arrive resets the count and bumps
 // the generation; the others wait (bounded) for the generation to change.
 // Returns false (in every thread of the block) if this block's wait ran out.
+// With a.test_stall block 0 leaves without arriving, so the others' waits
+// run out.
 __device__ bool grid_sync(UnwrapArgs& a) {
   __shared__ int ok_s;
   __syncthreads();
@@ -56,7 +58,10 @@ __device__ bool grid_sync(UnwrapArgs& a) {
     volatile unsigned* genp = a.bar_gen;
     const unsigned g = *genp;
     __threadfence();
-    if (atomicAdd(a.bar_count, 1u) == gridDim.x - 1) {
+    if (a.test_stall && blockIdx.x == 0) {
+      atomicOr(a.err, kErrTimeout);
+      ok = 0;
+    } else if (atomicAdd(a.bar_count, 1u) == gridDim.x - 1) {
       *a.bar_count = 0u;
       __threadfence();
       atomicAdd(a.bar_gen, 1u);

@@ -26,6 +26,8 @@ struct UnwrapArgs {
   long long npix, nodes;
   int n1, n2;
   int max_rounds;
+  int test_stall;         // != 0: block 0 never arrives at a grid barrier (test
+                          // of the bounded waits; the result is meaningless)
 };
 
 struct ProjectArgs {

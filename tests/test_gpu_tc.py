@@ -153,3 +153,25 @@ def test_tc_fullsize_autotune_and_invariants():
     fb = p.loss_grad(*x, frames=rest)[0].item()
     assert abs(fa + fb - f_all) <= 1e-6 * abs(f_all)
     p.sync_status()
+
+
+def test_tc_mma_wait_runs_out_and_reports():
+    """The tensor-core kernel's waits for its MMAs are bounded: with no MMA
+    issued (the test hook), each group's wait gives up after its time limit,
+    the call reports MPBP_ERR_TIMEOUT, and the context then computes the
+    oracle's result again."""
+    import time
+    from paper_2312_14907_gb300 import mpbp
+    spec, scan = custom_spec(128, 64, 5, 16, npeaks=3, offset=-8)
+    case = Case(spec, scan=scan, state="perturbed")
+    p, x = _gpu(case)
+    p.set_test_stall(True)
+    t0 = time.time()
+    p.loss_grad(*x)
+    with pytest.raises(mpbp.MPBPError) as e:
+        p.sync_status()
+    assert e.value.status == 5, e.value           # MPBP_ERR_TIMEOUT
+    assert time.time() - t0 < 20.0
+    p.set_test_stall(False)
+    _check(case, p.loss_grad(*x))
+    p.sync_status()

@@ -127,3 +127,32 @@ def test_projector_matches_oracle_and_removes_lattice_jumps():
     again = p.project_displacement(torch.from_numpy(got).cuda(), md).cpu().numpy()
     assert np.abs(again - got).max() <= 1e-4
     p.sync_status()
+
+
+def test_unwrap_barrier_wait_runs_out_and_reports():
+    """The unwrapper's grid barriers are bounded: with block 0 never arriving
+    (the test hook), the other blocks give up after their time limit, the call
+    reports MPBP_ERR_TIMEOUT, and the context then unwraps as the oracle
+    does again."""
+    import time
+    import oracle
+    from paper_2312_14907_gb300 import mpbp
+    rng = np.random.default_rng(5)
+    p, spec = _problem(96, 2)
+    n = spec.n1
+    phi = np.stack([_smooth(rng, n, n) for _ in range(spec.npeaks)])
+    wrapped = torch.from_numpy(_wrap(phi).astype(np.float32)).cuda()
+    p.set_test_stall(True)
+    t0 = time.time()
+    p.unwrap_phases(wrapped)
+    with pytest.raises(mpbp.MPBPError) as e:
+        p.sync_status()
+    assert e.value.status == 5, e.value           # MPBP_ERR_TIMEOUT
+    assert time.time() - t0 < 20.0
+    p.set_test_stall(False)
+    got = p.unwrap_phases(wrapped).cpu().numpy()
+    p.sync_status()
+    w = _wrap(phi).astype(np.float32)
+    for d in range(spec.npeaks):
+        ref = oracle.unwrap2d(w[d].astype(np.float64), None)
+        assert np.abs(got[d] - ref).max() <= 1e-3, (d, np.abs(got[d] - ref).max())
