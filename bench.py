@@ -504,12 +504,61 @@ def run_gpu(args):
 
     # ---- the 512^2 / M = 128 / 4-peak problem: 200 graph-captured iterations
     line["workload_512_iterations"] = iterations_block(torch, mpbp, args, flush, stream, rank)
+    # ---- the 16 problems of uneven sizes in one batched call
+    line["batched_16"] = batched_block(torch, mpbp, flush, stream)
     # ---- the 256^2 / M = 64 problem: its step, both precision modes, Alg. 1
     line["workload_256"] = secondary_block(torch, mpbp, args, flush, stream, pk)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def batched_block(torch, mpbp, flush, stream, n=5):
+    """The 16 independent problems of uneven sizes (objects 128..512, frame
+    sides 32/64/128, 3 or 4 peaks, 90,844 frames) evaluated by one
+    mpbp_loss_grad_batched call under each batch schedule (mode 0: one
+    persistent launch for every frame side; 1: one per side; 2: as 1, M = 128
+    problems on their own; 3: one launch per problem), CUDA events, L2
+    flushed between calls; then the schedule mpbp_autotune_batched picks."""
+    specs = synth.batched_configs()
+    probs, states = [], []
+    for spec in specs:
+        scan = synth.scan_positions(spec)
+        pr = mpbp.Problem.from_spec(spec, scan)
+        probe, yd = make_inputs(spec, scan, pr, torch)
+        pr.set_probe(torch.from_numpy(probe).cuda())
+        pr.set_data(yd)
+        del yd
+        probs.append(pr)
+        states.append([torch.from_numpy(a.astype(np.float32)).cuda() for a in synth.init_state(spec)])
+    nframes = sum(sp.nframes for sp in specs)
+    outs = mpbp.loss_grad_batched(probs, states)
+    res = {"problems": len(specs), "frames": nframes, "modes": {}}
+    for mode in (0, 1, 2, 3):
+        probs[0].set_batch_schedule(mode, 0)
+        for _ in range(2):
+            mpbp.loss_grad_batched(probs, states, outs)
+        evs = event_pairs(torch, n)
+        torch.cuda.synchronize()
+        for k in range(n):
+            flush.zero_()
+            evs[k][0].record(stream)
+            mpbp.loss_grad_batched(probs, states, outs)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in evs) / n
+        res["modes"][str(mode)] = {"ms_per_eval": ms, "value": nframes / (ms / 1e3), "unit": UNIT}
+    mpbp.autotune_batched(probs, states)
+    torch.cuda.synchronize()
+    for pr in probs:
+        pr.sync_status()
+    res["what"] = ("one mpbp_loss_grad_batched call over all 16 problems; mode 0: one persistent launch for "
+                   "every frame side, 1: one per side, 2: as 1 with M = 128 problems on their own, 3: one "
+                   "launch per problem (the single-problem kernels)")
+    for pr in probs:
+        pr.close()
+    return res
 
 
 SNAPSHOTS = (0, 1, 10, 199)   # iterates whose states are replayed on the oracle
