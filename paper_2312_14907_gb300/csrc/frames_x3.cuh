@@ -133,6 +133,29 @@ MPBP_DI void x3_finish_twiddles(const X3TwRaw& raw, X3Tw& t) {
   }
 }
 
+// TMA, in two parts on one mbarrier phase: the sqrt(y) tile of frame fr as
+// soon as the residual has read the staging buffer (thread 0 announces both
+// copies' bytes), the patch tile once the exchanges have freed theirs
+MPBP_DI void x3_fetch_amp_tma(const FrameArgs& p, const X3Roles& r, const FrameRef& fr, float* abuf,
+                              const BulkState& bs, const TmaMap* tm) {
+  constexpr int M = X3Cfg::M;
+  if (r.tid == 0) {
+    constexpr uint32_t kPatch = M * X3Cfg::PW * (uint32_t)sizeof(cf);
+    constexpr uint32_t kAmp = M * M * (uint32_t)sizeof(float);
+    fence_async_smem();
+    mbar_arrive_tx(bs.bar, (fr.valid ? kPatch + kAmp : 0u) + tm->tx_extra);
+    if (fr.valid) bulk_load(smem_addr(abuf), p.aT + (long long)fr.f * M * M, kAmp, bs.bar);
+  }
+}
+
+MPBP_DI void x3_fetch_patch_tma(const X3Roles& r, const FrameRef& fr, cf* buf, const BulkState& bs,
+                                const TmaMap* tm) {
+  if (r.tid == 0 && fr.valid) {
+    fence_async_smem();
+    tile_load_3d(smem_addr(buf), &tm->map, fr.s.y - (fr.s.y & 1), fr.s.x, fr.mpk, bs.bar);
+  }
+}
+
 // inputs of frame fr: the patch tile and sqrt(y) [q1][q0] (64 KB); TMA: one
 // thread issues a tile load and one bulk copy on the block's mbarrier, after
 // the barrier that freed the buffers; else cp.async by every thread
@@ -172,7 +195,7 @@ MPBP_DI void x3_fetch(const FrameArgs& p, const X3Roles& r, const FrameRef& fr, 
 // One frame's loss and gradient (inputs in flight); fetches the next frame's
 // inputs as soon as their buffers are free.  TMA: a wait that runs out clears
 // bs.ok and returns at once.
-template <bool TMA, bool LOSS, typename AddLoss>
+template <bool TMA, bool LOSS, bool BG, typename AddLoss>
 MPBP_DI void x3_frame(const FrameArgs& p, const X3Roles& r, const FrameRef& cur, const FrameRef& nxt,
                       AddLoss&& add_loss, BulkState& bs, const TmaMap* tm, cf* buf, float* abuf, uint32_t tp,
                       uint32_t tt) {
@@ -278,14 +301,16 @@ MPBP_DI void x3_frame(const FrameArgs& p, const X3Roles& r, const FrameRef& cur,
       v[mr * 16 + mm] = t16[ct::brev<16>(mm)];   // Psi(q0, m' + 8 m'') at v[16 m_r + m'']
     });
   });
-  const float* bg = p.bgT ? p.bgT + (long long)cur.f * M * M : nullptr;
   float fl = 0.0f;
+  // BG: the background b of Eq. 2 (a kernel of its own, so that the common
+  // case carries no per-value test)
+  const float* bg = BG ? p.bgT + (long long)cur.f * M * M : nullptr;
   sfor<0, 2>([&](auto m_) {
     constexpr int mr = decltype(m_)::value;
     sfor<0, 16>([&](auto i_) {
       constexpr int mm = decltype(i_)::value;
       const int q1 = r.mt + 4 * mr + 8 * mm;
-      const float bv = bg ? bg[q1 * M + r.q0] : 0.0f;
+      const float bv = BG ? bg[q1 * M + r.q0] : 0.0f;
       v[mr * 16 + mm] = residual(v[mr * 16 + mm], abuf[q1 * M + r.q0], bv, fl);
     });
   });
@@ -316,6 +341,9 @@ MPBP_DI void x3_frame(const FrameArgs& p, const X3Roles& r, const FrameRef& cur,
       buf[x3_b(r.mt + 4 * mr, r.q0, kr)] = v[mr * 16 + kr];
     });
   });
+  // the residual's reads of the sqrt(y) buffer are behind the barrier above:
+  // the next frame's tile can land there now
+  if constexpr (TMA) x3_fetch_amp_tma(p, r, nxt, abuf, bs, tm);
   X3TwRaw twr2;
   x3_issue_twiddles(tt, twr2);   // in flight across the barrier
   __syncthreads();
@@ -364,8 +392,12 @@ MPBP_DI void x3_frame(const FrameArgs& p, const X3Roles& r, const FrameRef& cur,
     v[k] = buf[x3_a(r.h, k, r.c)];
   });
   __syncthreads();   // both buffers are free
-  x3_fetch<TMA>(p, r, nxt, buf, abuf, bs, tm);
-  if constexpr (!TMA) cp_async_commit();
+  if constexpr (TMA) {
+    x3_fetch_patch_tma(r, nxt, buf, bs, tm);
+  } else {
+    x3_fetch<false>(p, r, nxt, buf, abuf, bs, tm);
+    cp_async_commit();
+  }
   fft_line<32>(v);   // Z(4 n + h, c) in slot brev(n)
 
   const int col = cur.s.y + r.c;
@@ -394,13 +426,13 @@ MPBP_DI void x3_frame(const FrameArgs& p, const X3Roles& r, const FrameRef& cur,
   }
 }
 
-// loss and gradient (LOSS: loss only): one frame per block, frames
-// round-robin over a persistent grid; TMA: inputs by tile and bulk copies
+// loss and gradient (LOSS: loss only; BG: with the background of Eq. 2): one
+// frame per block, frames round-robin over a persistent grid; TMA: inputs by tile and bulk copies
 // (tm: the objects' tensor map), else by cp.async.  The probe values of a
 // thread sit in tensor memory and are reloaded when the frame's probe
 // changes: once per block for one probe, per peak for one probe per peak,
 // per frame for probes shifted per scan position.
-template <bool TMA, bool LOSS = false>
+template <bool TMA, bool LOSS = false, bool BG = false>
 __global__ void __launch_bounds__(X3Cfg::T, 1) frames_x3(const FrameArgs p, const __grid_constant__ TmaMap tm) {
   using C = X3Cfg;
   constexpr int M = C::M;
@@ -442,7 +474,7 @@ __global__ void __launch_bounds__(X3Cfg::T, 1) frames_x3(const FrameArgs p, cons
         tp_src = P;
       }
     }
-    x3_frame<TMA, LOSS>(p, r, cur, nxt, [&](float fl) { lsum += (double)fl; }, bs, &tm, buf, abuf, tp, tt);
+    x3_frame<TMA, LOSS, BG>(p, r, cur, nxt, [&](float fl) { lsum += (double)fl; }, bs, &tm, buf, abuf, tp, tt);
     if (TMA && !bs.ok) {
       if (threadIdx.x == 0) atomicOr(p.err, kErrTimeout);
       break;
