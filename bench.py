@@ -687,7 +687,44 @@ def secondary_block(torch, mpbp, args, flush, stream, pk):
         "tensor_flops_per_frame": tc_flops,
         "tensor_peak_tflops": pk["bf16_tflops"], "peak_src": pk["src"] + " (dense bf16 = fp16 rate)"}
     out["alg1"] = alg1_block(torch, prob, spec, x, flush, stream)
+    out["alt_precision_m32"] = tc_m32_block(torch, mpbp, flush, stream, pk)
     out["unfused_torch"] = unfused_comparison(torch, prob, spec, scan, probe, yd, x, flush, stream)
+    prob.close()
+    return out
+
+
+def tc_m32_block(torch, mpbp, flush, stream, pk, n=10):
+    """Frame side 32 in both precision modes: loss and gradient evaluations of
+    the 512^2, 4-peak, 61 x 61-scan problem of the batched set (14,884 frames
+    of 32 x 32), FP32 FFTs against the tensor-core DFTs (four frames per
+    64 x 64 tile), CUDA events, L2 flushed between calls."""
+    spec = synth.batched_configs()[15]
+    scan = synth.scan_positions(spec)
+    prob = mpbp.Problem.from_spec(spec, scan)
+    probe, yd = make_inputs(spec, scan, prob, torch)
+    prob.set_probe(torch.from_numpy(probe).cuda())
+    prob.set_data(yd)
+    del yd
+    xp = synth.perturbed_state(spec, np.random.default_rng(spec.seed + 6), 0.05)
+    x = [torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda() for a in xp]
+    out = {"config": workload_config(spec)}
+    res = {}
+    for name, mode in (("fp32_fft", mpbp.PRECISION_FP32), ("tc_split16", mpbp.PRECISION_TC_SPLIT16)):
+        prob.set_precision(mode)
+        ms, kms = time_evals(torch, prob, x, n, flush, stream)
+        res[name] = [t.cpu().numpy() for t in prob.loss_grad(*x)]
+        out[name] = {"ms_per_eval": ms, "kernel_ms": kms, "value": spec.nframes / (ms / 1e3), "unit": UNIT}
+    tc_flops = 4 * 3 * 2 * 128 * 64 * 128 / 4   # per 32 x 32 frame: a quarter of a 64 x 64 tile's passes
+    out["tc_split16"]["tensor_tflops"] = tc_flops * spec.nframes / (out["tc_split16"]["kernel_ms"] / 1e3) / 1e12
+    out["tc_split16"]["tensor_peak_tflops"] = pk["bf16_tflops"]
+
+    def rel(a, b):
+        a, b = np.asarray(a, np.float64).ravel(), np.asarray(b, np.float64).ravel()
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    a, b = res["tc_split16"], res["fp32_fft"]
+    out["tc_vs_fft"] = {"loss_rel_err": abs(float(a[0][0]) - float(b[0][0])) / abs(float(b[0][0])),
+                        "g_rho_rel_l2": rel(a[1], b[1]), "g_u_rel_l2": rel(a[2], b[2]),
+                        "g_alpha_rel_l2": rel(a[3], b[3])}
     prob.close()
     return out
 

@@ -84,20 +84,23 @@ bool frames_raw16_supported(int m);
 cudaError_t frames_launch_raw(int m, const FrameArgs& a, int grid, cudaStream_t s, const TmaMap* tm = nullptr,
                               bool y16 = false);
 
-// Tensor-core variant of the gradient kernel for m = 64 (frames_tc.cu): the
-// DFT passes as split-FP16 GEMMs on tcgen05.  Two frames in flight per
-// 256-thread block.
+// Tensor-core variant of the gradient kernel for m = 64 and 32 (frames_tc.cu):
+// the DFT passes as split-FP16 GEMMs on tcgen05.  Two 64 x 64 tiles in flight
+// per 256-thread block: one frame each (m = 64) or four 32 x 32 frames each
+// (m = 32, with the block-diagonal pair of 32-point DFT matrices).
 constexpr int kTcThreads = 256;
-constexpr int kTcFramesPerBlock = 2;
+inline int tc_frames_per_block(int m) { return m == 32 ? 8 : 2; }
 constexpr size_t kTcSplitBytes = 2 * 128 * 128 * 2;   // W hi + lo, FP16
 
-// W hi and lo in the kernel's tensor-memory layout (kTcSplitBytes / 4 words, host)
-void tc_split_dft64(uint32_t* out);
+// W hi and lo in the kernel's tensor-memory layout (kTcSplitBytes / 4 words,
+// host): the 64-point DFT (n = 64) or diag(W32, W32) (n = 32)
+void tc_split_dft(uint32_t* out, int n);
 // Prepares the kernel on the current device: shared memory, occupancy.
 bool tc_prepare(int* blocks_per_sm, int* smem_bytes);
-// wsplit: device copy of tc_split_dft64's table (16-byte aligned).
+// wsplit: device copy of tc_split_dft's table for frame side m (16-byte aligned).
 // test_stall: no MMA is issued and none is committed, so the bounded wait for
 // its completion runs out (test of the timeout path; results meaningless).
-cudaError_t tc_launch(const FrameArgs& a, const void* wsplit, int grid, cudaStream_t s, bool test_stall = false);
+cudaError_t tc_launch(int m, const FrameArgs& a, const void* wsplit, int grid, cudaStream_t s,
+                      bool test_stall = false);
 
 }  // namespace mpbp

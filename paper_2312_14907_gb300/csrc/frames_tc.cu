@@ -244,6 +244,53 @@ MPBP_DI void fetch_at(const FrameArgs& p, const TcGroup& G, const FrameRef& r) {
   cp_async_commit();
 }
 
+// ---- four 32 x 32 frames per 64 x 64 tile (frame side 32).  With the
+// block-diagonal pair diag(W32, W32) in place of W64, each pass transforms
+// the tile's four quadrants independently, so frame f = 2 b0 + b1 occupies
+// rows 32 b0 .. and columns 32 b1 .. of the tile (b0: the block of k0 / q0,
+// b1: the block of k1 / q1).  A thread (column or row rq, part po) always
+// touches frame 2 po + (rq >> 5).
+
+// the four frames' object patches into the staging tile
+MPBP_DI void fetch_patch4(const FrameArgs& p, const TcGroup& G, const FrameRef (&r)[4]) {
+#pragma unroll 4
+  for (int i = 0; i < TM * TM / GT; ++i) {
+    const int e = G.t + i * GT;
+    const int k0 = e >> 6, k1 = e & 63;
+    const FrameRef& fr = r[2 * (k0 >> 5) + (k1 >> 5)];
+    const cf* obj = p.O + fr.mpk * p.obj_stride;
+    const int row = fr.s.x + (k0 & 31), col = fr.s.y + (k1 & 31);
+    const bool ok = fr.valid && row >= 0 && row < p.n1 && col >= 0 && col < p.n2;
+    cp_async8(G.patch + patch_idx(k0, k1), ok ? obj + (long long)row * p.n2 + col : obj, ok);
+  }
+  cp_async_commit();
+}
+
+// the four frames' sqrt(y) tiles ([q1][q0], 32 x 32 each) into the staging tile
+MPBP_DI void fetch_at4(const FrameArgs& p, const TcGroup& G, const FrameRef (&r)[4]) {
+#pragma unroll
+  for (int i = 0; i < TM * TM / 4 / GT; ++i) {
+    const int c = G.t + i * GT;   // 16-byte chunk: row q1 = c / 16, q0 = 4 (c % 16)
+    const int q1 = c >> 4, ch = c & 15;
+    const FrameRef& fr = r[2 * (ch >> 3) + (q1 >> 5)];
+    const float* src = p.aT + (long long)fr.f * 32 * 32 + (q1 & 31) * 32 + 4 * (ch & 7);
+    cp_async16z(G.at + q1 * TM + ((ch ^ (q1 & 7)) << 2), src, fr.valid);
+  }
+  cp_async_commit();
+}
+
+// maximum of non-negative floats over the 32 threads of each frame (one
+// barrier; slot sets alternate between the two uses per frame): lanes 0..15
+// and 16..31 of a warp are parts po = 0, 1, warps 0-1 / 2-3 column blocks
+MPBP_DI float group_max4(float v, float* red8, int id, int t) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((t & 15) == 0) red8[(t >> 4) & 7] = v;
+  group_bar(id);
+  const int po = (t >> 4) & 1, wb = (t >> 6) * 2;
+  return fmaxf(red8[wb * 2 + po], red8[(wb + 1) * 2 + po]);
+}
+
 // D = Wh Xh + Wh Xl + Wl Xh from the group's operand tiles, then wait
 // (bounded) until the accumulator holds it
 MPBP_DI void tc_pass(TcGroup& G, int* err, bool stall) {
@@ -286,13 +333,17 @@ MPBP_DI void tc_wait(TcGroup& G, int* err) {
 
 }  // namespace
 
-// stall != 0: no MMA is issued (test of the bounded completion waits)
+// stall != 0: no MMA is issued (test of the bounded completion waits).
+// Q4: frame side 32, four frames per group tile (wsplit: diag(W32, W32)).
+template <bool Q4>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     frames_tc64(const FrameArgs p, const uint32_t* __restrict__ wsplit, int stall) {
+  constexpr int FPG = Q4 ? 4 : 1;     // frames per group tile
+  constexpr int FS = Q4 ? 32 : TM;    // frame side
   extern __shared__ __align__(16) unsigned char smem_tc[];
   __shared__ uint32_t taddr_holder;
   __shared__ __align__(8) uint64_t mbar[NGROUPS];
-  __shared__ float redf[NGROUPS][2][4];
+  __shared__ float redf[NGROUPS][2][8];
   __shared__ double red[TC_THREADS / 32];
   const int tid = threadIdx.x;
   const int gi = tid / GT;
@@ -357,17 +408,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   double lsum = 0.0;
   float d[64], cre[32], cim[32];
 
-  const int stride = NGROUPS * gridDim.x;
-  int it = NGROUPS * blockIdx.x + gi;
-  FrameRef cur = frame_ref(p, it);
+  const int stride = NGROUPS * gridDim.x * FPG;
+  int it = (NGROUPS * blockIdx.x + gi) * FPG;
+  // the group's frames; this thread's one (fme) and its column within it
+  FrameRef curs[FPG];
+  for (int f = 0; f < FPG; ++f) curs[f] = frame_ref(p, it + f);
+  const int fme = Q4 ? 2 * po + (rq >> 5) : 0;
+  const int lc = Q4 ? (rq & 31) : rq;
   if (it < p.nframes) {
-    fetch_patch(p, G, cur);
-    fetch_at(p, G, cur);
+    if constexpr (Q4) {
+      fetch_patch4(p, G, curs);
+      fetch_at4(p, G, curs);
+    } else {
+      fetch_patch(p, G, curs[0]);
+      fetch_at(p, G, curs[0]);
+    }
   }
   for (; it < p.nframes && G.ok; it += stride) {
-    const FrameRef nxt = frame_ref(p, it + stride);
+    FrameRef nxts[FPG];
+    for (int f = 0; f < FPG; ++f) nxts[f] = frame_ref(p, it + stride + f);
     const bool has_next = it + stride < p.nframes;
-    const cf* P = frame_probe(p, cur, TM * TM);
+    const FrameRef cur = curs[fme];
+    const cf* P = frame_probe(p, cur, FS * FS);
     cp_async_wait_all();
     group_bar(G.id);
 
@@ -379,12 +441,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         const int k0 = 32 * po + j;
-        const cf v = cmul(ldg_cf(P + k0 * TM + rq), G.patch[patch_idx(k0, rq)]);
+        const cf v = cmul(ldg_cf(P + (Q4 ? j : k0) * FS + lc), G.patch[patch_idx(k0, rq)]);
         cre[j] = v.x;
         cim[j] = v.y;
         mx = abs_max(abs_max(mx, v.x), v.y);
       }
-      e1 = scale_exp(group_max(mx, redf[gi][0], G.id));
+      e1 = scale_exp(Q4 ? group_max4(mx, redf[gi][0], G.id, t) : group_max(mx, redf[gi][0], G.id));
       const float s = pow2f(e1);
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -393,7 +455,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
     }
     tc_pass(G, p.err, stall);   // [(q0, po)][k1] = 2^e1 F_0 psi
-    if (has_next) fetch_patch(p, G, nxt);   // every thread is past its patch reads
+    if (has_next) {   // every thread is past its patch reads
+      if constexpr (Q4) fetch_patch4(p, G, nxts);
+      else fetch_patch(p, G, nxts[0]);
+    }
     tc_wait(G, p.err);
 
     // operand row q0 = rq, block po: 2^-6 of the first pass (stays below 2^15)
@@ -409,7 +474,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (G.ok) tmem_row64(dlane, d);
       pair_columns(d, po, cre, cim);
       const float un = pow2f(6 - e1);
-      const float* bg = p.bgT ? p.bgT + (long long)cur.f * TM * TM + rq * TM + 32 * po : nullptr;
+      const float* bg = p.bgT ? (Q4 ? p.bgT + (long long)cur.f * FS * FS + lc * FS
+                                    : p.bgT + (long long)cur.f * TM * TM + rq * TM + 32 * po)
+                              : nullptr;
       float av[32];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {   // q0 = 32 po + 4i .. + 3
@@ -429,7 +496,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         mx = abs_max(abs_max(mx, z.x), z.y);
       }
       if (cur.valid) lsum += 0.5 * (double)fl;
-      e3 = scale_exp(group_max(mx, redf[gi][1], G.id));
+      e3 = scale_exp(Q4 ? group_max4(mx, redf[gi][1], G.id, t) : group_max(mx, redf[gi][1], G.id));
       const float s = pow2f(e3);
 #pragma unroll
       for (int c = 0; c < 4; ++c) {   // operand row q1: conj(chi) at q0
@@ -438,7 +505,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
     }
     tc_pass(G, p.err, stall);   // [(k0, po)][q1] = 2^e3 F_0 conj(chi)
-    if (has_next) fetch_at(p, G, nxt);   // every thread is past its sqrt(y) reads
+    if (has_next) {   // every thread is past its sqrt(y) reads
+      if constexpr (Q4) fetch_at4(p, G, nxts);
+      else fetch_at(p, G, nxts[0]);
+    }
     tc_wait(G, p.err);
 
     if (G.ok) tmem_row64(dlane, d);
@@ -448,7 +518,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // the probe values of the scatter load while the pass runs
     cf pv[32];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) pv[j] = ldg_cf(P + (32 * po + j) * TM + rq);
+    for (int j = 0; j < 32; ++j) pv[j] = ldg_cf(P + (Q4 ? j : 32 * po + j) * FS + lc);
     tc_wait(G, p.err);
 
     // A6 + A7: Z(k0, k1) for k1 = rq, k0 = 32 po + j
@@ -456,17 +526,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       tmem_row64(dlane, d);
       pair_columns(d, po, cre, cim);
       const float uz = pow2f(6 - e3);
-      const int col = cur.s.y + rq;
+      const int col = cur.s.y + lc;
       cf* acc = p.acc + cur.mpk * p.obj_stride;
       if (cur.valid && col >= 0 && col < p.n2) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          const int r = cur.s.x + 32 * po + j;
+          const int r = cur.s.x + (Q4 ? 0 : 32 * po) + j;
           if (r >= 0 && r < p.n1) red_add_v2(acc + (long long)r * p.n2 + col, cmul(pv[j], cf{cre[j] * uz, cim[j] * uz}));
         }
       }
     }
-    cur = nxt;
+    for (int f = 0; f < FPG; ++f) curs[f] = nxts[f];
   }
   cp_async_wait_all();   // copies of a frame this group no longer processes
 
@@ -480,8 +550,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
 // W hi and lo as the A operand in tensor memory: [2][128 rows][64 columns],
 // column c of a row holding elements 2c (low half) and 2c + 1 (high half);
-// row r is transform row (r mod 16) + 16 (r div 32), part (r div 16) mod 2
-void tc_split_dft64(uint32_t* out) {
+// row r is transform row (r mod 16) + 16 (r div 32), part (r div 16) mod 2.
+// n = 64: the 64-point DFT; n = 32: the block-diagonal pair diag(W32, W32)
+// (rows and columns of the two 32-blocks, zero between them).
+void tc_split_dft(uint32_t* out, int n) {
   const double two_pi = 6.283185307179586476925286766559;
   for (int r = 0; r < TK; ++r) {
     const int q = (r & 15) | ((r >> 5) << 4), po = (r >> 4) & 1;
@@ -489,9 +561,12 @@ void tc_split_dft64(uint32_t* out) {
       uint16_t hv[2], lv[2];
       for (int e = 0; e < 2; ++e) {
         const int K = 2 * c + e, pi = K >> 6, k = K & 63;
-        const double th = two_pi * (double)((q * k) % TM) / TM;
+        const bool same_block = n == TM || (q >> 5) == (k >> 5);
+        const int qq = q % n, kk = k % n;
+        const double th = two_pi * (double)((qq * kk) % n) / n;
         const double cs = std::cos(th), sn = std::sin(th);
-        const double v = po == 0 ? (pi == 0 ? cs : sn) : (pi == 0 ? -sn : cs);
+        const double v0 = po == 0 ? (pi == 0 ? cs : sn) : (pi == 0 ? -sn : cs);
+        const double v = same_block ? v0 : 0.0;
         const __half h = __double2half(v);
         const __half l = __double2half(v - (double)__half2float(h));
         hv[e] = __half_as_ushort(h);
@@ -505,19 +580,24 @@ void tc_split_dft64(uint32_t* out) {
 
 bool tc_prepare(int* blocks_per_sm, int* smem_bytes) {
   *smem_bytes = TC_SMEM;
-  if (cudaFuncSetAttribute(frames_tc64, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) != cudaSuccess ||
-      cudaFuncSetAttribute(frames_tc64, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           cudaSharedmemCarveoutMaxShared) != cudaSuccess)
-    return false;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, frames_tc64, TC_THREADS, TC_SMEM) != cudaSuccess)
+  for (auto kern : {frames_tc64<false>, frames_tc64<true>})
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+      return false;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, frames_tc64<false>, TC_THREADS, TC_SMEM) !=
+      cudaSuccess)
     return false;
   // the tensor memory of every resident block must fit the SM's 512 columns
   if (*blocks_per_sm * TMEM_COLS > 512) *blocks_per_sm = 512 / TMEM_COLS;
   return *blocks_per_sm > 0;
 }
 
-cudaError_t tc_launch(const FrameArgs& a, const void* wsplit, int grid, cudaStream_t s, bool test_stall) {
-  frames_tc64<<<grid, TC_THREADS, TC_SMEM, s>>>(a, static_cast<const uint32_t*>(wsplit), test_stall ? 1 : 0);
+cudaError_t tc_launch(int m, const FrameArgs& a, const void* wsplit, int grid, cudaStream_t s, bool test_stall) {
+  if (m == 32)
+    frames_tc64<true><<<grid, TC_THREADS, TC_SMEM, s>>>(a, static_cast<const uint32_t*>(wsplit), test_stall ? 1 : 0);
+  else
+    frames_tc64<false><<<grid, TC_THREADS, TC_SMEM, s>>>(a, static_cast<const uint32_t*>(wsplit), test_stall ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -202,7 +202,8 @@ int frames_grid_fft(const mpbp_ctx* c, long long nframes) {
 
 // the gradient-mode frame kernel of the context's precision
 cudaError_t launch_frames(const mpbp_ctx* c, const FrameArgs& fa, int grid, cudaStream_t s) {
-  if (c->precision == MPBP_PRECISION_TC_SPLIT16) return tc_launch(fa, c->tc_w, grid, s, c->test_tx_extra != 0);
+  if (c->precision == MPBP_PRECISION_TC_SPLIT16)
+    return tc_launch(c->M, fa, c->tc_w, grid, s, c->test_tx_extra != 0);
   if (!c->tile_grad || fa.O != c->O) return frames_launch(c->M, fa, grid, false, s, nullptr, c->fft_schedule);
   TmaMap tm = c->tm_grad;
   tm.tx_extra = c->test_tx_extra;
@@ -596,12 +597,12 @@ mpbp_status mpbp_set_precision(mpbp_ctx* c, int32_t mode) {
   if (mode == MPBP_PRECISION_FP32) {
     c->fk = c->fk_fft;
   } else {
-    if (c->M != 64) return fail(c, MPBP_ERR_UNSUPPORTED, "tensor-core DFTs need frame side 64");
+    if (c->M != 64 && c->M != 32) return fail(c, MPBP_ERR_UNSUPPORTED, "tensor-core DFTs need frame side 32 or 64");
     int bps = 0, smem = 0;
     if (!tc_prepare(&bps, &smem)) return fail(c, MPBP_ERR_CUDA, "tensor-core kernel cannot run here");
     if (!c->tc_w) {
       std::vector<uint32_t> w(kTcSplitBytes / 4);
-      tc_split_dft64(w.data());
+      tc_split_dft(w.data(), c->M);
       MPBP_CUDA(c, cudaDeviceSynchronize());
       void* d = nullptr;
       if (cudaMalloc(&d, kTcSplitBytes) != cudaSuccess) {
@@ -611,7 +612,7 @@ mpbp_status mpbp_set_precision(mpbp_ctx* c, int32_t mode) {
       c->tc_w = d;
       MPBP_CUDA(c, cudaMemcpy(d, w.data(), kTcSplitBytes, cudaMemcpyHostToDevice));
     }
-    c->fk = FrameKernelInfo{kTcThreads, smem, kTcFramesPerBlock, bps};
+    c->fk = FrameKernelInfo{kTcThreads, smem, tc_frames_per_block(c->M), bps};
   }
   c->precision = mode;
   c->batch_key.clear();

@@ -1,4 +1,4 @@
-"""Tensor-core DFT precision mode (frame side 64) vs the FP64 oracle.
+"""Tensor-core DFT precision mode (frame sides 64 and 32) vs the FP64 oracle.
 
 The split-FP16 products keep about 22 bits of each operand and accumulate in
 FP32, so the same tolerances as the FFT kernels apply: loss relative error
@@ -38,18 +38,24 @@ def _check(case, got, frames=None):
     assert rel_l2(g_alpha, ga) <= GRAD_TOL, (g_alpha, ga)
 
 
-# (n, scan side, step, offset, peaks, comps): several frames per block, ragged
-# edges, scan positions overhanging the grid on every side
+# (m, n, scan side, step, offset, peaks, comps): several frames per block,
+# ragged edges, scan positions overhanging the grid on every side; at M = 32
+# frame counts that leave a group's tile partly empty, and one with more
+# frames than the grid's tiles take in one pass (1,600 > 152 x 8)
 SIZES = [
-    (64, 1, 1, 0, 1, 1),
-    (128, 5, 16, -8, 3, 3),
-    (150, 7, 15, -20, 4, 2),
+    (64, 64, 1, 1, 0, 1, 1),
+    (64, 128, 5, 16, -8, 3, 3),
+    (64, 150, 7, 15, -20, 4, 2),
+    (32, 32, 1, 1, 0, 1, 1),
+    (32, 80, 5, 11, -6, 3, 3),
+    (32, 96, 7, 13, -9, 2, 2),
+    (32, 200, 20, 9, -5, 4, 3),
 ]
 
 
-@pytest.mark.parametrize("n,side,step,off,D,C", SIZES)
-def test_tc_loss_grad_matches_oracle(n, side, step, off, D, C):
-    spec, scan = custom_spec(n, 64, side, step, npeaks=D, ncomp=C, offset=off)
+@pytest.mark.parametrize("m,n,side,step,off,D,C", SIZES)
+def test_tc_loss_grad_matches_oracle(m, n, side, step, off, D, C):
+    spec, scan = custom_spec(n, m, side, step, npeaks=D, ncomp=C, offset=off)
     case = Case(spec, scan=scan, state="perturbed")
     p, x = _gpu(case)
     assert p.info()["precision"] == 1
@@ -57,10 +63,11 @@ def test_tc_loss_grad_matches_oracle(n, side, step, off, D, C):
     p.sync_status()
 
 
-def test_tc_random_probe_per_peak_and_background():
-    spec, scan = custom_spec(140, 64, 4, 22, npeaks=3, offset=-9, probe_per_peak=True)
+@pytest.mark.parametrize("m", [64, 32])
+def test_tc_random_probe_per_peak_and_background(m):
+    spec, scan = custom_spec(140 * m // 64, m, 4, 22 * m // 64, npeaks=3, offset=-9, probe_per_peak=True)
     rng = np.random.default_rng(5)
-    probe = (rng.standard_normal((3, 64, 64)) + 1j * rng.standard_normal((3, 64, 64))).astype(np.complex64)
+    probe = (rng.standard_normal((3, m, m)) + 1j * rng.standard_normal((3, m, m))).astype(np.complex64)
     case = Case(spec, scan=scan, probe=probe, state="perturbed", bg=True)
     p, x = _gpu(case)
     _check(case, p.loss_grad(*x))
@@ -71,9 +78,10 @@ def test_tc_random_probe_per_peak_and_background():
     p.sync_status()
 
 
-def test_tc_frame_subsets_and_bounds():
+@pytest.mark.parametrize("m", [64, 32])
+def test_tc_frame_subsets_and_bounds(m):
     from paper_2312_14907_gb300 import mpbp
-    spec, scan = custom_spec(128, 64, 4, 20, npeaks=3, offset=-6)
+    spec, scan = custom_spec(2 * m, m, 4, 20 * m // 64, npeaks=3, offset=-6)
     case = Case(spec, scan=scan, state="perturbed")
     p, x = _gpu(case)
     frames = np.array([0, 3, 3, 7, 15, 40, 47], np.int32)
@@ -88,11 +96,13 @@ def test_tc_frame_subsets_and_bounds():
     _check(case, p.loss_grad(*x))   # the context stays usable
 
 
-def test_tc_agrees_with_fft_path_on_bench_problem():
-    """The full 256^2, 3-peak, 64x64-frame problem: both precision modes in the
-    same context, and the oracle on the whole frame set."""
+@pytest.mark.parametrize("k", [2, 1])
+def test_tc_agrees_with_fft_path_on_bench_problem(k):
+    """The full 256^2, 3-peak, 64x64-frame problem and the 64^2, 32x32-frame
+    one: both precision modes in the same context, and the oracle on the whole
+    frame set."""
     from paper_2312_14907_gb300 import synth
-    case = Case(synth.config(2), state="perturbed", seed=1)
+    case = Case(synth.config(k), state="perturbed", seed=1)
     p, x = _gpu(case, precision=0)
     fft = [t.cpu().numpy() for t in p.loss_grad(*x)]
     p.set_precision(1)
@@ -125,9 +135,9 @@ def test_tc_host_entry_point_and_step():
     p.sync_status()
 
 
-def test_tc_needs_frame_side_64():
+def test_tc_needs_frame_side_32_or_64():
     from paper_2312_14907_gb300 import mpbp
-    spec, scan = custom_spec(64, 32, 3, 10, npeaks=2, offset=0)
+    spec, scan = custom_spec(48, 16, 3, 10, npeaks=2, offset=0)
     case = Case(spec, scan=scan, state="perturbed")
     p, x = _gpu(case, precision=0)
     with pytest.raises(mpbp.MPBPError) as e:
