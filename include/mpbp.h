@@ -475,13 +475,14 @@ mpbp_status mpbp_frames_timing_read(mpbp_ctx *ctx, double *total_ms, int32_t *co
 mpbp_status mpbp_set_batch_schedule(mpbp_ctx *ctx, int32_t mode, int32_t order);
 
 /* Autotuner for one context: times mpbp_loss_grad at rho, u, alpha (dev)
- * with every schedule from 1 to the occupancy limit of resident frame-kernel
- * blocks per SM -- for frame side 128 in FP32 precision, under both FFT
- * schedules (mpbp_set_fft_schedule) -- and keeps the fastest
- * (mpbp_set_schedule, mpbp_set_fft_schedule).  loss, g_rho and
- * g_u (dev) receive the evaluations.  With cache_path != NULL (host string)
- * the choice is first looked up in that JSON-lines file under a key made of
- * the GPU name, M, D, n1 x n2 and the frame count, and appended to it after
+ * over every candidate schedule and keeps the fastest: the DFT arithmetic
+ * (frame sides 32 and 64: FP32 FFTs or split tensor-core DFTs, both within the
+ * same error bounds; mpbp_set_precision), the FFT schedule (frame side 128,
+ * FP32: mpbp_set_fft_schedule) and the resident frame-kernel blocks per SM
+ * from 1 to the occupancy limit (mpbp_set_schedule).  loss, g_rho and g_u
+ * (dev) receive the evaluations.  With cache_path != NULL (host string) the
+ * choice is first looked up in that JSON-lines file under a key made of the
+ * GPU name, M, D, n1 x n2 and the frame count, and appended to it after
  * tuning.  Synchronous.  Needs probe and data. */
 mpbp_status mpbp_autotune(mpbp_ctx *ctx, const float *rho, const float *u, const float *alpha,
                           double *loss, float *g_rho, float *g_u, const char *cache_path,

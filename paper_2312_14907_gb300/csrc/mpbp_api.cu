@@ -1724,39 +1724,56 @@ mpbp_status mpbp_autotune(mpbp_ctx* c, const float* rho, const float* u, const f
     return fail(c, MPBP_ERR_INVALID_ARG, "null argument");
   if (!c->has_probe || !c->has_data) return fail(c, MPBP_ERR_NO_DATA, "probe or data not set");
   std::ostringstream k;
-  k << gpu_name(c->device) << "|single|m" << c->M << "|p" << c->precision << "|d" << c->D << "|n" << c->n1 << "x" << c->n2
-    << "|f" << c->nframes;
+  k << gpu_name(c->device) << "|single|m" << c->M << "|d" << c->D << "|n" << c->n1 << "x" << c->n2 << "|f"
+    << c->nframes;
   const double cached = cache_lookup(cache_path, k.str(), "blocks_per_sm");
   if (cached >= 1.0) {
+    const double prec = cache_lookup(cache_path, k.str(), "precision");
+    if (prec >= 0.0 && (int)prec != c->precision) {
+      const mpbp_status ps = mpbp_set_precision(c, (int32_t)prec);
+      if (ps != MPBP_OK) return ps;
+    }
     const double sched = cache_lookup(cache_path, k.str(), "fft_schedule");
     if (sched >= 0.0) c->fft_schedule = (int)sched;
     return mpbp_set_schedule(c, (int32_t)cached);
   }
   cudaStream_t s = S(stream);
-  // candidates: resident blocks per SM x (M = 128, FP32 FFTs) the FFT schedule
-  const int nsched = (c->M == 128 && c->precision == MPBP_PRECISION_FP32) ? 2 : 1;
-  int best = c->fk.blocks_per_sm, best_sched = c->fft_schedule;
+  // candidates: the DFT arithmetic (frame sides 32 and 64: FP32 FFTs or the
+  // split tensor-core DFTs, both within the same error bounds) x (M = 128,
+  // FP32) the FFT schedule x resident blocks per SM
+  std::vector<int> precs = {MPBP_PRECISION_FP32};
+  if (c->M == 32 || c->M == 64) precs.push_back(MPBP_PRECISION_TC_SPLIT16);
+  int best = 1, best_sched = c->fft_schedule, best_prec = c->precision;
   double best_ms = 1e30;
-  for (int sc = 0; sc < nsched; ++sc) {
-    if (nsched > 1) c->fft_schedule = sc;
-    for (int b = 1; b <= c->fk.blocks_per_sm; ++b) {
-      mpbp_set_schedule(c, b);
-      mpbp_status st = MPBP_OK;
-      const double ms = time_ms(s, 3, [&]() {
-        return mpbp_loss_grad(c, rho, u, alpha, nullptr, 0, loss, g_rho, g_u, nullptr, stream);
-      }, &st);
-      if (st != MPBP_OK) return st;
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = b;
-        best_sched = c->fft_schedule;
+  for (int prec : precs) {
+    mpbp_status ps = mpbp_set_precision(c, prec);
+    if (ps != MPBP_OK) return ps;
+    const int nsched = (c->M == 128 && prec == MPBP_PRECISION_FP32) ? 2 : 1;
+    for (int sc = 0; sc < nsched; ++sc) {
+      if (nsched > 1) c->fft_schedule = sc;
+      for (int b = 1; b <= c->fk.blocks_per_sm; ++b) {
+        mpbp_set_schedule(c, b);
+        mpbp_status st = MPBP_OK;
+        const double ms = time_ms(s, 3, [&]() {
+          return mpbp_loss_grad(c, rho, u, alpha, nullptr, 0, loss, g_rho, g_u, nullptr, stream);
+        }, &st);
+        if (st != MPBP_OK) return st;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = b;
+          best_sched = c->fft_schedule;
+          best_prec = prec;
+        }
       }
     }
   }
+  mpbp_status ps = mpbp_set_precision(c, best_prec);
+  if (ps != MPBP_OK) return ps;
   c->fft_schedule = best_sched;
   mpbp_set_schedule(c, best);
   std::ostringstream f;
-  f << "\"blocks_per_sm\": " << best << ", \"fft_schedule\": " << best_sched << ", \"ms\": " << best_ms;
+  f << "\"blocks_per_sm\": " << best << ", \"fft_schedule\": " << best_sched << ", \"precision\": " << best_prec
+    << ", \"ms\": " << best_ms;
   cache_store(cache_path, k.str(), f.str());
   return MPBP_OK;
 }

@@ -34,7 +34,9 @@ def test_single_problem_autotune_and_cache(tmp_path):
     b = p.autotune(*x, cache_path=str(cache))
     assert 1 <= b <= p.info()["blocks_per_sm"] or b >= 1
     lines = [json.loads(l) for l in cache.read_text().splitlines()]
-    assert len(lines) == 1 and lines[0]["blocks_per_sm"] == b and "|single|m64|p0|d3|" in lines[0]["key"]
+    assert len(lines) == 1 and lines[0]["blocks_per_sm"] == b and "|single|m64|d3|" in lines[0]["key"]
+    # the DFT arithmetic is a candidate at M = 64 (FP32 FFTs or tensor cores)
+    assert lines[0]["precision"] in (0, 1) and p.info()["precision"] == lines[0]["precision"]
     _check(case, p.loss_grad(*x))
     # a second problem of the same shape reads the cache instead of tuning
     p2, x2 = _gpu(case)

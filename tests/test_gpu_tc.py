@@ -148,13 +148,15 @@ def test_tc_needs_frame_side_32_or_64():
 
 
 def test_tc_fullsize_autotune_and_invariants():
-    """Autotuner over the tensor-core kernel's schedules; loss additivity over
-    a partition of the frames on the full bench problem."""
+    """The autotuner over the schedules (the DFT arithmetic among them); loss
+    additivity over a partition of the frames on the full bench problem in
+    the tensor-core mode."""
     from paper_2312_14907_gb300 import synth
     case = Case(synth.config(2), state="perturbed", seed=2)
     p, x = _gpu(case)
-    p.autotune(*x)
-    assert p.info()["precision"] == 1
+    p.autotune(*x)                     # the DFT arithmetic is one of its candidates
+    assert p.info()["precision"] in (0, 1)
+    p.set_precision(1)
     f_all = p.loss_grad(*x)[0].item()
     nf = case.spec.nframes
     half = torch.arange(0, nf, 2, dtype=torch.int32, device="cuda")
