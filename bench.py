@@ -567,66 +567,72 @@ SNAPSHOTS = (0, 1, 10, 199)   # iterates whose states are replayed on the oracle
 def iterations_block(torch, mpbp, args, flush, stream, rank, iters=200):
     """The 512^2, M = 128, 4-peak problem: `iters` optimizer iterations (GD +
     lagged Armijo) replayed from one captured CUDA graph, timed as a whole
-    (CUDA events, L2 flushed before); then the same trajectory again, untimed,
-    keeping the states at SNAPSHOTS, whose loss and gradient on a seeded 1/16
-    of the scan positions are compared with the FP64 oracle's at the same
-    states (rank 0, unless --no-cpu-baseline)."""
+    (CUDA events, L2 flushed before), in each DFT arithmetic (FP32 FFTs; the
+    split tensor-core DFTs); then the same trajectory again, untimed, keeping
+    the states at SNAPSHOTS, whose loss and gradient on a seeded 1/16 of the
+    scan positions are compared with the FP64 oracle's at the same states
+    (rank 0, unless --no-cpu-baseline)."""
     spec, scan, prob, probe, yd, x, t0 = setup_problem(torch, mpbp, 3)
     del yd
     # a generic start (a seeded 5% perturbation of the true object): at the
     # flat start the far field of most pixels is below rounding and the
     # gradient is not well conditioned, so no parity is defined there
     xp = synth.perturbed_state(spec, np.random.default_rng(spec.seed + 6), 0.05)
-    for t, a in zip(x, xp):
-        t.copy_(torch.from_numpy(np.ascontiguousarray(a, np.float32)))
-    x0 = [t.clone() for t in x]
-    state = prob.step_init(t0, w_rho=1.0, w_u=1e-3, w_alpha=1e-3)
-    prob.step_capture(*x, state)
-    prob.step_replay()                      # warm-up (iterate 0 -> 1)
-    torch.cuda.synchronize()
-    for t, t_init in zip(x, x0):
-        t.copy_(t_init)
-    state = prob.step_init(t0, w_rho=1.0, w_u=1e-3, w_alpha=1e-3, state=state)
-    flush.zero_()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(iters):
-        prob.step_replay()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    prob.sync_status()
-    ms = e0.elapsed_time(e1)
-    st = mpbp.Problem.read_state(state)
-    out = {"config": workload_config(spec), "iterations": iters, "ms_total": ms, "ms_per_iteration": ms / iters,
-           "value": spec.nframes * iters / (ms / 1e3), "unit": UNIT,
-           "what": "GD + lagged-Armijo steps replayed from one captured CUDA graph (FP32 FFTs), from a seeded "
-                   "5% perturbation of the true object",
-           "accepted": st.n_accept, "rejected": st.n_reject, "loss_first": None, "loss_last": st.f_last}
-    # the trajectory again with its snapshots
-    for t, t_init in zip(x, x0):
-        t.copy_(t_init)
-    state = prob.step_init(t0, w_rho=1.0, w_u=1e-3, w_alpha=1e-3, state=state)
-    snaps = {}
-    for k in range(iters):
-        if k in SNAPSHOTS:
-            snaps[k] = [t.cpu().numpy().copy() for t in x]
-        prob.step_replay()
-        if k == 0:
-            torch.cuda.synchronize()
-            out["loss_first"] = mpbp.Problem.read_state(state).f_last
-    torch.cuda.synchronize()
-    prob.sync_status()
-    out["tc_split16"] = "not built for frame side 128 (the split tensor-core DFT covers M = 64)"
-    if rank == 0 and not args.no_cpu_baseline:
-        out["vs_oracle"] = trajectory_vs_oracle(torch, mpbp, spec, scan, probe, snaps)
+    x0 = [torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda() for a in xp]
+    out = {"config": workload_config(spec), "iterations": iters,
+           "what": "GD + lagged-Armijo steps replayed from one captured CUDA graph, from a seeded 5% "
+                   "perturbation of the true object"}
+    state = None
+    for name, prec in (("fp32_fft", mpbp.PRECISION_FP32), ("tc_split16", mpbp.PRECISION_TC_SPLIT16)):
+        prob.set_precision(prec)
+        for t, t_init in zip(x, x0):
+            t.copy_(t_init)
+        state = prob.step_init(t0, w_rho=1.0, w_u=1e-3, w_alpha=1e-3, state=state)
+        prob.step_capture(*x, state)
+        prob.step_replay()                      # warm-up (iterate 0 -> 1)
+        torch.cuda.synchronize()
+        for t, t_init in zip(x, x0):
+            t.copy_(t_init)
+        state = prob.step_init(t0, w_rho=1.0, w_u=1e-3, w_alpha=1e-3, state=state)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(iters):
+            prob.step_replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prob.sync_status()
+        ms = e0.elapsed_time(e1)
+        st = mpbp.Problem.read_state(state)
+        res = {"ms_total": ms, "ms_per_iteration": ms / iters, "value": spec.nframes * iters / (ms / 1e3),
+               "unit": UNIT, "accepted": st.n_accept, "rejected": st.n_reject, "loss_last": st.f_last}
+        # the trajectory again with its snapshots
+        for t, t_init in zip(x, x0):
+            t.copy_(t_init)
+        state = prob.step_init(t0, w_rho=1.0, w_u=1e-3, w_alpha=1e-3, state=state)
+        snaps = {}
+        for k in range(iters):
+            if k in SNAPSHOTS:
+                snaps[k] = [t.cpu().numpy().copy() for t in x]
+            prob.step_replay()
+            if k == 0:
+                torch.cuda.synchronize()
+                res["loss_first"] = mpbp.Problem.read_state(state).f_last
+        torch.cuda.synchronize()
+        prob.sync_status()
+        if rank == 0 and not args.no_cpu_baseline:
+            res["vs_oracle"] = trajectory_vs_oracle(torch, mpbp, spec, scan, probe, snaps, prec)
+        out[name] = res
+    prob.set_precision(mpbp.PRECISION_FP32)
     prob.close()
     return out
 
 
-def trajectory_vs_oracle(torch, mpbp, spec, scan, probe, snaps):
-    """Loss and gradient of the GPU and of the FP64 oracle at the GPU's own
-    iterates, on a seeded 1/16 of the scan positions (every peak) with count
-    data that do not come from the CUDA path (synth.template_counts)."""
+def trajectory_vs_oracle(torch, mpbp, spec, scan, probe, snaps, precision=0):
+    """Loss and gradient of the GPU (in the given DFT arithmetic) and of the
+    FP64 oracle at the GPU's own iterates, on a seeded 1/16 of the scan
+    positions (every peak) with count data that do not come from the CUDA path
+    (synth.template_counts)."""
     import oracle
     sub_scan, js = sample_subproblem(spec, scan, max(1, scan.shape[0] // 16), spec.seed + 18)
     y = synth.template_counts(spec, spec.seed + 19, scan_index=js)
@@ -635,6 +641,7 @@ def trajectory_vs_oracle(torch, mpbp, spec, scan, probe, snaps):
                      spec.probe_per_peak)
     q.set_probe(torch.from_numpy(probe).cuda())
     q.set_data(torch.from_numpy(np.ascontiguousarray(y, np.float32)).cuda())
+    q.set_precision(precision)
 
     def rel(a, b):
         a, b = np.asarray(a, np.float64).ravel(), np.asarray(b, np.float64).ravel()

@@ -124,7 +124,7 @@ enum {
 /* Arithmetic of the 2-D DFTs (F of Eq. 2 and its adjoint in the gradient). */
 enum {
   MPBP_PRECISION_FP32 = 0,      /* FP32 radix-2 FFTs on the CUDA cores (default) */
-  MPBP_PRECISION_TC_SPLIT16 = 1 /* dense DFT matrices on the tensor cores (M = 32, 64) */
+  MPBP_PRECISION_TC_SPLIT16 = 1 /* dense DFT matrices on the tensor cores (M >= 32) */
 };
 
 /* Name of a status code (static string). */
@@ -429,10 +429,12 @@ mpbp_status mpbp_set_schedule(mpbp_ctx *ctx, int32_t blocks_per_sm);
  *     high and low part after a per-frame power-of-two scaling, products
  *     hi*hi + hi*lo + lo*hi accumulated in FP32 (about 2^-21 relative error
  *     per transform, against about 2^-22 log2(M) for the FFTs).  Frame sides
- *     64 (one frame per 64 x 64 tile) and 32 (four frames per tile, with the
+ *     64 (one frame per 64 x 64 tile), 32 (four frames per tile, with the
  *     block-diagonal pair of 32-point DFT matrices, each frame scaled on its
- *     own): MPBP_ERR_UNSUPPORTED for other M, and the context keeps its
- *     previous mode.
+ *     own) and 128 (a radix-2 x 2 step on the CUDA cores splits each
+ *     transform into four 64 x 64 ones on the tensor cores):
+ *     MPBP_ERR_UNSUPPORTED for other M, and the context keeps its previous
+ *     mode.
  * Applies to mpbp_loss_grad, mpbp_loss_grad_host, mpbp_step and to problems
  * that mpbp_loss_grad_batched launches on their own (batch mode 3, or a side
  * the mode does not fuse); mpbp_forward and the fused batched kernels always

@@ -84,10 +84,12 @@ bool frames_raw16_supported(int m);
 cudaError_t frames_launch_raw(int m, const FrameArgs& a, int grid, cudaStream_t s, const TmaMap* tm = nullptr,
                               bool y16 = false);
 
-// Tensor-core variant of the gradient kernel for m = 64 and 32 (frames_tc.cu):
-// the DFT passes as split-FP16 GEMMs on tcgen05.  Two 64 x 64 tiles in flight
-// per 256-thread block: one frame each (m = 64) or four 32 x 32 frames each
-// (m = 32, with the block-diagonal pair of 32-point DFT matrices).
+// Tensor-core variant of the gradient kernel for m = 32, 64, 128
+// (frames_tc.cu): the DFT passes as split-FP16 GEMMs on tcgen05.  Two 64 x 64
+// tiles in flight per 256-thread block: one frame each (m = 64), four
+// 32 x 32 frames each (m = 32, with the block-diagonal pair of 32-point DFT
+// matrices), or one 128 x 128 frame per tile as four 64 x 64 sub-transforms
+// after a radix-2 x 2 step on the CUDA cores (m = 128).
 constexpr int kTcThreads = 256;
 inline int tc_frames_per_block(int m) { return m == 32 ? 8 : 2; }
 constexpr size_t kTcSplitBytes = 2 * 128 * 128 * 2;   // W hi + lo, FP16

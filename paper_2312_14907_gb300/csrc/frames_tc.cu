@@ -333,6 +333,25 @@ MPBP_DI void tc_wait(TcGroup& G, int* err) {
 
 }  // namespace
 
+// W hi (group 0) and W lo (group 1) into TMEM: lane r = W row r
+MPBP_DI void tc_load_w(const uint32_t* __restrict__ wsplit, int gi, const TcGroup& G, uint32_t tbase) {
+  const uint32_t* src = wsplit + (size_t)gi * TK * W_COLS + (size_t)G.t * W_COLS;
+  const uint32_t dst = tbase + G.lane + (uint32_t)(gi * W_COLS);
+#pragma unroll
+  for (int c0 = 0; c0 < W_COLS; c0 += 16) {
+    uint32_t v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __ldg(src + c0 + j);
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            dst + (uint32_t)c0),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+  }
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 // stall != 0: no MMA is issued (test of the bounded completion waits).
 // Q4: frame side 32, four frames per group tile (wsplit: diag(W32, W32)).
 template <bool Q4>
@@ -379,24 +398,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   G.patch = reinterpret_cast<cf*>(G.bl + B_BYTES);
   G.at = reinterpret_cast<float*>(G.bh + 2 * B_BYTES + PATCH_BYTES);
 
-  // W hi (group 0) and W lo (group 1) into TMEM: lane r = W row r
-  {
-    const uint32_t* src = wsplit + (size_t)gi * TK * W_COLS + (size_t)G.t * W_COLS;
-    const uint32_t dst = tbase + G.lane + (uint32_t)(gi * W_COLS);
-#pragma unroll
-    for (int c0 = 0; c0 < W_COLS; c0 += 16) {
-      uint32_t v[16];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = __ldg(src + c0 + j);
-      asm volatile(
-          "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
-              dst + (uint32_t)c0),
-          "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
-          "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
-          : "memory");
-    }
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-  }
+  tc_load_w(wsplit, gi, G, tbase);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -548,6 +550,226 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TMEM_COLS) : "memory");
 }
 
+// ----------------------------------------------------------------------------
+// Frame side 128: each 2-D transform by one radix-2 x 2 step on the CUDA cores
+// and four 64 x 64 tensor-core transforms.  With W = exp(-2 pi i / 128),
+// sub-frame (a, b) in {0, 1}^2 and n0, n1, k0, k1 < 64:
+//   y_ab(n0, n1) = W^(a n0 + b n1) sum_{i,j} (-1)^(a i + b j) psi(n0 + 64 i, n1 + 64 j)
+//   Psi(2 k0 + a, 2 k1 + b) = F64x64[y_ab](k0, k1)
+// and for the adjoint, with G_ab = F64x64[conj(chi)(2 k0 + a, 2 k1 + b)],
+//   Z(n0 + 64 i, n1 + 64 j) = sum_ab (-1)^(a i + b j) W^(a n0 + b n1) G_ab(n0, n1).
+// A group takes one frame and its four sub-frames in turn, each through the
+// four passes of the 64 x 64 kernel (W64 in tensor memory); psi is formed
+// from the probe and the objects in global memory (L2), the sub-frame's
+// sqrt(y) values are gathered with stride 2, and each sub-frame's share of Z
+// is scattered to the four quadrants.
+// ----------------------------------------------------------------------------
+constexpr int T8_G_BYTES = 2 * B_BYTES + AT_BYTES;   // operands + the sub-frame's sqrt(y)
+constexpr int TC128_SMEM = NGROUPS * T8_G_BYTES;
+
+// sqrt(y) of sub-frame (a, b): element (q1, q0) of the staging tile = the
+// frame's sqrt(y) at (2 q0 + a, 2 q1 + b) (stored [Q1][Q0], 128 x 128)
+MPBP_DI void fetch_at_sub(const FrameArgs& p, const TcGroup& G, const FrameRef& r, int a, int b) {
+  const float* src = p.aT + (long long)r.f * 128 * 128;
+#pragma unroll 4
+  for (int i = 0; i < TM * TM / GT; ++i) {
+    const int e = G.t + i * GT;
+    const int q1 = e >> 6, q0 = e & 63;
+    const unsigned d = (unsigned)__cvta_generic_to_shared(G.at + q1 * TM + ((((q0 >> 2) ^ (q1 & 7)) << 2) | (q0 & 3)));
+    const float* sp = r.valid ? src + (2 * q1 + b) * 128 + 2 * q0 + a : src;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(sp), "r"(r.valid ? 4 : 0) : "memory");
+  }
+  cp_async_commit();
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    frames_tc128(const FrameArgs p, const uint32_t* __restrict__ wsplit, int stall) {
+  constexpr int FS = 128;
+  extern __shared__ __align__(16) unsigned char smem_tc[];
+  __shared__ uint32_t taddr_holder;
+  __shared__ __align__(8) uint64_t mbar[NGROUPS];
+  __shared__ float redf[NGROUPS][2][8];
+  __shared__ double red[TC_THREADS / 32];
+  __shared__ cf w128[FS];   // W^j
+  const int tid = threadIdx.x;
+  const int gi = tid / GT;
+  if (blockIdx.x == 0 && tid == 0 && p.arrivals) *p.arrivals = 0u;
+  if (tid < FS) {
+    float sn, cs;
+    sincospif((float)tid / 64.0f, &sn, &cs);
+    w128[tid] = cf{cs, -sn};
+  }
+  if (tid < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&taddr_holder)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int g = 0; g < NGROUPS; ++g)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[g])), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tbase = taddr_holder;
+
+  TcGroup G;
+  G.id = 1 + gi;
+  G.t = tid % GT;
+  G.lane = (uint32_t)((G.t >> 5) * 32) << 16;
+  G.wcol = tbase;
+  G.dcol = tbase + 2 * W_COLS + TM * gi;
+  G.mbar = smem_u32(&mbar[gi]);
+  G.phase = 0u;
+  G.ok = 1;
+  G.bh = smem_tc + gi * T8_G_BYTES;
+  G.bl = G.bh + B_BYTES;
+  G.patch = nullptr;
+  G.at = reinterpret_cast<float*>(G.bh + 2 * B_BYTES);
+  tc_load_w(wsplit, gi, G, tbase);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+  const int t = G.t;
+  const int rq = (t & 15) | ((t >> 5) << 4);   // transform row of this thread's TMEM lane
+  const int po = (t >> 4) & 1;                  // its part
+  const uint32_t dlane = G.dcol + G.lane;
+  double lsum = 0.0;
+  float d[64], cre[32], cim[32];
+
+  const int stride = NGROUPS * gridDim.x;
+  for (int it = NGROUPS * blockIdx.x + gi; it < p.nframes && G.ok; it += stride) {
+    const FrameRef cur = frame_ref(p, it);
+    const cf* P = frame_probe(p, cur, FS * FS);
+    const cf* obj = p.O + cur.mpk * p.obj_stride;
+    for (int ab = 0; ab < 4 && G.ok; ++ab) {
+      const int a = ab >> 1, b = ab & 1;
+      group_bar(G.id);   // the staging tile's last reads (previous residual) are done
+      fetch_at_sub(p, G, cur, a, b);
+
+      // A2: thread (column n1 = rq, half po) forms y_ab(n0, n1), n0 = 32 po + j
+      int e1;
+      {
+        float mx = 0.0f;
+#pragma unroll 4
+        for (int j = 0; j < 32; ++j) {
+          const int n0 = 32 * po + j;
+          cf sum = cf{0.0f, 0.0f};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int i = q >> 1, jj = q & 1;
+            const int r0 = n0 + 64 * i, c0 = rq + 64 * jj;
+            const int row = cur.s.x + r0, col = cur.s.y + c0;
+            cf psi = cf{0.0f, 0.0f};
+            if (cur.valid && row >= 0 && row < p.n1 && col >= 0 && col < p.n2)
+              psi = cmul(ldg_cf(P + r0 * FS + c0), ldg_cf(obj + (long long)row * p.n2 + col));
+            if ((a * i + b * jj) & 1) sum = csub(sum, psi);
+            else sum = cadd(sum, psi);
+          }
+          const cf v = cmul(sum, w128[(a * n0 + b * rq) & (FS - 1)]);
+          cre[j] = v.x;
+          cim[j] = v.y;
+          mx = abs_max(abs_max(mx, v.x), v.y);
+        }
+        e1 = scale_exp(group_max(mx, redf[gi][0], G.id));
+        const float s = pow2f(e1);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          split_store8(G.bh, G.bl, rq, 32 * po + 8 * c, cre + 8 * c, s);
+          split_store8(G.bh, G.bl, rq, 64 + 32 * po + 8 * c, cim + 8 * c, s);
+        }
+      }
+      tc_pass(G, p.err, stall);   // [(k0, po)][n1] = 2^e1 F_0 y_ab
+      tc_wait(G, p.err);
+      if (G.ok) tmem_row64(dlane, d);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) split_store8(G.bh, G.bl, rq, 64 * po + 8 * c, d + 8 * c, pow2f(-6));
+      tc_pass(G, p.err, stall);   // [(k1, po)][k0] = 2^(e1 - 6) Psi(2 k0 + a, 2 k1 + b)
+      tc_wait(G, p.err);
+
+      // A4 on Psi(2 q0 + a, 2 q1 + b), q1 = rq, q0 = 32 po + j
+      int e3;
+      {
+        if (G.ok) tmem_row64(dlane, d);
+        pair_columns(d, po, cre, cim);
+        cp_async_wait_all();
+        group_bar(G.id);   // the sub-frame's sqrt(y) values are staged
+        const float un = pow2f(6 - e1);
+        const float* bg = p.bgT ? p.bgT + (long long)cur.f * FS * FS + (2 * rq + b) * FS + a : nullptr;
+        float av[32];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {   // q0 = 32 po + 4i .. + 3
+          const float4 v = *reinterpret_cast<const float4*>(G.at + at_idx(rq, 32 * po + 4 * i));
+          av[4 * i] = v.x;
+          av[4 * i + 1] = v.y;
+          av[4 * i + 2] = v.z;
+          av[4 * i + 3] = v.w;
+        }
+        float fl = 0.0f, mx = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float bv = bg ? __ldg(bg + 2 * (32 * po + j)) : 0.0f;
+          const cf z = residual(cf{cre[j] * un, cim[j] * un}, av[j], bv, fl);
+          cre[j] = z.x;
+          cim[j] = z.y;
+          mx = abs_max(abs_max(mx, z.x), z.y);
+        }
+        if (cur.valid) lsum += 0.5 * (double)fl;
+        e3 = scale_exp(group_max(mx, redf[gi][1], G.id));
+        const float s = pow2f(e3);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {   // operand row q1: conj(chi) at q0
+          split_store8(G.bh, G.bl, rq, 32 * po + 8 * c, cre + 8 * c, s);
+          split_store8(G.bh, G.bl, rq, 64 + 32 * po + 8 * c, cim + 8 * c, s);
+        }
+      }
+      tc_pass(G, p.err, stall);   // [(n0, po)][q1] = 2^e3 F_0 conj(chi)_ab
+      tc_wait(G, p.err);
+      if (G.ok) tmem_row64(dlane, d);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) split_store8(G.bh, G.bl, rq, 64 * po + 8 * c, d + 8 * c, pow2f(-6));
+      tc_pass(G, p.err, stall);   // [(n1, po)][n0] = 2^(e3 - 6) G_ab
+      tc_wait(G, p.err);
+
+      // A6 + A7: G_ab(n0, n1), n1 = rq, n0 = 32 po + j, to the four quadrants
+      if (G.ok) {
+        tmem_row64(dlane, d);
+        pair_columns(d, po, cre, cim);
+        const float uz = pow2f(6 - e3);
+        cf* acc = p.acc + cur.mpk * p.obj_stride;
+        if (cur.valid) {
+#pragma unroll 2
+          for (int j = 0; j < 32; ++j) {
+            const int n0 = 32 * po + j;
+            const cf g = cmul(cf{cre[j] * uz, cim[j] * uz}, w128[(a * n0 + b * rq) & (FS - 1)]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int i = q >> 1, jj = q & 1;
+              const int r0 = n0 + 64 * i, c0 = rq + 64 * jj;
+              const int row = cur.s.x + r0, col = cur.s.y + c0;
+              if (row >= 0 && row < p.n1 && col >= 0 && col < p.n2) {
+                const cf z = ((a * i + b * jj) & 1) ? cf{-g.x, -g.y} : g;
+                red_add_v2(acc + (long long)row * p.n2 + col, cmul(ldg_cf(P + r0 * FS + c0), z));
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  cp_async_wait_all();
+
+  const double tot = block_sum_d<TC_THREADS>(lsum, red);
+  if (tid == 0) p.loss_part[blockIdx.x] = tot;
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (tid < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TMEM_COLS) : "memory");
+}
+
 // W hi and lo as the A operand in tensor memory: [2][128 rows][64 columns],
 // column c of a row holding elements 2c (low half) and 2c + 1 (high half);
 // row r is transform row (r mod 16) + 16 (r div 32), part (r div 16) mod 2.
@@ -585,6 +807,10 @@ bool tc_prepare(int* blocks_per_sm, int* smem_bytes) {
         cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared) != cudaSuccess)
       return false;
+  if (cudaFuncSetAttribute(frames_tc128, cudaFuncAttributeMaxDynamicSharedMemorySize, TC128_SMEM) != cudaSuccess ||
+      cudaFuncSetAttribute(frames_tc128, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+    return false;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, frames_tc64<false>, TC_THREADS, TC_SMEM) !=
       cudaSuccess)
     return false;
@@ -594,7 +820,9 @@ bool tc_prepare(int* blocks_per_sm, int* smem_bytes) {
 }
 
 cudaError_t tc_launch(int m, const FrameArgs& a, const void* wsplit, int grid, cudaStream_t s, bool test_stall) {
-  if (m == 32)
+  if (m == 128)
+    frames_tc128<<<grid, TC_THREADS, TC128_SMEM, s>>>(a, static_cast<const uint32_t*>(wsplit), test_stall ? 1 : 0);
+  else if (m == 32)
     frames_tc64<true><<<grid, TC_THREADS, TC_SMEM, s>>>(a, static_cast<const uint32_t*>(wsplit), test_stall ? 1 : 0);
   else
     frames_tc64<false><<<grid, TC_THREADS, TC_SMEM, s>>>(a, static_cast<const uint32_t*>(wsplit), test_stall ? 1 : 0);

@@ -597,12 +597,13 @@ mpbp_status mpbp_set_precision(mpbp_ctx* c, int32_t mode) {
   if (mode == MPBP_PRECISION_FP32) {
     c->fk = c->fk_fft;
   } else {
-    if (c->M != 64 && c->M != 32) return fail(c, MPBP_ERR_UNSUPPORTED, "tensor-core DFTs need frame side 32 or 64");
+    if (c->M != 32 && c->M != 64 && c->M != 128)
+      return fail(c, MPBP_ERR_UNSUPPORTED, "tensor-core DFTs need frame side 32, 64 or 128");
     int bps = 0, smem = 0;
     if (!tc_prepare(&bps, &smem)) return fail(c, MPBP_ERR_CUDA, "tensor-core kernel cannot run here");
     if (!c->tc_w) {
       std::vector<uint32_t> w(kTcSplitBytes / 4);
-      tc_split_dft(w.data(), c->M);
+      tc_split_dft(w.data(), c->M == 32 ? 32 : 64);   // M = 128: four 64 x 64 sub-transforms
       MPBP_CUDA(c, cudaDeviceSynchronize());
       void* d = nullptr;
       if (cudaMalloc(&d, kTcSplitBytes) != cudaSuccess) {
@@ -1738,11 +1739,11 @@ mpbp_status mpbp_autotune(mpbp_ctx* c, const float* rho, const float* u, const f
     return mpbp_set_schedule(c, (int32_t)cached);
   }
   cudaStream_t s = S(stream);
-  // candidates: the DFT arithmetic (frame sides 32 and 64: FP32 FFTs or the
+  // candidates: the DFT arithmetic (frame sides 32, 64, 128: FP32 FFTs or the
   // split tensor-core DFTs, both within the same error bounds) x (M = 128,
   // FP32) the FFT schedule x resident blocks per SM
   std::vector<int> precs = {MPBP_PRECISION_FP32};
-  if (c->M == 32 || c->M == 64) precs.push_back(MPBP_PRECISION_TC_SPLIT16);
+  if (c->M >= 32) precs.push_back(MPBP_PRECISION_TC_SPLIT16);
   int best = 1, best_sched = c->fft_schedule, best_prec = c->precision;
   double best_ms = 1e30;
   for (int prec : precs) {

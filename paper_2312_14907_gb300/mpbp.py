@@ -285,7 +285,7 @@ class Problem:
 
     def set_precision(self, mode):
         """DFT arithmetic of the gradient evaluations: PRECISION_FP32 (FFTs) or
-        PRECISION_TC_SPLIT16 (tensor cores, frame sides 32 and 64)."""
+        PRECISION_TC_SPLIT16 (tensor cores, frame sides 32, 64 and 128)."""
         self._check(self._lib.mpbp_set_precision(self._h, int(mode)), "mpbp_set_precision")
 
     def set_fft_schedule(self, schedule):

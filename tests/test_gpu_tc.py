@@ -41,7 +41,8 @@ def _check(case, got, frames=None):
 # (m, n, scan side, step, offset, peaks, comps): several frames per block,
 # ragged edges, scan positions overhanging the grid on every side; at M = 32
 # frame counts that leave a group's tile partly empty, and one with more
-# frames than the grid's tiles take in one pass (1,600 > 152 x 8)
+# frames than the grid's tiles take in one pass (1,600 > 152 x 8); at M = 128
+# one with more frames than two per block (338 > 152 x 2)
 SIZES = [
     (64, 64, 1, 1, 0, 1, 1),
     (64, 128, 5, 16, -8, 3, 3),
@@ -50,6 +51,8 @@ SIZES = [
     (32, 80, 5, 11, -6, 3, 3),
     (32, 96, 7, 13, -9, 2, 2),
     (32, 200, 20, 9, -5, 4, 3),
+    (128, 200, 3, 40, -20, 2, 3),
+    (128, 256, 13, 10, -6, 2, 3),
 ]
 
 
@@ -63,7 +66,7 @@ def test_tc_loss_grad_matches_oracle(m, n, side, step, off, D, C):
     p.sync_status()
 
 
-@pytest.mark.parametrize("m", [64, 32])
+@pytest.mark.parametrize("m", [64, 32, 128])
 def test_tc_random_probe_per_peak_and_background(m):
     spec, scan = custom_spec(140 * m // 64, m, 4, 22 * m // 64, npeaks=3, offset=-9, probe_per_peak=True)
     rng = np.random.default_rng(5)

@@ -18,7 +18,10 @@ pytestmark = pytest.mark.gpu
 KEEP = (0, 1, 10)
 
 
-def test_graph_trajectory_replayed_on_the_oracle():
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_trajectory_replayed_on_the_oracle(precision):
+    """Both DFT arithmetics: FP32 FFTs (0) and the split tensor-core DFTs (1,
+    four 64 x 64 sub-transforms per 128 x 128 frame)."""
     import oracle
     from paper_2312_14907_gb300 import mpbp, synth
     spec = synth.config(3)
@@ -29,6 +32,7 @@ def test_graph_trajectory_replayed_on_the_oracle():
     yd = torch.from_numpy(synth.template_counts(spec, spec.seed + 80)).cuda()
     p.set_data(yd)
     del yd
+    p.set_precision(precision)
     xs = synth.perturbed_state(spec, np.random.default_rng(spec.seed + 81), 0.05)
     x = [torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda() for a in xs]
     overlap = (spec.m / spec.step) ** 2 * spec.npeaks
@@ -52,9 +56,17 @@ def test_graph_trajectory_replayed_on_the_oracle():
     q_full = mpbp.Problem.from_spec(spec, scan)
     q_full.set_probe(torch.from_numpy(probe).cuda())
     q_full.set_data(torch.from_numpy(synth.template_counts(spec, spec.seed + 80)).cuda())
+    q_full.set_precision(precision)
     for k, a in snaps.items():
-        f = q_full.loss(*[torch.from_numpy(v).cuda() for v in a]).item()
-        assert abs(f - f_rec[k]) <= 1e-9 * abs(f), (k, f, f_rec[k])
+        # the loss of a step equals a plain evaluation at its state (the loss
+        # alone, on the FFTs, for FP32; the same precision's loss and gradient
+        # otherwise)
+        if precision == 0:
+            f = q_full.loss(*[torch.from_numpy(v).cuda() for v in a]).item()
+            assert abs(f - f_rec[k]) <= 1e-9 * abs(f), (k, f, f_rec[k])
+        else:
+            f = q_full.loss_grad(*[torch.from_numpy(v).cuda() for v in a])[0].item()
+            assert abs(f - f_rec[k]) <= 1e-12 * abs(f), (k, f, f_rec[k])
     q_full.close()
     # the oracle at the GPU's iterates, on a seeded 1/16 of the scan positions
     js = np.sort(np.random.default_rng(spec.seed + 82).choice(scan.shape[0], scan.shape[0] // 16, replace=False))
@@ -64,6 +76,7 @@ def test_graph_trajectory_replayed_on_the_oracle():
     q = mpbp.Problem(spec.n1, spec.n2, spec.ncomp, spec.npeaks, spec.m, sub, spec.G, spec.phase_scale)
     q.set_probe(torch.from_numpy(probe).cuda())
     q.set_data(torch.from_numpy(y).cuda())
+    q.set_precision(precision)
     for k, a in snaps.items():
         got = [t.cpu().numpy() for t in q.loss_grad(*[torch.from_numpy(v).cuda() for v in a])]
         f, gr, gu, ga = orc.loss_grad(*a, probe, y)
