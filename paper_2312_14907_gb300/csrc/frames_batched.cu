@@ -42,7 +42,7 @@ MPBP_DI void batch_item(const BatchArgs& b, int it, int2 item, bool prefetched,
   const long long slot = (b.frame_base[item.x] + item.y + gi) * kBatchWarpSlots;
   t2_frame<M, false>(
       p, g, cur,
-      [&](const FrameArgs*& pn) {
+      [&](const FrameArgs*& pn, const TmaMap*&) {
         if (same) {
           pn = &b.probs[item2.x];
           return frame_ref(*pn, item2.y + gi);
@@ -80,18 +80,25 @@ __global__ void __launch_bounds__(kBatchThreads, 1) frames_batched(const __grid_
 
 // One persistent launch over the frames of every problem with frame side M
 // (items are single frames); the block shape and occupancy are those of the
-// single-problem kernel for M.
-template <int M>
+// single-problem kernel for M.  TMA: the inputs by tile and bulk copies as in
+// the single-problem kernel, each problem's objects through its own tensor
+// map (b.tmaps, device memory), on the block's mbarrier with the same bounded
+// wait; else per-element cp.async.
+template <int M, bool TMA>
 __global__ void __launch_bounds__(T2Cfg<M>::T, T2Cfg<M>::MINB) frames_batched_m(const __grid_constant__ BatchArgs b) {
+  using C = T2Cfg<M>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // arguments of the frames' problems, three-way rotated: the slot written at
   // the top of an iteration was last read two frames earlier, and a thread
   // can only be here after every thread has passed that frame's barriers
   __shared__ FrameArgs sp[3];
+  __shared__ __align__(8) uint64_t mbar;
   if (blockIdx.x == 0)
     for (int i = threadIdx.x; i < b.nprob; i += blockDim.x)
       if (b.probs[i].arrivals) *b.probs[i].arrivals = 0u;
-  const T2Group<M> g = T2Group<M>::make(threadIdx.x, 0, smem_raw);
+  unsigned char* smem = TMA ? smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u) : smem_raw;
+  const T2Group<M> g = T2Group<M>::make(threadIdx.x, 0, smem, TMA ? C::TBUF : C::BUF);
+  BulkState bs{smem_addr(&mbar), 0u, true};
   int it = blockIdx.x;
   if (it >= b.nitems) return;
   int cs = 0;   // which of sp[] holds the current problem
@@ -99,11 +106,12 @@ __global__ void __launch_bounds__(T2Cfg<M>::T, T2Cfg<M>::MINB) frames_batched_m(
   {
     const int2 item = b.items[it];
     stage_args(&sp[0], &b.probs[item.x]);
+    if (TMA && threadIdx.x == 0) mbar_init(bs.bar, 1);
     __syncthreads();
     cur = frame_ref(sp[0], item.y);
-    t2_fetch<M, false>(sp[0], g, cur);
+    t2_fetch<M, false, false, TMA>(sp[0], g, cur, &bs, TMA ? &b.tmaps[item.x] : nullptr);
   }
-  cp_async_commit();
+  if constexpr (!TMA) cp_async_commit();
   for (; it < b.nitems; it += gridDim.x) {
     const int2 item = b.items[it];
     const int it2 = it + gridDim.x;
@@ -112,23 +120,29 @@ __global__ void __launch_bounds__(T2Cfg<M>::T, T2Cfg<M>::MINB) frames_batched_m(
     const int ns = cs == 2 ? 0 : cs + 1;
     // visible after the barrier that opens t2_frame
     stage_args(&sp[ns], &b.probs[item2.x]);
-    cur = t2_frame<M, false>(
+    cur = t2_frame<M, false, false, TMA>(
         sp[cs], g, cur,
-        [&](const FrameArgs*& pn) {
+        [&](const FrameArgs*& pn, const TmaMap*& tmn) {
           pn = &sp[ns];
+          if (TMA) tmn = &b.tmaps[item2.x];
           return frame_ref(*pn, item2.y);
         },
         [&](float fl) {
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) fl += __shfl_xor_sync(0xffffffffu, fl, o);
           if ((g.tid & 31) == 0) b.frame_part[slot + (g.tid >> 5)] = (double)fl;
-        });
+        },
+        &bs, TMA ? &b.tmaps[item.x] : nullptr);
+    if (TMA && !bs.ok) {
+      if (threadIdx.x == 0) atomicOr(sp[cs].err, kErrTimeout);
+      break;
+    }
     cs = ns;
   }
   cp_async_wait_all();
 }
 
-bool batched_m_prepare(int m, int* blocks_per_sm) {
+bool batched_m_prepare(int m, bool tma, int* blocks_per_sm) {
   auto prep = [&](auto kern, int threads, int smem) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
       return false;
@@ -136,18 +150,31 @@ bool batched_m_prepare(int m, int* blocks_per_sm) {
                cudaSuccess && *blocks_per_sm > 0;
   };
   switch (m) {
-    case 32: return prep(frames_batched_m<32>, T2Cfg<32>::T, T2Cfg<32>::SMEM);
-    case 64: return prep(frames_batched_m<64>, T2Cfg<64>::T, T2Cfg<64>::SMEM);
-    case 128: return prep(frames_batched_m<128>, T2Cfg<128>::T, T2Cfg<128>::SMEM);
+    case 32:
+      return tma ? prep(frames_batched_m<32, true>, T2Cfg<32>::T, T2Cfg<32>::SMEM_TMA)
+                 : prep(frames_batched_m<32, false>, T2Cfg<32>::T, T2Cfg<32>::SMEM);
+    case 64:
+      return tma ? prep(frames_batched_m<64, true>, T2Cfg<64>::T, T2Cfg<64>::SMEM_TMA)
+                 : prep(frames_batched_m<64, false>, T2Cfg<64>::T, T2Cfg<64>::SMEM);
+    case 128: return !tma && prep(frames_batched_m<128, false>, T2Cfg<128>::T, T2Cfg<128>::SMEM);
     default: return false;
   }
 }
 
-cudaError_t batched_m_launch(int m, const BatchArgs& b, int grid, cudaStream_t s) {
+cudaError_t batched_m_launch(int m, bool tma, const BatchArgs& b, int grid, cudaStream_t s) {
   switch (m) {
-    case 32: frames_batched_m<32><<<grid, T2Cfg<32>::T, T2Cfg<32>::SMEM, s>>>(b); break;
-    case 64: frames_batched_m<64><<<grid, T2Cfg<64>::T, T2Cfg<64>::SMEM, s>>>(b); break;
-    case 128: frames_batched_m<128><<<grid, T2Cfg<128>::T, T2Cfg<128>::SMEM, s>>>(b); break;
+    case 32:
+      if (tma) frames_batched_m<32, true><<<grid, T2Cfg<32>::T, T2Cfg<32>::SMEM_TMA, s>>>(b);
+      else frames_batched_m<32, false><<<grid, T2Cfg<32>::T, T2Cfg<32>::SMEM, s>>>(b);
+      break;
+    case 64:
+      if (tma) frames_batched_m<64, true><<<grid, T2Cfg<64>::T, T2Cfg<64>::SMEM_TMA, s>>>(b);
+      else frames_batched_m<64, false><<<grid, T2Cfg<64>::T, T2Cfg<64>::SMEM, s>>>(b);
+      break;
+    case 128:
+      if (tma) return cudaErrorInvalidValue;
+      frames_batched_m<128, false><<<grid, T2Cfg<128>::T, T2Cfg<128>::SMEM, s>>>(b);
+      break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

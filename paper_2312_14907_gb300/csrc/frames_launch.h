@@ -36,6 +36,8 @@ struct BatchArgs {
   FrameArgs probs[kBatchMaxProbs];       // per-problem arguments (frames == nullptr)
   int prob_m[kBatchMaxProbs];            // frame side
   long long frame_base[kBatchMaxProbs];  // first slot of the problem in frame_part
+  const TmaMap* tmaps;                   // per-side launches with tile copies: [nprob]
+                                         // tensor maps (device memory), else nullptr
   const int2* items;                     // [nitems] (problem, first frame)
   double* frame_part;                    // [frames][kBatchWarpSlots] loss partials,
                                          // zeroed before the launch
@@ -48,8 +50,9 @@ bool batched_prepare(int* blocks_per_sm);
 cudaError_t batched_launch(const BatchArgs& b, int grid, cudaStream_t s);
 
 // One launch per frame side: items are single frames of problems with side m.
-bool batched_m_prepare(int m, int* blocks_per_sm);
-cudaError_t batched_m_launch(int m, const BatchArgs& b, int grid, cudaStream_t s);
+// tma (m = 32, 64): the inputs by tile and bulk copies, b.tmaps set.
+bool batched_m_prepare(int m, bool tma, int* blocks_per_sm);
+cudaError_t batched_m_launch(int m, bool tma, const BatchArgs& b, int grid, cudaStream_t s);
 
 // Layout of the M = 128 loss-and-gradient kernel (ignored for other sides):
 // radix-2 stages of each 128-point line across four threads by shuffles

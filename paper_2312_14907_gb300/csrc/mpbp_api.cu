@@ -86,6 +86,7 @@ struct mpbp_ctx {
   struct PlanLaunch {
     int m;          // frame side, or 0 for the single launch over every side
     int grid;
+    bool tma;       // per-side launch with tile copies (args.tmaps set)
     BatchArgs args;
   };
   std::vector<PlanLaunch> batch_plan;
@@ -1534,9 +1535,23 @@ mpbp_status mpbp_loss_grad_batched(int32_t n, mpbp_ctx* const* ctxs, const float
       if (!group.empty()) add_launch(side, group);
     }
     // device tables in the lead context's batch buffer
+    // per-side launches of frame sides 32 and 64 whose problems all have
+    // tile copies (rows of 16-byte multiples) take their inputs by TMA, each
+    // problem through its own tensor map in the batch buffer
+    std::vector<char> launch_tma(launches.size(), 0);
+    size_t ntm = 0;
+    for (size_t l = 0; l < launches.size(); ++l) {
+      const Launch& L = launches[l];
+      if (L.m != 32 && L.m != 64) continue;
+      bool all = true;
+      for (int k : L.probs) all = all && ctxs[fused[k]]->tile_grad;
+      launch_tma[l] = all;
+      if (all) ntm += L.probs.size();
+    }
     Carver cv;
     const size_t oI = cv.take<int2>(items.empty() ? 1 : items.size());
     const size_t oFP = cv.take<double>((size_t)(total_frames > 0 ? total_frames : 1) * kBatchWarpSlots);
+    const size_t oTM = cv.take<TmaMap>(ntm > 0 ? ntm : 1);
     const size_t need = align_up(cv.off, 256);
     if (need > lead->batch_ws_bytes) {
       MPBP_CUDA(lead, cudaStreamSynchronize(s));
@@ -1555,25 +1570,37 @@ mpbp_status mpbp_loss_grad_batched(int32_t n, mpbp_ctx* const* ctxs, const float
       MPBP_CUDA(lead, cudaMemcpyAsync(wb + oI, items.data(), sizeof(int2) * items.size(),
                                       cudaMemcpyHostToDevice, s));
     double* frame_part = reinterpret_cast<double*>(wb + oFP);
-    for (const Launch& L : launches) {
+    std::vector<TmaMap> tms(ntm > 0 ? ntm : 1);
+    size_t tm_next = 0;
+    for (size_t l = 0; l < launches.size(); ++l) {
+      const Launch& L = launches[l];
       mpbp_ctx::PlanLaunch P{};
       P.m = L.m;
+      P.tma = launch_tma[l] != 0;
+      if (P.tma) P.args.tmaps = reinterpret_cast<const TmaMap*>(wb + oTM) + tm_next;
       for (size_t k = 0; k < L.probs.size(); ++k) {
         mpbp_ctx* c = ctxs[fused[L.probs[k]]];
         P.args.probs[k] = frame_args(c, nullptr, (int)c->nframes);
         P.args.prob_m[k] = c->M;
         P.args.frame_base[k] = base[L.probs[k]];
+        if (P.tma) {
+          tms[tm_next] = c->tm_grad;
+          tms[tm_next].tx_extra = c->test_tx_extra;
+          ++tm_next;
+        }
       }
       P.args.nprob = (int)L.probs.size();
       P.args.items = reinterpret_cast<const int2*>(wb + oI) + L.first;
       P.args.nitems = (int)L.count;
       P.args.frame_part = frame_part;
       int bps = 1;
-      const bool ok = L.m == 0 ? batched_prepare(&bps) : batched_m_prepare(L.m, &bps);
+      const bool ok = L.m == 0 ? batched_prepare(&bps) : batched_m_prepare(L.m, P.tma, &bps);
       if (!ok) return fail(lead, MPBP_ERR_CUDA, "batched kernel setup");
       P.grid = (int)std::min<long long>((long long)L.count, (long long)lead->num_sms * bps);
       lead->batch_plan.push_back(P);
     }
+    if (ntm > 0)
+      MPBP_CUDA(lead, cudaMemcpyAsync(wb + oTM, tms.data(), sizeof(TmaMap) * ntm, cudaMemcpyHostToDevice, s));
     lead->batch_base = base;
     lead->batch_fused = fused;
     lead->batch_frames = total_frames;
@@ -1602,7 +1629,7 @@ mpbp_status mpbp_loss_grad_batched(int32_t n, mpbp_ctx* const* ctxs, const float
   for (int k = 0; k < nf; ++k) ctxs[fused[k]]->acc_dirty = true;
   for (const auto& P : lead->batch_plan) {
     if (P.m == 0) MPBP_CUDA(lead, batched_launch(P.args, P.grid, s));
-    else MPBP_CUDA(lead, batched_m_launch(P.m, P.args, P.grid, s));
+    else MPBP_CUDA(lead, batched_m_launch(P.m, P.tma, P.args, P.grid, s));
   }
   std::vector<int> grid_of(n, 0);
   for (int i = 0; i < n; ++i) {
@@ -1844,6 +1871,7 @@ mpbp_status mpbp_frames_timing_read(mpbp_ctx* c, double* total_ms, int32_t* coun
 mpbp_status mpbp_set_test_stall(mpbp_ctx* c, int32_t on) {
   if (!c) return MPBP_ERR_INVALID_ARG;
   c->test_tx_extra = on ? 16u : 0u;
+  c->version++;   // batched plans copy the tensor maps with the hook
   return MPBP_OK;
 }
 

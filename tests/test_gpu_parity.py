@@ -360,3 +360,29 @@ def test_tile_copy_wait_runs_out_and_reports(m, schedule):
     p.set_test_stall(False)
     _check_loss_grad(case, p.loss_grad(*x))
     p.sync_status()
+
+
+def test_batched_tile_copy_wait_runs_out_and_reports():
+    """The per-side batched launches take their inputs by tile copies, each
+    problem through its own tensor map, with the same bounded wait: with the
+    test hook on one problem its copies' barrier waits run out, the call
+    reports MPBP_ERR_TIMEOUT for that problem, and the batch then computes
+    the oracle's results again."""
+    import time
+    from paper_2312_14907_gb300 import mpbp
+    cases = [Case(*custom_spec(96, 32, 5, 14, npeaks=3, offset=-2, seed=1), state="perturbed"),
+             Case(*custom_spec(160, 64, 4, 30, npeaks=4, offset=-5, seed=2), state="perturbed")]
+    probs, states = zip(*[_gpu(c) for c in cases])
+    probs[0].set_batch_schedule(1, 0)        # one launch per frame side
+    probs[1].set_test_stall(True)
+    t0 = time.time()
+    mpbp.loss_grad_batched(list(probs), list(states))
+    with pytest.raises(mpbp.MPBPError) as e:
+        probs[1].sync_status()
+    assert e.value.status == 5, e.value           # MPBP_ERR_TIMEOUT
+    assert time.time() - t0 < 20.0
+    probs[1].set_test_stall(False)
+    for c, o in zip(cases, mpbp.loss_grad_batched(list(probs), list(states))):
+        _check_loss_grad(c, o)
+    for p in probs:
+        p.sync_status()
