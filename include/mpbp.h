@@ -499,8 +499,10 @@ mpbp_status mpbp_autotune_batched(int32_t n, mpbp_ctx *const *ctxs, const float 
                                   double *const *loss, float *const *g_rho, float *const *g_u,
                                   const char *cache_path, void *stream);
 
-/* Synchronises `stream`, then returns and clears the first error latched on
- * the device since the last call (MPBP_OK if none). */
+/* Synchronises `stream`, then clears the errors latched on the device since
+ * the last call and returns one of them (MPBP_OK if none): MPBP_ERR_BOUNDS,
+ * else MPBP_ERR_TIMEOUT (the results of a call whose bounded wait ran out are
+ * undefined, a non-finite loss among them), else MPBP_ERR_NONFINITE. */
 mpbp_status mpbp_sync_status(mpbp_ctx *ctx, void *stream);
 
 #ifdef __cplusplus

@@ -10,7 +10,7 @@
 //   X1(q0, c)  = sum_h  W4^(k'' h) W^(k' h) [sum_n W32^(n k') psi(4n + h, c)]
 //   Psi(q0,q1) = sum_c_r W16^(m'' c_r) W^(m' c_r) [sum_c_a W8^(m' c_a) X1(q0, c_r + 16 c_a)]
 // Layouts (register index -> thread index):
-//   L1  n (32)                    | c, h        lane = 8 h + (c mod 8), warp = c / 8
+//   L1  n (32)                    | c, h        lane = c mod 32, warp = 4 h + c / 32
 //   L2  h or k'' (4) x c_a or m'  | k', c_r     lane = c_r + 16 (k' mod 2), warp = k' / 2
 //   L3  c_r or m'' (16) x m_r (2) | q0, m_t     lane = k', warp = 4 k'' + m_t;  m' = m_t + 4 m_r
 // L1: the 32-point transforms over n.  L2: twiddle W^(k' h), 4-point
@@ -20,8 +20,23 @@
 // factorisation backwards (16-point over m'' in L3, twiddle W^(m' c_r) and
 // 8-point over m' in L2, 4-point over k'' and twiddle W^(k' h) in L2, 32-point
 // over k' in L1) and ends in L1, the columns layout of the scatter (A6, A7).
-// The per-thread twiddles W^(h k'), h = 1..3, and W^(m' c_r), m' = 1..7, are
-// formed once per block and kept in tensor memory (20 words a thread).
+// The twiddles W^(h k'), h = 1..3, and W^(m' c_r), m' = 1..7, are formed once
+// per block into a 1.7 KB shared table.
+//
+// Gradient accumulation (A7).  A block takes a contiguous range of the
+// frames in the order it is given; the host orders them by peak, scan column
+// and scan row, so that a block's consecutive frames mostly share their
+// columns and overlap in rows.  Tensor memory holds the probe (columns
+// 0..255) and, in columns 256..511, the gradient of a 128-row window of the
+// block's current column strip: TMEM lane c is column c of the frame (the
+// four warps of L1 that hold column c share that lane), and absolute row R
+// sits in slot R mod 128.  A frame adds P conj(F^H chi) into the slots of its
+// rows; when the next frame of the strip starts d rows lower, the d rows that
+// leave the window are added to the object-sized accumulator with
+// red.global.add and their slots cleared, so the rows shared by successive
+// frames cross to global memory once.  A frame in another strip (another
+// column, peak, or a row outside the window) writes the whole window back
+// first; the block writes back what is left at its end.
 //
 // Shared layouts (complex values), every 16-lane half-warp on 16 distinct
 // 8-byte banks:
@@ -44,7 +59,8 @@ struct X3Cfg {
   static constexpr int BUF = (B_VALS > PATCH_VALS ? B_VALS : PATCH_VALS) * (int)sizeof(cf);
   static constexpr int ABUF = M * M * (int)sizeof(float);       // sqrt(y) [q1][q0]
   static constexpr int SMEM = BUF + ABUF + 128;                  // + alignment of the tile destination
-  static constexpr uint32_t TMEM_COLS = 512;                     // probe (0..255), twiddles (256..)
+  static constexpr uint32_t TMEM_COLS = 512;                     // probe (0..255), gradient window (256..)
+  static constexpr uint32_t ACC_COL = 256;
   static_assert(A_VALS <= B_VALS && BUF % 16 == 0, "layouts");
 };
 
@@ -61,8 +77,8 @@ struct X3Roles {
     X3Roles r;
     r.tid = tid;
     const int w = tid >> 5, l = tid & 31;
-    r.c = 8 * w + (l & 7);
-    r.h = l >> 3;
+    r.c = 32 * (w & 3) + l;   // a warp holds 32 consecutive columns of one row h
+    r.h = w >> 2;
     r.kp = 2 * w + (l >> 4);
     r.cr = l & 15;
     r.q0 = l + 32 * (w >> 2);
@@ -76,32 +92,22 @@ MPBP_DI int x3_b(int mp, int q0, int i) { return (mp * 128 + q0) * 17 + i; }
 
 // W^j = exp(-2 pi i j / 128)
 MPBP_DI cf x3_w128(int j) {
-  float s, c;
-  sincospif((float)(j & 127) / 64.0f, &s, &c);
-  return cf{c, -s};
+  float sn, cs;
+  sincospif((float)(j & 127) / 64.0f, &sn, &cs);
+  return cf{cs, -sn};
 }
 
-// The thread's 20 twiddle words into tensor memory: W^(h k'), h = 1..3, then
-// W^(m' c_r), m' = 1..7 (words 6..19)
-MPBP_DI void x3_twiddles_to_tmem(const X3Roles& r, uint32_t tt) {
-  uint32_t w[16], w4[16];
-#pragma unroll
-  for (int i = 0; i < 10; ++i) {
-    const cf t = i < 3 ? x3_w128((i + 1) * r.kp) : x3_w128((i - 2) * r.cr);
-    const int k = 2 * i;
-    if (k < 16) {
-      w[k] = __float_as_uint(t.x);
-      w[k + 1] = __float_as_uint(t.y);
-    } else {
-      w4[k - 16] = __float_as_uint(t.x);
-      w4[k - 15] = __float_as_uint(t.y);
-    }
-  }
-#pragma unroll
-  for (int k = 4; k < 16; ++k) w4[k] = 0u;
-  tmem_st16(tt, w);
-  tmem_st16(tt + 16, w4);
-  tmem_wait_st();
+// the twiddles of L2: th[h - 1][k'] = W^(h k'), um[m' - 1][c_r] = W^(m' c_r)
+struct X3Tables {
+  cf th[3][32];
+  cf um[7][16];
+};
+
+// every thread of the block (before a barrier)
+MPBP_DI void x3_tables_init(X3Tables& t) {
+  const int i = threadIdx.x;
+  if (i < 96) t.th[i / 32][i % 32] = x3_w128((i / 32 + 1) * (i % 32));
+  else if (i < 96 + 112) t.um[(i - 96) / 16][(i - 96) % 16] = x3_w128(((i - 96) / 16 + 1) * ((i - 96) % 16));
 }
 
 struct X3Tw {
@@ -109,28 +115,64 @@ struct X3Tw {
   cf um[8];   // um[m'] = W^(m' c_r), um[0] unused
 };
 
-// the twiddle words in flight (issued before a barrier, used after it)
-struct X3TwRaw {
-  uint32_t w[16], w4[16];
-};
-
-MPBP_DI void x3_issue_twiddles(uint32_t tt, X3TwRaw& raw) {
-  tmem_ld16(tt, raw.w);
-  tmem_ld16(tt + 16, raw.w4);
+MPBP_DI void x3_twiddles(const X3Tables& t, const X3Roles& r, X3Tw& tw) {
+#pragma unroll
+  for (int h = 1; h < 4; ++h) tw.th[h] = t.th[h - 1][r.kp];
+#pragma unroll
+  for (int m = 1; m < 8; ++m) tw.um[m] = t.um[m - 1][r.cr];
 }
 
-MPBP_DI void x3_finish_twiddles(const X3TwRaw& raw, X3Tw& t) {
-  tmem_wait_ld();
-  const uint32_t(&w)[16] = raw.w;
-  const uint32_t(&w4)[16] = raw.w4;
-#pragma unroll
-  for (int i = 0; i < 10; ++i) {
-    const int k = 2 * i;
-    const cf v = k < 16 ? cf{__uint_as_float(w[k]), __uint_as_float(w[k + 1])}
-                        : cf{__uint_as_float(w4[k - 16]), __uint_as_float(w4[k - 15])};
-    if (i < 3) t.th[i + 1] = v;
-    else t.um[i - 2] = v;
+// the gradient window of a block: strip (peak, first column) and its first row
+struct X3Win {
+  bool ok;
+  int mpk, y, x;
+};
+
+// Add rows [x0, x0 + d) of the window to the accumulator (A7) and, if zero,
+// clear their slots; thread (c, h) takes rows x0 + h + 4 i.  Whole block,
+// converged; ta: the thread's lane at the window's first column.
+MPBP_DI void x3_flush(const FrameArgs& p, const X3Roles& r, const X3Win& w, int x0, int d, uint32_t ta,
+                      bool zero) {
+  const int col = w.y + r.c;
+  const bool cok = col >= 0 && col < p.n2;
+  cf* const base = p.acc + (long long)w.mpk * p.obj_stride + col;
+  const unsigned n1 = (unsigned)p.n1;
+  const int cnt = d > r.h ? (d - r.h + 3) / 4 : 0;   // warp-uniform
+  for (int i0 = 0; i0 < cnt; i0 += 8) {
+    uint32_t v[8][2];
+    sfor<0, 8>([&](auto j_) {
+      constexpr int j = decltype(j_)::value;
+      if (i0 + j < cnt) tmem_ld2(ta + 2u * (uint32_t)((x0 + r.h + 4 * (i0 + j)) & 127), v[j]);
+    });
+    tmem_wait_ld();
+    sfor<0, 8>([&](auto j_) {
+      constexpr int j = decltype(j_)::value;
+      if (i0 + j < cnt) {
+        const int row = x0 + r.h + 4 * (i0 + j);
+        red_add_v2_if(base + (long long)row * p.n2, cf{__uint_as_float(v[j][0]), __uint_as_float(v[j][1])},
+                      cok && (unsigned)row < n1);
+        if (zero) tmem_st2(ta + 2u * (uint32_t)(row & 127), 0u, 0u);
+      }
+    });
   }
+}
+
+// the thread's 32 probe values P(4 n + h, c) (its L1 role) into its TMEM
+// words, in four chunks of 16 words: chunk n mod 4 holds n = n mod 4 + 4 m,
+// m = 0..7, the order in which the last transform's outputs are scattered
+MPBP_DI void x3_probe_to_tmem(const cf* P, const X3Roles& r, uint32_t tp) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    uint32_t w[16];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const cf v = ldg_cf(P + (4 * (4 * j + c) + r.h) * X3Cfg::M + r.c);
+      w[2 * j] = __float_as_uint(v.x);
+      w[2 * j + 1] = __float_as_uint(v.y);
+    }
+    tmem_st16(tp + 16 * c, w);
+  }
+  tmem_wait_st();
 }
 
 // TMA, in two parts on one mbarrier phase: the sqrt(y) tile of frame fr as
@@ -198,7 +240,7 @@ MPBP_DI void x3_fetch(const FrameArgs& p, const X3Roles& r, const FrameRef& fr, 
 template <bool TMA, bool LOSS, bool BG, typename AddLoss>
 MPBP_DI void x3_frame(const FrameArgs& p, const X3Roles& r, const FrameRef& cur, const FrameRef& nxt,
                       AddLoss&& add_loss, BulkState& bs, const TmaMap* tm, cf* buf, float* abuf, uint32_t tp,
-                      uint32_t tt) {
+                      uint32_t ta, const X3Tables& tab, X3Win& win) {
   using C = X3Cfg;
   constexpr int M = C::M, PW = C::PW;
   // the probe values of A2 load from tensor memory while the inputs land
@@ -215,6 +257,7 @@ MPBP_DI void x3_frame(const FrameArgs& p, const X3Roles& r, const FrameRef& cur,
     cp_async_wait_all();
     __syncthreads();
   }
+  tmem_fence_after_sync();   // the previous frame's window updates
   const int dlt = TMA ? (cur.s.y & 1) : 0;   // a tile starts at an even column
 
   // ---- A2 + the 32-point transforms over n (L1)
@@ -222,7 +265,7 @@ MPBP_DI void x3_frame(const FrameArgs& p, const X3Roles& r, const FrameRef& cur,
   tmem_wait_ld();
   sfor<0, 32>([&](auto n_) {
     constexpr int n = decltype(n_)::value;
-    const cf pv = cf{__uint_as_float(w[n / 8][2 * (n % 8)]), __uint_as_float(w[n / 8][2 * (n % 8) + 1])};
+    const cf pv = cf{__uint_as_float(w[n % 4][2 * (n / 4)]), __uint_as_float(w[n % 4][2 * (n / 4) + 1])};
     v[n] = cmul(pv, buf[(4 * n + r.h) * PW + r.c + dlt]);
   });
   fft_line<32>(v);   // Y(h, k', c) in slot brev(k')
@@ -231,15 +274,13 @@ MPBP_DI void x3_frame(const FrameArgs& p, const X3Roles& r, const FrameRef& cur,
     constexpr int k = decltype(k_)::value;
     buf[x3_a(r.h, k, r.c)] = v[ct::brev<32>(k)];
   });
-  X3TwRaw twr;
-  x3_issue_twiddles(tt, twr);   // in flight across the barrier
   __syncthreads();
 
   // ---- L2: twiddle, 4-point over h, 8-point over c_a, twiddle
   cf x[32];
   {
   X3Tw tw;
-  x3_finish_twiddles(twr, tw);   // x[4 h + .. ] layouts as named below
+  x3_twiddles(tab, r, tw);
   sfor<0, 4>([&](auto h_) {
     constexpr int hh = decltype(h_)::value;
     sfor<0, 8>([&](auto a_) {
@@ -344,13 +385,11 @@ MPBP_DI void x3_frame(const FrameArgs& p, const X3Roles& r, const FrameRef& cur,
   // the residual's reads of the sqrt(y) buffer are behind the barrier above:
   // the next frame's tile can land there now
   if constexpr (TMA) x3_fetch_amp_tma(p, r, nxt, abuf, bs, tm);
-  X3TwRaw twr2;
-  x3_issue_twiddles(tt, twr2);   // in flight across the barrier
   __syncthreads();
 
   // ---- L2: twiddle, 8-point over m', 4-point over k'', twiddle
   X3Tw tw;
-  x3_finish_twiddles(twr2, tw);
+  x3_twiddles(tab, r, tw);
   sfor<0, 4>([&](auto k_) {
     constexpr int kk = decltype(k_)::value;
     cf t8[8];
@@ -391,43 +430,67 @@ MPBP_DI void x3_frame(const FrameArgs& p, const X3Roles& r, const FrameRef& cur,
     constexpr int k = decltype(k_)::value;
     v[k] = buf[x3_a(r.h, k, r.c)];
   });
-  __syncthreads();   // both buffers are free
+  // the window moves to this frame's rows: rows that leave it go out
+  if (cur.valid) {
+    const bool slide = win.ok && cur.mpk == win.mpk && cur.s.y == win.y && cur.s.x >= win.x &&
+                       cur.s.x - win.x < X3Cfg::M;
+    if (win.ok) x3_flush(p, r, win, win.x, slide ? cur.s.x - win.x : X3Cfg::M, ta, true);
+    win = X3Win{true, cur.mpk, cur.s.y, cur.s.x};
+  }
+  tmem_wait_st();
+  tmem_fence_before_sync();
+  __syncthreads();   // both buffers are free; the slots the window left are clear
+  tmem_fence_after_sync();
   if constexpr (TMA) {
     x3_fetch_patch_tma(r, nxt, buf, bs, tm);
   } else {
     x3_fetch<false>(p, r, nxt, buf, abuf, bs, tm);
     cp_async_commit();
   }
-  fft_line<32>(v);   // Z(4 n + h, c) in slot brev(n)
-
-  const int col = cur.s.y + r.c;
-  const bool cok = cur.valid && col >= 0 && col < p.n2;
-  int row = cur.s.x + r.h;
-  cf* a = p.acc + cur.mpk * p.obj_stride + (long long)row * p.n2 + col;
-  const long long step = 4LL * p.n2;
-  const unsigned n1 = (unsigned)p.n1;
-  {
-    uint32_t w2[2][16];
-    tmem_ld16(tp, w2[0]);
-    tmem_wait_ld();
-    sfor<0, 4>([&](auto c_) {
-      constexpr int c = decltype(c_)::value;
-      if constexpr (c + 1 < 4) tmem_ld16(tp + 16 * (c + 1), w2[(c + 1) & 1]);
-      sfor<0, 8>([&](auto j_) {
-        constexpr int j = decltype(j_)::value, n = 8 * c + j;
-        const cf pv = cf{__uint_as_float(w2[c & 1][2 * j]), __uint_as_float(w2[c & 1][2 * j + 1])};
-        const cf wv = cmul(pv, v[ct::brev<32>(n)]);
-        red_add_v2_if(a, wv, cok && (unsigned)row < n1);
-        a += step;
-        row += 4;
-      });
-      if constexpr (c + 1 < 4) tmem_wait_ld();
+  if (!cur.valid) return;
+  // the 32-point transform over k' split by frequency, n = 4 m + r:
+  //   Z(n) = sum_j W8^(j m) [W32^(j r) sum_s W4^(s r) v(j + 8 s)],
+  // a radix-4 step, then one 8-point transform per r, whose outputs are
+  // multiplied by the probe (A6) and added into the window's slots of rows
+  // s.x + h + 4 n
+  sfor<0, 8>([&](auto j_) {
+    constexpr int j = decltype(j_)::value;
+    cf t4[4] = {v[j], v[j + 8], v[j + 16], v[j + 24]};
+    fft_line<4>(t4);
+    sfor<0, 4>([&](auto r_) {
+      constexpr int rr = decltype(r_)::value;
+      v[j + 8 * rr] = twmul<j * rr, 32>(t4[ct::brev<4>(rr)]);   // u_r(j) at v[j + 8 r]
     });
-  }
+  });
+  const int b0 = cur.s.x + r.h;   // row of n = 0
+  sfor<0, 4>([&](auto r_) {
+    constexpr int rr = decltype(r_)::value;
+    uint32_t pw[16], o[8][2];
+    tmem_ld16(tp + 16 * rr, pw);   // P at n = 4 m + r, m = 0..7
+    sfor<0, 8>([&](auto m_) {
+      constexpr int m = decltype(m_)::value;
+      tmem_ld2(ta + 2u * (uint32_t)((b0 + 4 * (4 * m + rr)) & 127), o[m]);
+    });
+    cf t8[8];
+    sfor<0, 8>([&](auto j_) { t8[decltype(j_)::value] = v[decltype(j_)::value + 8 * rr]; });
+    fft_line<8>(t8);   // Z(4 m + r) in slot brev(m)
+    tmem_wait_ld();
+    sfor<0, 8>([&](auto m_) {
+      constexpr int m = decltype(m_)::value;
+      const cf pv = cf{__uint_as_float(pw[2 * m]), __uint_as_float(pw[2 * m + 1])};
+      const cf z = t8[ct::brev<8>(m)];
+      const float gx = fmaf(pv.x, z.x, fmaf(-pv.y, z.y, __uint_as_float(o[m][0])));
+      const float gy = fmaf(pv.x, z.y, fmaf(pv.y, z.x, __uint_as_float(o[m][1])));
+      tmem_st2(ta + 2u * (uint32_t)((b0 + 4 * (4 * m + rr)) & 127), __float_as_uint(gx), __float_as_uint(gy));
+    });
+  });
+  tmem_wait_st();
+  tmem_fence_before_sync();
 }
 
-// loss and gradient (LOSS: loss only; BG: with the background of Eq. 2): one
-// frame per block, frames round-robin over a persistent grid; TMA: inputs by tile and bulk copies
+// loss and gradient (LOSS: loss only; BG: with the background of Eq. 2): a
+// persistent grid, block b taking frames [N b / G, N (b + 1) / G) of the
+// order given (p.frames, else 0..N-1); TMA: inputs by tile and bulk copies
 // (tm: the objects' tensor map), else by cp.async.  The probe values of a
 // thread sit in tensor memory and are reloaded when the frame's probe
 // changes: once per block for one probe, per peak for one probe per peak,
@@ -440,6 +503,7 @@ __global__ void __launch_bounds__(X3Cfg::T, 1) frames_x3(const FrameArgs p, cons
   __shared__ double red[C::T / 32];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
+  __shared__ X3Tables tab;
   if (blockIdx.x == 0 && threadIdx.x == 0 && p.arrivals) *p.arrivals = 0u;
   unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
   cf* buf = reinterpret_cast<cf*>(smem);
@@ -449,32 +513,42 @@ __global__ void __launch_bounds__(X3Cfg::T, 1) frames_x3(const FrameArgs p, cons
   const int warp = threadIdx.x >> 5;
   if (warp == 0) tmem_alloc(smem_addr(&tmem_base), C::TMEM_COLS);
   if (TMA && threadIdx.x == 0) mbar_init(bs.bar, 1);
+  x3_tables_init(tab);
   tmem_fence_before_sync();
   __syncthreads();
   tmem_fence_after_sync();
-  // this thread's words: lane 32 (warp mod 4) + lane id; the probe in columns
-  // 64 (warp / 4) .. + 63, the twiddles in 256 + 32 (warp / 4) .. + 19
+  // this thread's lane is 32 (warp mod 4) + lane id = its column c; its probe
+  // words are columns 64 (warp / 4) .. + 63; the window's slot s of column c
+  // is columns 256 + 2 s, + 1 (every warp holding column c reaches them)
   const uint32_t tp = tmem_addr(tmem_base, 32u * (warp & 3), 64u * (warp >> 2));
-  const uint32_t tt = tmem_addr(tmem_base, 32u * (warp & 3), 256u + 32u * (warp >> 2));
-  x3_twiddles_to_tmem(r, tt);
+  const uint32_t ta = tmem_addr(tmem_base, 32u * (warp & 3), C::ACC_COL);
+  if constexpr (!LOSS) {
+    // clear the window: warp w the slots 32 (w / 4) .. + 31 of its lanes
+    const uint32_t z[16] = {};
+    sfor<0, 4>([&](auto k_) { tmem_st16(ta + 64u * (warp >> 2) + 16u * decltype(k_)::value, z); });
+    tmem_wait_st();
+    tmem_fence_before_sync();   // ordered before the first frame's barriers
+  }
+  X3Win win{false, 0, 0, 0};
   const cf* tp_src = nullptr;   // the probe held in tensor memory (block-uniform)
   double lsum = 0.0;
-  int it = blockIdx.x;
-  FrameRef cur = frame_ref(p, it);
+  const int lo = (int)((long long)p.nframes * blockIdx.x / gridDim.x);
+  const int hi = (int)((long long)p.nframes * (blockIdx.x + 1) / gridDim.x);
+  const FrameRef none = frame_ref(p, p.nframes);   // not valid: nothing to fetch
+  FrameRef cur = lo < hi ? frame_ref(p, lo) : none;
   x3_fetch<TMA>(p, r, cur, buf, abuf, bs, &tm);
   if constexpr (!TMA) cp_async_commit();
-  for (; it < p.nframes; it += gridDim.x) {
-    const FrameRef nxt = frame_ref(p, it + gridDim.x);
+  for (int it = lo; it < hi; ++it) {
+    const FrameRef nxt = it + 1 < hi ? frame_ref(p, it + 1) : none;
     {
       const cf* P = frame_probe(p, cur, M * M);
       if (P != tp_src) {
-        // the probe values of this thread's L1 role: P(4 n + h, c)
-        T4Group<M> g4 = T4Group<M>::make(threadIdx.x, smem);
-        t4_probe_to_tmem<M>(P, g4, tp);
+        x3_probe_to_tmem(P, r, tp);
         tp_src = P;
       }
     }
-    x3_frame<TMA, LOSS, BG>(p, r, cur, nxt, [&](float fl) { lsum += (double)fl; }, bs, &tm, buf, abuf, tp, tt);
+    x3_frame<TMA, LOSS, BG>(p, r, cur, nxt, [&](float fl) { lsum += (double)fl; }, bs, &tm, buf, abuf, tp, ta,
+                            tab, win);
     if (TMA && !bs.ok) {
       if (threadIdx.x == 0) atomicOr(p.err, kErrTimeout);
       break;
@@ -482,6 +556,13 @@ __global__ void __launch_bounds__(X3Cfg::T, 1) frames_x3(const FrameArgs p, cons
     cur = nxt;
   }
   cp_async_wait_all();
+  if constexpr (!LOSS) {
+    if (bs.ok && win.ok) {   // what is left of the window
+      __syncthreads();
+      tmem_fence_after_sync();
+      x3_flush(p, r, win, win.x, M, ta, false);
+    }
+  }
   const double tot = block_sum_d<C::T>(lsum, red);
   if (threadIdx.x == 0) p.loss_part[blockIdx.x] = tot;
   tmem_fence_before_sync();

@@ -59,6 +59,7 @@ struct mpbp_ctx {
   cf* acc = nullptr;
   cf* probe = nullptr;
   int2* scan = nullptr;
+  int* strip_order = nullptr;   // [nframes] frames by peak, scan column, scan row
   float* aT = nullptr;
   float* bgT = nullptr;
   double* loss_part = nullptr;
@@ -205,10 +206,16 @@ int frames_grid_fft(const mpbp_ctx* c, long long nframes) {
 cudaError_t launch_frames(const mpbp_ctx* c, const FrameArgs& fa, int grid, cudaStream_t s) {
   if (c->precision == MPBP_PRECISION_TC_SPLIT16)
     return tc_launch(c->M, fa, c->tc_w, grid, s, c->test_tx_extra != 0);
-  if (!c->tile_grad || fa.O != c->O) return frames_launch(c->M, fa, grid, false, s, nullptr, c->fft_schedule);
+  FrameArgs f2 = fa;
+  // every frame of the context: the exchange kernel at M = 128 takes them in
+  // column strips (any order gives the same sums up to rounding)
+  if (c->M == 128 && c->fft_schedule == kLayoutExchange && !fa.frames && fa.frame0 == 0 &&
+      fa.nframes == c->nframes && fa.aT == c->aT)
+    f2.frames = c->strip_order;
+  if (!c->tile_grad || fa.O != c->O) return frames_launch(c->M, f2, grid, false, s, nullptr, c->fft_schedule);
   TmaMap tm = c->tm_grad;
   tm.tx_extra = c->test_tx_extra;
-  return frames_launch(c->M, fa, grid, false, s, &tm, c->fft_schedule);
+  return frames_launch(c->M, f2, grid, false, s, &tm, c->fft_schedule);
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -476,6 +483,7 @@ mpbp_status mpbp_create(const mpbp_problem* pr, mpbp_ctx** out) {
   size_t oAcc = cv.take<cf>(c->npix * c->D);
   size_t oProbe = cv.take<cf>(Dp * mm);
   size_t oScan = cv.take<int2>(c->J);
+  size_t oOrd = cv.take<int>(c->nframes);
   size_t oAT = cv.take<float>(c->nframes * mm);
   size_t oLP = cv.take<double>(max_frames_grid);
   size_t oPart = cv.take<double>((size_t)c->finish_grid * (c->D + 3));
@@ -503,6 +511,7 @@ mpbp_status mpbp_create(const mpbp_problem* pr, mpbp_ctx** out) {
   c->acc = reinterpret_cast<cf*>(b + oAcc);
   c->probe = reinterpret_cast<cf*>(b + oProbe);
   c->scan = reinterpret_cast<int2*>(b + oScan);
+  c->strip_order = reinterpret_cast<int*>(b + oOrd);
   c->aT = reinterpret_cast<float*>(b + oAT);
   c->loss_part = reinterpret_cast<double*>(b + oLP);
   c->part = reinterpret_cast<double*>(b + oPart);
@@ -523,7 +532,19 @@ mpbp_status mpbp_create(const mpbp_problem* pr, mpbp_ctx** out) {
 
   std::vector<int2> sc(c->J);
   for (int j = 0; j < c->J; ++j) sc[j] = make_int2(pr->scan[2 * j], pr->scan[2 * j + 1]);
+  // column strips: a block of the M = 128 exchange kernel takes a contiguous
+  // run of this order, so that its successive frames overlap in rows
+  std::vector<int> ord((size_t)c->nframes);
+  for (long long f = 0; f < c->nframes; ++f) ord[(size_t)f] = (int)f;
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+    const int pa = a / c->J, pb = b / c->J;
+    const int2 sa = sc[a - pa * c->J], sb = sc[b - pb * c->J];
+    if (pa != pb) return pa < pb;
+    if (sa.y != sb.y) return sa.y < sb.y;
+    return sa.x < sb.x;
+  });
   if (cudaMemcpy(c->scan, sc.data(), sizeof(int2) * c->J, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->strip_order, ord.data(), sizeof(int) * ord.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(c->acc, 0, sizeof(cf) * c->npix * c->D) != cudaSuccess ||
       cudaMemset(c->err, 0, sizeof(int)) != cudaSuccess ||
       cudaMemset(c->arrivals, 0, sizeof(unsigned)) != cudaSuccess ||
@@ -1881,9 +1902,11 @@ mpbp_status mpbp_sync_status(mpbp_ctx* c, void* stream) {
   int h = 0;
   MPBP_CUDA(c, cudaMemcpy(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost));
   if (h) MPBP_CUDA(c, cudaMemset(c->err, 0, sizeof(int)));
+  // a wait that ran out leaves the evaluation's results undefined (a
+  // non-finite loss among them), so it is reported ahead of the loss check
   if (h & kErrBounds) return fail(c, MPBP_ERR_BOUNDS, "frame index out of range");
-  if (h & kErrNonfinite) return fail(c, MPBP_ERR_NONFINITE, "non-finite loss");
   if (h & kErrTimeout) return fail(c, MPBP_ERR_TIMEOUT, "a bounded wait on the GPU ran out");
+  if (h & kErrNonfinite) return fail(c, MPBP_ERR_NONFINITE, "non-finite loss");
   return MPBP_OK;
 }
 

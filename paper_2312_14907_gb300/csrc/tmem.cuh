@@ -51,6 +51,16 @@ MPBP_DI void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
       : "memory");
 }
 
+// 2 consecutive columns (one complex value) of the thread's lane (whole
+// warp, converged; taddr's column even)
+MPBP_DI void tmem_ld2(uint32_t taddr, uint32_t (&v)[2]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(v[0]), "=r"(v[1]) : "r"(taddr));
+}
+
+MPBP_DI void tmem_st2(uint32_t taddr, uint32_t v0, uint32_t v1) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1,%2};" ::"r"(taddr), "r"(v0), "r"(v1) : "memory");
+}
+
 // the thread's earlier tcgen05.ld / tcgen05.st have completed
 MPBP_DI void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 MPBP_DI void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
