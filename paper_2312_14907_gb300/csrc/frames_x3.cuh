@@ -274,13 +274,13 @@ MPBP_DI void x3_frame(const FrameArgs& p, const X3Roles& r, const FrameRef& cur,
     constexpr int k = decltype(k_)::value;
     buf[x3_a(r.h, k, r.c)] = v[ct::brev<32>(k)];
   });
-  __syncthreads();
-
-  // ---- L2: twiddle, 4-point over h, 8-point over c_a, twiddle
   cf x[32];
   {
   X3Tw tw;
-  x3_twiddles(tab, r, tw);
+  x3_twiddles(tab, r, tw);   // the table is constant: read ahead of the barrier
+  __syncthreads();
+
+  // ---- L2: twiddle, 4-point over h, 8-point over c_a, twiddle
   sfor<0, 4>([&](auto h_) {
     constexpr int hh = decltype(h_)::value;
     sfor<0, 8>([&](auto a_) {
@@ -385,11 +385,11 @@ MPBP_DI void x3_frame(const FrameArgs& p, const X3Roles& r, const FrameRef& cur,
   // the residual's reads of the sqrt(y) buffer are behind the barrier above:
   // the next frame's tile can land there now
   if constexpr (TMA) x3_fetch_amp_tma(p, r, nxt, abuf, bs, tm);
+  X3Tw tw;
+  x3_twiddles(tab, r, tw);
   __syncthreads();
 
   // ---- L2: twiddle, 8-point over m', 4-point over k'', twiddle
-  X3Tw tw;
-  x3_twiddles(tab, r, tw);
   sfor<0, 4>([&](auto k_) {
     constexpr int kk = decltype(k_)::value;
     cf t8[8];
@@ -538,8 +538,13 @@ __global__ void __launch_bounds__(X3Cfg::T, 1) frames_x3(const FrameArgs p, cons
   FrameRef cur = lo < hi ? frame_ref(p, lo) : none;
   x3_fetch<TMA>(p, r, cur, buf, abuf, bs, &tm);
   if constexpr (!TMA) cp_async_commit();
+  // frame indices are read one frame ahead of their scan positions, so that
+  // neither global load waits on the other
+  int f1 = lo + 1 < hi ? frame_at(p, lo + 1) : 0;
   for (int it = lo; it < hi; ++it) {
-    const FrameRef nxt = it + 1 < hi ? frame_ref(p, it + 1) : none;
+    const int f2 = it + 2 < hi ? frame_at(p, it + 2) : 0;
+    const FrameRef nxt = it + 1 < hi ? frame_ref_of(p, f1) : none;
+    f1 = f2;
     {
       const cf* P = frame_probe(p, cur, M * M);
       if (P != tp_src) {
