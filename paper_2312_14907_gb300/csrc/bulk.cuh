@@ -79,6 +79,19 @@ MPBP_DI void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t b
                : "memory");
 }
 
+// a contiguous copy of data read once per evaluation (the frames' sqrt(y)):
+// as bulk_load, with an L2 evict-first policy, so that the stream does not
+// push the objects and the gradient accumulator out of L2
+MPBP_DI void bulk_load_stream(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar), "l"(pol)
+      : "memory");
+}
+
 // generic-proxy accesses of shared memory (ordered before this point by a
 // barrier) before the asynchronous copies that follow
 MPBP_DI void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }

@@ -130,7 +130,7 @@ MPBP_DI void t4_fetch(const FrameArgs& p, const T4Group<M>& g, const FrameRef& r
         const float* src = p.aT + (long long)r.f * M * M;
         const uint32_t dst = smem_addr(g.abuf);
 #pragma unroll 1
-        for (int b = 0; b < M / C::AB; ++b) bulk_load(dst + b * C::ABAND, src + b * C::AB * M, kBand, bs.bar);
+        for (int b = 0; b < M / C::AB; ++b) bulk_load_stream(dst + b * C::ABAND, src + b * C::AB * M, kBand, bs.bar);
       }
     }
   } else {

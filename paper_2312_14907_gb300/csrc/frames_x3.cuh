@@ -186,7 +186,7 @@ MPBP_DI void x3_fetch_amp_tma(const FrameArgs& p, const X3Roles& r, const FrameR
     constexpr uint32_t kAmp = M * M * (uint32_t)sizeof(float);
     fence_async_smem();
     mbar_arrive_tx(bs.bar, (fr.valid ? kPatch + kAmp : 0u) + tm->tx_extra);
-    if (fr.valid) bulk_load(smem_addr(abuf), p.aT + (long long)fr.f * M * M, kAmp, bs.bar);
+    if (fr.valid) bulk_load_stream(smem_addr(abuf), p.aT + (long long)fr.f * M * M, kAmp, bs.bar);
   }
 }
 
@@ -214,7 +214,7 @@ MPBP_DI void x3_fetch(const FrameArgs& p, const X3Roles& r, const FrameRef& fr, 
       mbar_arrive_tx(bs.bar, (fr.valid ? kPatch + kAmp : 0u) + tm->tx_extra);
       if (fr.valid) {
         tile_load_3d(smem_addr(buf), &tm->map, fr.s.y - (fr.s.y & 1), fr.s.x, fr.mpk, bs.bar);
-        bulk_load(smem_addr(abuf), p.aT + (long long)fr.f * M * M, kAmp, bs.bar);
+        bulk_load_stream(smem_addr(abuf), p.aT + (long long)fr.f * M * M, kAmp, bs.bar);
       }
     }
   } else {
