@@ -151,6 +151,28 @@ def test_m128_steady_state_matches_oracle(n2, tiles, schedule):
     p.sync_status()
 
 
+@pytest.mark.parametrize("n2,tiles,step", [(200, 3, 6), (199, 0, 5)])
+def test_m64_steady_state_matches_oracle(n2, tiles, step):
+    """The M = 64 gradient kernel runs four blocks per SM (608 blocks): 1,352
+    frames (26 x 26 scan, 2 peaks) give every block two or three frames, so
+    each prefetches the next frame's inputs, reuses its buffers and flips its
+    barrier phase.  Then with one block per SM (about nine frames a block),
+    and through a frame list.  Element by element against the oracle, tile
+    copies (even n2) and cp.async (odd n2)."""
+    spec, scan = custom_spec(170, 64, 26, step, npeaks=2, offset=-6, n2=n2)
+    case = Case(spec, scan=scan, state="perturbed")
+    p, x = _gpu(case)
+    info = p.info()
+    assert info["tile_copies"] == tiles, info
+    assert spec.nframes > 2 * info["frames_grid"], (spec.nframes, info)
+    _check_loss_grad(case, p.loss_grad(*x))
+    p.set_schedule(1)
+    _check_loss_grad(case, p.loss_grad(*x))
+    frames = np.random.default_rng(64).permutation(spec.nframes)[:300].astype(np.int32)
+    _check_loss_grad(case, p.loss_grad(*x, frames=torch.from_numpy(frames).cuda()), frames=frames)
+    p.sync_status()
+
+
 def test_frame_subset_matches_oracle():
     spec, scan = custom_spec(64, 32, 6, 6, npeaks=3, offset=0)
     case = Case(spec, scan=scan, state="perturbed")
