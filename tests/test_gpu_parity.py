@@ -173,6 +173,29 @@ def test_m64_steady_state_matches_oracle(n2, tiles, step):
     p.sync_status()
 
 
+@pytest.mark.parametrize("n2", [256, 255])
+def test_m128_irregular_scan_matches_oracle(n2):
+    """Scan positions off any grid: 173 seeded positions (some repeated, some
+    overhanging every edge) and 2 peaks, 346 frames, so that every block of
+    the 152-block M = 128 grid takes two or three frames of the column-strip
+    order.  A block's gradient window then moves by arbitrary row steps,
+    repeats a position (a step of 0), jumps by more than a window, and
+    changes column or peak between frames; element by element against the
+    oracle, through tile copies (even n2) and cp.async (odd n2)."""
+    rng = np.random.default_rng(1701)
+    spec, _ = custom_spec(256, 128, 13, 10, npeaks=2, offset=-6, n2=n2)
+    pos = np.stack([rng.integers(-40, 200, 150), rng.integers(-40, n2 - 88, 150)], axis=1)
+    # a few columns with several rows each: strips whose steps vary
+    cols = rng.integers(-20, n2 - 100, 4)
+    extra = np.array([[r, c] for c in cols for r in sorted(rng.integers(-30, 180, 5))])
+    scan = np.concatenate([pos, extra, pos[:3]]).astype(np.int32)
+    case = Case(spec, scan=scan, state="perturbed")
+    p, x = _gpu(case)
+    assert case.oracle.nframes > 2 * p.info()["frames_grid"]
+    _check_loss_grad(case, p.loss_grad(*x))
+    p.sync_status()
+
+
 def test_frame_subset_matches_oracle():
     spec, scan = custom_spec(64, 32, 6, 6, npeaks=3, offset=0)
     case = Case(spec, scan=scan, state="perturbed")
