@@ -378,7 +378,9 @@ def run_gpu(args):
             torch.empty(spec.npeaks, dtype=torch.float64).pin_memory())
     n_e2e = max(3, min(args.steps, 10))
 
-    def e2e_rate(yhost):
+    call_ms = {}
+
+    def e2e_rate(yhost, key):
         for _ in range(2):
             prob.loss_grad_host(rh, uh, ah, y=yhost, out=outs)
         if world > 1:
@@ -390,9 +392,21 @@ def run_gpu(args):
             t1 = time.perf_counter()
             prob.loss_grad_host(rh, uh, ah, y=yhost, out=outs)
             ts.append(time.perf_counter() - t1)
+        call_ms[key] = {"min": min(ts) * 1e3, "median": statistics.median(ts) * 1e3, "max": max(ts) * 1e3,
+                        "calls": [round(t * 1e3, 2) for t in ts]}
         return replicas.max_over_ranks(sum(ts), device="cuda")
 
-    e2e_s = e2e_rate(yh)
+    e2e_s = e2e_rate(yh, "f32")
+    # the host link's own rate in this run: the same bytes of y as one plain
+    # copy from pinned memory into the (identical) device data tensor
+    link_ts = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        yd.copy_(yh, non_blocking=True)
+        torch.cuda.synchronize()
+        link_ts.append(time.perf_counter() - t1)
+    link_gbs = yh.numel() * 4 / min(link_ts) / 1e9
     h2d = yh.numel() * 4 + rh.numel() * 4 + uh.numel() * 4 + ah.numel() * 4
     d2h = 8 + outs[1].numel() * 4 + outs[2].numel() * 4 + outs[3].numel() * 8
     # the same call with the photon counts as 16-bit integers (exact: the
@@ -400,7 +414,7 @@ def run_gpu(args):
     assert bool((yd == torch.round(yd)).all()) and float(yd.max()) < 32768
     yh16 = yd.to(torch.int16).view(torch.uint16).cpu().pin_memory()
     del yh
-    e2e16_s = e2e_rate(yh16)
+    e2e16_s = e2e_rate(yh16, "u16")
     del yh16
     h2d16 = spec.nframes * spec.m ** 2 * 2 + rh.numel() * 4 + uh.numel() * 4 + ah.numel() * 4
     e2e_frames = spec.nframes * n_e2e * world
@@ -456,10 +470,15 @@ def run_gpu(args):
                      "hbm_frac": (spec.nframes * 4 * spec.m ** 2 / (kavg_ms / 1e3) / 1e9) / pk["hbm_gbs"]},
         "e2e": {"value": e2e_frames / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h),
-                "call": "mpbp_loss_grad_host (host y, rho, u, alpha in; loss and gradients out)"},
+                "call": "mpbp_loss_grad_host (host y, rho, u, alpha in; loss and gradients out)",
+                "link_h2d_gbs": link_gbs,
+                "frac_of_link": (h2d * n_e2e / e2e_s / 1e9) / link_gbs,
+                "link_src": "one pinned copy of the same y bytes in this run (torch copy_, best of 3)",
+                "ms_per_call": call_ms["f32"]},
         "e2e_counts16": {"value": e2e_frames / e2e16_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d16),
                          "d2h_bytes_per_step": int(d2h),
-                         "call": "mpbp_loss_grad_host_counts16 (y as 16-bit photon counts; otherwise as e2e)"},
+                         "call": "mpbp_loss_grad_host_counts16 (y as 16-bit photon counts; otherwise as e2e)",
+                         "ms_per_call": call_ms["u16"]},
         "gpu_launches": info["launches_step"] * args.steps,
         "clocks": clk.summary(),
         "wall_s": wall,
