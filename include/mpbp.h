@@ -109,6 +109,8 @@ typedef struct {
                                  forward kernel (none when a row of O is not a
                                  multiple of 16 bytes, i.e. odd n2: cp.async)  */
   int32_t fft_schedule;       /* MPBP_FFT_* in use (frame side 128)            */
+  int32_t deterministic;      /* 1: the gradient sums are bitwise reproducible
+                                 (mpbp_set_deterministic)                     */
 } mpbp_info;
 
 /* How the 128-point lines of the frame side M = 128 are split over the four
@@ -416,6 +418,28 @@ mpbp_status mpbp_loss_grad_noalloc(const mpbp_problem *problem, const float *pro
  * Eq. 2; other frame sides ignore it).  Host-side only; a captured step keeps
  * the schedule of its capture.  MPBP_ERR_INVALID_ARG for an unknown value. */
 mpbp_status mpbp_set_fft_schedule(mpbp_ctx *ctx, int32_t schedule);
+
+/* Deterministic gradient (the A7 sums of Eq. 11 in a fixed order).  With on
+ * != 0 the frame kernel's gradient windows write back into per-block pieces
+ * (a run of frames of one scan column strip) with plain stores, and a second
+ * kernel sums, for every object pixel, the pieces covering it in a fixed
+ * order, in place of red.global.add into one accumulator: loss, g_rho, g_u
+ * and g_alpha are then the same bits on every call with the same inputs and
+ * schedule (with the atomic sums they agree only to rounding).  Costs a
+ * device workspace of about 8 x 128 x (rows spanned by a strip + 128) bytes
+ * per piece (about 1 GB for 87,846 frames of 128 x 128 on a 1024^2 object),
+ * allocated here and kept while the context lives, and the clearing and
+ * summing of it on each evaluation.  Needs frame side 128 on FP32 FFTs with
+ * the exchange schedule and tile copies (rows of O a multiple of 16 bytes):
+ * else MPBP_ERR_UNSUPPORTED.  While on, evaluations over a frame list
+ * (mpbp_loss_grad with frames, mpbp_adam_step minibatches), the host-buffer
+ * calls, mpbp_loss_grad_batched and mpbp_autotune return
+ * MPBP_ERR_UNSUPPORTED, and so do mpbp_set_precision / mpbp_set_fft_schedule
+ * to another arithmetic or schedule.  mpbp_loss_grad over every frame,
+ * mpbp_loss_grad_phases, mpbp_step and its captured replay are
+ * deterministic.  Synchronous (builds its plan on the host); a later
+ * mpbp_set_schedule rebuilds it.  on == 0 returns to the atomic sums. */
+mpbp_status mpbp_set_deterministic(mpbp_ctx *ctx, int32_t on);
 
 /* Overrides the fused frame kernel's schedule: resident blocks per SM used to
  * size its persistent grid (0 = occupancy maximum).  Host-side only. */

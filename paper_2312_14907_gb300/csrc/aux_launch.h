@@ -65,5 +65,10 @@ cudaError_t launch_finish(const FinishArgs& a, const ReduceArgs& r, int grid, cu
 // loss = fixed-order sum of n per-block loss partials (one warp); err gets
 // the non-finite bit
 cudaError_t launch_loss_reduce(const double* part, long long n, double* loss, int* err, cudaStream_t s);
+// the deterministic gradient: acc [D][n1][n2] = per pixel, the fixed-order
+// sum of the plan's pieces covering it (pieces w columns wide; plan in
+// device memory)
+cudaError_t launch_det_reduce(const DetPlan* plan, cf* acc, int D, int n1, int n2, int w, int num_sms,
+                              cudaStream_t s);
 
 }  // namespace mpbp

@@ -122,21 +122,31 @@ MPBP_DI void x3_twiddles(const X3Tables& t, const X3Roles& r, X3Tw& tw) {
   for (int m = 1; m < 8; ++m) tw.um[m] = t.um[m - 1][r.cr];
 }
 
-// the gradient window of a block: strip (peak, first column) and its first row
+// the gradient window of a block: strip (peak, first column) and its first
+// row; with a deterministic plan, the block's current piece
 struct X3Win {
   bool ok;
   int mpk, y, x;
+  int piece;
 };
 
 // Add rows [x0, x0 + d) of the window to the accumulator (A7) and, if zero,
 // clear their slots; thread (c, h) takes rows x0 + h + 4 i.  Whole block,
-// converged; ta: the thread's lane at the window's first column.
+// converged; ta: the thread's lane at the window's first column.  With a
+// deterministic plan the rows go to the block's current piece instead, by
+// plain loads and stores (the piece has no other writer, and successive
+// write-backs of a row are separated by block barriers).
 MPBP_DI void x3_flush(const FrameArgs& p, const X3Roles& r, const X3Win& w, int x0, int d, uint32_t ta,
                       bool zero) {
   const int col = w.y + r.c;
   const bool cok = col >= 0 && col < p.n2;
   cf* const base = p.acc + (long long)w.mpk * p.obj_stride + col;
   const unsigned n1 = (unsigned)p.n1;
+  cf* pbase = nullptr;   // the piece's column c at row 0
+  if (p.det) {
+    const DetPiece pc = p.det->pieces[w.piece];
+    pbase = p.det->pool + pc.off - (long long)pc.row0 * X3Cfg::M + r.c;
+  }
   const int cnt = d > r.h ? (d - r.h + 3) / 4 : 0;   // warp-uniform
   for (int i0 = 0; i0 < cnt; i0 += 8) {
     uint32_t v[8][2];
@@ -149,8 +159,14 @@ MPBP_DI void x3_flush(const FrameArgs& p, const X3Roles& r, const X3Win& w, int 
       constexpr int j = decltype(j_)::value;
       if (i0 + j < cnt) {
         const int row = x0 + r.h + 4 * (i0 + j);
-        red_add_v2_if(base + (long long)row * p.n2, cf{__uint_as_float(v[j][0]), __uint_as_float(v[j][1])},
-                      cok && (unsigned)row < n1);
+        const cf g = cf{__uint_as_float(v[j][0]), __uint_as_float(v[j][1])};
+        if (pbase) {
+          cf* q = pbase + (long long)row * X3Cfg::M;
+          const cf o = *q;
+          *q = cf{o.x + g.x, o.y + g.y};
+        } else {
+          red_add_v2_if(base + (long long)row * p.n2, g, cok && (unsigned)row < n1);
+        }
         if (zero) tmem_st2(ta + 2u * (uint32_t)(row & 127), 0u, 0u);
       }
     });
@@ -435,7 +451,9 @@ MPBP_DI void x3_frame(const FrameArgs& p, const X3Roles& r, const FrameRef& cur,
     const bool slide = win.ok && cur.mpk == win.mpk && cur.s.y == win.y && cur.s.x >= win.x &&
                        cur.s.x - win.x < X3Cfg::M;
     if (win.ok) x3_flush(p, r, win, win.x, slide ? cur.s.x - win.x : X3Cfg::M, ta, true);
-    win = X3Win{true, cur.mpk, cur.s.y, cur.s.x};
+    // a new strip starts the block's next piece (the host splits them there)
+    const bool strip = !win.ok || cur.mpk != win.mpk || cur.s.y != win.y;
+    win = X3Win{true, cur.mpk, cur.s.y, cur.s.x, win.piece + (strip ? 1 : 0)};
   }
   tmem_wait_st();
   tmem_fence_before_sync();
@@ -529,7 +547,7 @@ __global__ void __launch_bounds__(X3Cfg::T, 1) frames_x3(const FrameArgs p, cons
     tmem_wait_st();
     tmem_fence_before_sync();   // ordered before the first frame's barriers
   }
-  X3Win win{false, 0, 0, 0};
+  X3Win win{false, 0, 0, 0, p.det ? p.det->block_piece0[blockIdx.x] - 1 : 0};
   const cf* tp_src = nullptr;   // the probe held in tensor memory (block-uniform)
   double lsum = 0.0;
   const int lo = (int)((long long)p.nframes * blockIdx.x / gridDim.x);

@@ -133,6 +133,17 @@ struct mpbp_ctx {
   cudaGraphExec_t step_exec = nullptr;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
   size_t ev_used = 0;
+  // the deterministic gradient (mpbp_set_deterministic): host copies of the
+  // scan and of the column-strip order, and the plan for grid det_grid
+  std::vector<int2> scan_h;
+  std::vector<int> order_h;
+  bool det = false;
+  int det_grid = 0;
+  void* det_meta = nullptr;   // pieces, block starts, column lists, the DetPlan
+  cf* det_pool = nullptr;
+  size_t det_pool_elems = 0, det_pool_cap = 0;
+  const DetPlan* det_plan = nullptr;
+  std::vector<void*> det_old;   // earlier plans' buffers (a captured step may use them)
   std::string last_error;
 };
 
@@ -202,16 +213,129 @@ int frames_grid_fft(const mpbp_ctx* c, long long nframes) {
   return (int)std::max<long long>(g, 1);
 }
 
+// a launch over every frame of the context from its own data and objects
+bool full_launch(const mpbp_ctx* c, const FrameArgs& fa) {
+  return !fa.frames && fa.frame0 == 0 && fa.nframes == c->nframes && fa.aT == c->aT && fa.O == c->O;
+}
+
+// The deterministic gradient's plan for a grid of `grid` blocks (host work
+// and synchronous uploads: called outside any stream capture).  Block b
+// takes positions [N b / G, N (b + 1) / G) of the strip order; its run is cut
+// into pieces where the peak or the first column changes, as the kernel's
+// window does.  A piece spans its frames' rows plus a frame, 128 columns.
+mpbp_status det_prepare(mpbp_ctx* c, int grid) {
+  if (c->det_grid == grid && c->det_plan) return MPBP_OK;
+  constexpr int W = 128;
+  const long long N = c->nframes;
+  std::vector<DetPiece> pieces;
+  std::vector<int> b0(grid);
+  for (int b = 0; b < grid; ++b) {
+    const long long lo = N * b / grid, hi = N * (b + 1) / grid;
+    b0[b] = (int)pieces.size();
+    for (long long it = lo; it < hi; ++it) {
+      const int f = c->order_h[(size_t)it];
+      const int m = f / c->J;
+      const int2 sp = c->scan_h[f - m * c->J];
+      if (it == lo || m != pieces.back().mpk || sp.y != pieces.back().y) {
+        pieces.push_back(DetPiece{0, sp.x, sp.x, m, sp.y});   // rows: the last row start, for now
+      } else {
+        DetPiece& pc = pieces.back();
+        pc.row0 = std::min(pc.row0, sp.x);
+        pc.rows = std::max(pc.rows, sp.x);
+      }
+    }
+  }
+  long long off = 0;
+  for (DetPiece& pc : pieces) {
+    pc.rows = pc.rows - pc.row0 + W;
+    pc.off = off;
+    off += (long long)pc.rows * W;
+  }
+  // per (peak, column): the pieces that cover it, in piece order
+  const long long ncol = (long long)c->D * c->n2;
+  std::vector<int> cnt((size_t)ncol + 1, 0);
+  for (const DetPiece& pc : pieces)
+    for (int col = std::max(pc.y, 0); col < std::min(pc.y + W, c->n2); ++col) cnt[(size_t)(pc.mpk * (long long)c->n2 + col + 1)]++;
+  for (long long i = 0; i < ncol; ++i) cnt[(size_t)i + 1] += cnt[(size_t)i];
+  std::vector<int> lists((size_t)cnt[(size_t)ncol]);
+  {
+    std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+    for (size_t p = 0; p < pieces.size(); ++p) {
+      const DetPiece& pc = pieces[p];
+      for (int col = std::max(pc.y, 0); col < std::min(pc.y + W, c->n2); ++col)
+        lists[(size_t)fill[(size_t)(pc.mpk * (long long)c->n2 + col)]++] = (int)p;
+    }
+  }
+  // device copies: one block of tables, and the pool (kept if large enough)
+  Carver cv;
+  const size_t oP = cv.take<DetPiece>(pieces.size());
+  const size_t oB = cv.take<int>(b0.size());
+  const size_t oS = cv.take<int>(cnt.size());
+  const size_t oL = cv.take<int>(std::max<size_t>(lists.size(), 1));
+  const size_t oD = cv.take<DetPlan>(1);
+  if (c->det_meta) c->det_old.push_back(c->det_meta);
+  c->det_meta = nullptr;
+  c->det_plan = nullptr;
+  c->det_grid = 0;
+  if (cudaMalloc(&c->det_meta, cv.off) != cudaSuccess) {
+    cudaGetLastError();
+    c->det_meta = nullptr;
+    return fail(c, MPBP_ERR_OOM, "deterministic gradient: tables");
+  }
+  if ((size_t)off > c->det_pool_cap) {
+    if (c->det_pool) c->det_old.push_back(c->det_pool);
+    c->det_pool = nullptr;
+    c->det_pool_cap = 0;
+    if (cudaMalloc(&c->det_pool, sizeof(cf) * (size_t)off) != cudaSuccess) {
+      cudaGetLastError();
+      c->det_pool = nullptr;
+      return fail(c, MPBP_ERR_OOM, "deterministic gradient: pieces");
+    }
+    c->det_pool_cap = (size_t)off;
+  }
+  c->det_pool_elems = (size_t)off;
+  char* m = static_cast<char*>(c->det_meta);
+  DetPlan plan{c->det_pool, reinterpret_cast<DetPiece*>(m + oP), reinterpret_cast<int*>(m + oB),
+               reinterpret_cast<int*>(m + oS), reinterpret_cast<int*>(m + oL)};
+  if (cudaMemcpy(m + oP, pieces.data(), sizeof(DetPiece) * pieces.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(m + oB, b0.data(), sizeof(int) * b0.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(m + oS, cnt.data(), sizeof(int) * cnt.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      (!lists.empty() &&
+       cudaMemcpy(m + oL, lists.data(), sizeof(int) * lists.size(), cudaMemcpyHostToDevice) != cudaSuccess) ||
+      cudaMemcpy(m + oD, &plan, sizeof(plan), cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(c, MPBP_ERR_CUDA, "deterministic gradient: upload");
+  c->det_plan = reinterpret_cast<const DetPlan*>(m + oD);
+  c->det_grid = grid;
+  return MPBP_OK;
+}
+
 // the gradient-mode frame kernel of the context's precision
 cudaError_t launch_frames(const mpbp_ctx* c, const FrameArgs& fa, int grid, cudaStream_t s) {
-  if (c->precision == MPBP_PRECISION_TC_SPLIT16)
+  if (c->det) {
+    // only launches over every frame with the plan's grid get here (the
+    // entry points refuse the others); anything else is a library bug
+    if (!full_launch(c, fa) || grid != c->det_grid || !c->det_plan || c->precision != MPBP_PRECISION_FP32 ||
+        c->fft_schedule != kLayoutExchange || !c->tile_grad)
+      return cudaErrorNotSupported;
+  } else if (c->precision == MPBP_PRECISION_TC_SPLIT16) {
     return tc_launch(c->M, fa, c->tc_w, grid, s, c->test_tx_extra != 0);
+  }
   FrameArgs f2 = fa;
   // every frame of the context: the exchange kernel at M = 128 takes them in
   // column strips (any order gives the same sums up to rounding)
   if (c->M == 128 && c->fft_schedule == kLayoutExchange && !fa.frames && fa.frame0 == 0 &&
       fa.nframes == c->nframes && fa.aT == c->aT)
     f2.frames = c->strip_order;
+  if (c->det) {
+    f2.det = c->det_plan;
+    cudaError_t e = cudaMemsetAsync(c->det_pool, 0, sizeof(cf) * c->det_pool_elems, s);
+    if (e != cudaSuccess) return e;
+    TmaMap tm = c->tm_grad;
+    tm.tx_extra = c->test_tx_extra;
+    e = frames_launch(c->M, f2, grid, false, s, &tm, c->fft_schedule);
+    if (e != cudaSuccess) return e;
+    return launch_det_reduce(c->det_plan, c->acc, c->D, c->n1, c->n2, 128, c->num_sms, s);
+  }
   if (!c->tile_grad || fa.O != c->O) return frames_launch(c->M, f2, grid, false, s, nullptr, c->fft_schedule);
   TmaMap tm = c->tm_grad;
   tm.tx_extra = c->test_tx_extra;
@@ -363,6 +487,8 @@ mpbp_status enqueue_loss_grad(mpbp_ctx* c, const float* rho, const float* u, con
                               mpbp_step_state* st, cudaStream_t s,
                               const float* phi = nullptr, float* g_phi = nullptr,
                               const StepPtrs* step = nullptr) {
+  if (c->det && frames)
+    return fail(c, MPBP_ERR_UNSUPPORTED, "the deterministic gradient is for evaluations over every frame");
   if (c->acc_dirty) {
     MPBP_CUDA(c, cudaMemsetAsync(c->acc, 0, sizeof(cf) * c->npix * c->D, s));
     c->acc_dirty = false;
@@ -543,6 +669,8 @@ mpbp_status mpbp_create(const mpbp_problem* pr, mpbp_ctx** out) {
     if (sa.y != sb.y) return sa.y < sb.y;
     return sa.x < sb.x;
   });
+  c->scan_h = sc;
+  c->order_h = ord;
   if (cudaMemcpy(c->scan, sc.data(), sizeof(int2) * c->J, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(c->strip_order, ord.data(), sizeof(int) * ord.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(c->acc, 0, sizeof(cf) * c->npix * c->D) != cudaSuccess ||
@@ -585,6 +713,9 @@ void mpbp_destroy(mpbp_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->adam_buf) cudaFree(c->adam_buf);
   if (c->uw_buf) cudaFree(c->uw_buf);
+  if (c->det_meta) cudaFree(c->det_meta);
+  if (c->det_pool) cudaFree(c->det_pool);
+  for (void* q : c->det_old) cudaFree(q);
   delete c;
 }
 
@@ -596,11 +727,31 @@ mpbp_status mpbp_get_info(const mpbp_ctx* c, mpbp_info* info) {
   info->frames_smem = c->fk.smem;
   info->blocks_per_sm = c->blocks_per_sm;
   info->num_sms = c->num_sms;
-  info->launches_loss_grad = 3;  // object build, frames, gradient assembly + reductions
-  info->launches_step = 3;       // the same; the assembly also applies the update
+  // object build, frames, gradient assembly + reductions (the assembly also
+  // applies the step's update); deterministic: + the pieces' clearing and sum
+  info->launches_loss_grad = c->det ? 5 : 3;
+  info->launches_step = c->det ? 5 : 3;
   info->precision = c->precision;
   info->tile_copies = (c->tile_grad ? 1 : 0) | (c->tile_fwd ? 2 : 0);
   info->fft_schedule = c->fft_schedule;
+  info->deterministic = c->det ? 1 : 0;
+  return MPBP_OK;
+}
+
+mpbp_status mpbp_set_deterministic(mpbp_ctx* c, int32_t on) {
+  if (!c) return MPBP_ERR_INVALID_ARG;
+  if (!on) {
+    c->det = false;
+    return MPBP_OK;
+  }
+  if (c->M != 128) return fail(c, MPBP_ERR_UNSUPPORTED, "the deterministic gradient needs frame side 128");
+  if (c->precision != MPBP_PRECISION_FP32 || c->fft_schedule != kLayoutExchange)
+    return fail(c, MPBP_ERR_UNSUPPORTED, "the deterministic gradient needs FP32 FFTs on the exchange schedule");
+  if (!c->tile_grad)
+    return fail(c, MPBP_ERR_UNSUPPORTED, "the deterministic gradient needs tile copies (rows of O a multiple of 16 bytes)");
+  const mpbp_status r = det_prepare(c, frames_grid_for(c, c->nframes));
+  if (r != MPBP_OK) return r;
+  c->det = true;
   return MPBP_OK;
 }
 
@@ -608,6 +759,8 @@ mpbp_status mpbp_set_fft_schedule(mpbp_ctx* c, int32_t schedule) {
   if (!c) return MPBP_ERR_INVALID_ARG;
   if (schedule != MPBP_FFT_SHUFFLE && schedule != MPBP_FFT_EXCHANGE)
     return fail(c, MPBP_ERR_INVALID_ARG, "unknown FFT schedule");
+  if (c->det && schedule != MPBP_FFT_EXCHANGE)
+    return fail(c, MPBP_ERR_UNSUPPORTED, "the deterministic gradient runs on the exchange schedule");
   c->fft_schedule = schedule;
   return MPBP_OK;
 }
@@ -616,6 +769,8 @@ mpbp_status mpbp_set_precision(mpbp_ctx* c, int32_t mode) {
   if (!c) return MPBP_ERR_INVALID_ARG;
   if (mode != MPBP_PRECISION_FP32 && mode != MPBP_PRECISION_TC_SPLIT16)
     return fail(c, MPBP_ERR_INVALID_ARG, "unknown precision mode");
+  if (c->det && mode != MPBP_PRECISION_FP32)
+    return fail(c, MPBP_ERR_UNSUPPORTED, "the deterministic gradient runs on the FP32 FFTs");
   if (mode == MPBP_PRECISION_FP32) {
     c->fk = c->fk_fft;
   } else {
@@ -647,6 +802,7 @@ mpbp_status mpbp_set_schedule(mpbp_ctx* c, int32_t blocks_per_sm) {
   int b = blocks_per_sm == 0 ? c->fk.blocks_per_sm : std::min<int>(blocks_per_sm, c->fk.blocks_per_sm);
   c->blocks_per_sm = std::max(b, 1);
   c->frames_grid_cap = std::min(c->num_sms * c->blocks_per_sm, c->num_sms * 64);
+  if (c->det) return det_prepare(c, frames_grid_for(c, c->nframes));   // the plan follows the grid
   return MPBP_OK;
 }
 
@@ -809,6 +965,7 @@ mpbp_status loss_grad_host_impl(mpbp_ctx* c, const void* y, bool y16, const floa
   if (!c || !rho || !u || !alpha || !loss) return fail(c, MPBP_ERR_INVALID_ARG, "null argument");
   if (!c->has_probe) return fail(c, MPBP_ERR_NO_DATA, "probe not set");
   if (!y && !c->has_data) return fail(c, MPBP_ERR_NO_DATA, "data not set");
+  if (c->det) return fail(c, MPBP_ERR_UNSUPPORTED, "the deterministic gradient takes device-resident data");
   cudaStream_t s = S(stream);
   const long long nx = c->npix * (1 + c->C) + c->D;
   const long long mm = (long long)c->M * c->M;
@@ -1469,6 +1626,9 @@ mpbp_status mpbp_loss_grad_batched(int32_t n, mpbp_ctx* const* ctxs, const float
   if (n == 0) return MPBP_OK;
   mpbp_ctx* lead = ctxs[0];
   if (!lead) return MPBP_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i)
+    if (ctxs[i] && ctxs[i]->det)
+      return fail(lead, MPBP_ERR_UNSUPPORTED, "batched evaluations use the atomic gradient (a problem is deterministic)");
   cudaStream_t s = S(stream);
   for (int i = 0; i < n; ++i) {
     mpbp_ctx* c = ctxs[i];
@@ -1772,6 +1932,7 @@ mpbp_status mpbp_autotune(mpbp_ctx* c, const float* rho, const float* u, const f
   if (!c || !rho || !u || !alpha || !loss || !g_rho || !g_u)
     return fail(c, MPBP_ERR_INVALID_ARG, "null argument");
   if (!c->has_probe || !c->has_data) return fail(c, MPBP_ERR_NO_DATA, "probe or data not set");
+  if (c->det) return fail(c, MPBP_ERR_UNSUPPORTED, "the autotuner's candidates include atomic schedules");
   std::ostringstream k;
   k << gpu_name(c->device) << "|single|m" << c->M << "|d" << c->D << "|n" << c->n1 << "x" << c->n2 << "|f"
     << c->nframes;

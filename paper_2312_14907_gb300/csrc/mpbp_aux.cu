@@ -6,6 +6,8 @@
 //       of mpbp_step (applied by the gradient assembly, pixel by pixel)
 #include "aux_launch.h"
 
+#include <algorithm>
+
 namespace mpbp {
 
 // ----------------------------------------------------------------------------
@@ -431,6 +433,52 @@ __global__ void loss_reduce_kernel(const double* __restrict__ part, long long n,
     *loss = v;
     if (!isfinite(v)) atomicOr(err, kErrNonfinite);
   }
+}
+
+// ----------------------------------------------------------------------------
+// The deterministic gradient (A7): acc_m(row, col) = the sum, in piece
+// order, of the pieces covering that pixel (a piece holds the gradient rows
+// one block wrote back for a run of frames of one column strip; DetPlan).
+// One thread per pixel of the D object-sized accumulators, consecutive
+// threads on consecutive columns; every pixel is written, so acc needs no
+// clearing before.
+// ----------------------------------------------------------------------------
+constexpr int kDetThreads = 256;
+
+__global__ void __launch_bounds__(kDetThreads) det_reduce_kernel(const DetPlan* __restrict__ plan, cf* acc, int D,
+                                                                  int n1, int n2, int w) {
+  const long long npix = (long long)n1 * n2;
+  const cf* pool = plan->pool;
+  const DetPiece* pieces = plan->pieces;
+  const int* col_start = plan->col_start;
+  const int* col_piece = plan->col_piece;
+  for (long long i = blockIdx.x * (long long)kDetThreads + threadIdx.x; i < npix * D;
+       i += (long long)gridDim.x * kDetThreads) {
+    const int m = (int)(i / npix);
+    const long long rc = i - m * npix;
+    const int row = (int)(rc / n2), col = (int)(rc - (long long)row * n2);
+    const int k0 = col_start[m * n2 + col], k1 = col_start[m * n2 + col + 1];
+    float sx = 0.0f, sy = 0.0f;
+    for (int k = k0; k < k1; ++k) {
+      const DetPiece pc = pieces[col_piece[k]];
+      const int r = row - pc.row0;
+      if (r >= 0 && r < pc.rows) {
+        const cf v = pool[pc.off + (long long)r * w + (col - pc.y)];
+        sx += v.x;
+        sy += v.y;
+      }
+    }
+    acc[i] = cf{sx, sy};
+  }
+}
+
+cudaError_t launch_det_reduce(const DetPlan* plan, cf* acc, int D, int n1, int n2, int w, int num_sms,
+                              cudaStream_t s) {
+  const long long n = (long long)D * n1 * n2;
+  const long long need = (n + kDetThreads - 1) / kDetThreads;
+  const int grid = (int)std::max<long long>(1, std::min<long long>(need, (long long)num_sms * 8));
+  det_reduce_kernel<<<grid, kDetThreads, 0, s>>>(plan, acc, D, n1, n2, w);
+  return cudaGetLastError();
 }
 
 // ----------------------------------------------------------------------------

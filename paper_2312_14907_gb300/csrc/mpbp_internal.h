@@ -68,6 +68,32 @@ struct FrameArgs {
   // transposed layout on the way
   const float* yraw;
   float* aT_w;
+  // deterministic gradient (M = 128 exchange kernel, every frame of the
+  // context in column-strip order): where the gradient window writes back,
+  // or nullptr for red.global.add into acc
+  const struct DetPlan* det;
+};
+
+// One piece of the deterministic gradient: a run of frames of one block that
+// share peak and first column (a column strip, or the part of one that a
+// block takes).  Its rows [row0, row0 + rows) x columns [y, y + 128) sit at
+// pool + off, row-major; the block that owns it adds into it with plain
+// loads and stores.
+struct DetPiece {
+  long long off;   // complex elements into the pool
+  int row0, rows;
+  int mpk, y;
+};
+
+// The deterministic gradient's plan for one grid size: pieces in order,
+// each block's first piece, and per (peak, column) the pieces covering that
+// column (CSR: col_start[D * n2 + 1], col_piece[...]) in piece order.
+struct DetPlan {
+  cf* pool;
+  const DetPiece* pieces;
+  const int* block_piece0;
+  const int* col_start;
+  const int* col_piece;
 };
 
 // Per-pixel coefficients of phi_m = phase_scale * G_m . u.

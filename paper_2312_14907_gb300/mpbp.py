@@ -69,7 +69,8 @@ class Info(ctypes.Structure):
                 ("blocks_per_sm", ctypes.c_int32), ("num_sms", ctypes.c_int32),
                 ("launches_loss_grad", ctypes.c_int32), ("launches_step", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("tile_copies", ctypes.c_int32),
-                ("fft_schedule", ctypes.c_int32)]
+                ("fft_schedule", ctypes.c_int32),
+                ("deterministic", ctypes.c_int32)]
 
 
 EXPORTS = ["mpbp_status_string", "mpbp_create", "mpbp_destroy", "mpbp_last_error",
@@ -82,7 +83,8 @@ EXPORTS = ["mpbp_status_string", "mpbp_create", "mpbp_destroy", "mpbp_last_error
            "mpbp_adam_init", "mpbp_adam_step", "mpbp_adam_get_state", "mpbp_adam_set_state",
            "mpbp_loss_grad_phases", "mpbp_unwrap_phases", "mpbp_project_displacement",
            "mpbp_illumination", "mpbp_set_test_stall", "mpbp_loss_grad_host_counts16",
-           "mpbp_set_scan_offsets", "mpbp_shift_probe", "mpbp_loss", "mpbp_set_fft_schedule"]
+           "mpbp_set_scan_offsets", "mpbp_shift_probe", "mpbp_loss", "mpbp_set_fft_schedule",
+           "mpbp_set_deterministic"]
 
 FFT_SHUFFLE = 0           # M = 128: radix-2 stages across threads by warp shuffles
 FFT_EXCHANGE = 1          # M = 128: three register layouts joined by shared-memory exchanges
@@ -143,6 +145,8 @@ def load(build_if_missing=True):
     lib.mpbp_set_schedule.restype = st
     lib.mpbp_set_fft_schedule.argtypes = [V, I32]
     lib.mpbp_set_fft_schedule.restype = st
+    lib.mpbp_set_deterministic.argtypes = [V, I32]
+    lib.mpbp_set_deterministic.restype = st
     lib.mpbp_set_precision.argtypes = [V, I32]
     lib.mpbp_set_precision.restype = st
     lib.mpbp_adam_init.argtypes = [V, P(AdamParams), V, V]
@@ -291,6 +295,11 @@ class Problem:
     def set_fft_schedule(self, schedule):
         """FFT schedule of the M = 128 gradient kernel: FFT_SHUFFLE or FFT_EXCHANGE."""
         self._check(self._lib.mpbp_set_fft_schedule(self._h, int(schedule)), "mpbp_set_fft_schedule")
+
+    def set_deterministic(self, on=True):
+        """Bitwise-reproducible gradient sums (mpbp_set_deterministic; frame
+        side 128, every frame of the context per evaluation)."""
+        self._check(self._lib.mpbp_set_deterministic(self._h, 1 if on else 0), "mpbp_set_deterministic")
 
     def set_schedule(self, blocks_per_sm):
         self._check(self._lib.mpbp_set_schedule(self._h, int(blocks_per_sm)), "mpbp_set_schedule")
