@@ -496,6 +496,20 @@ def run_gpu(args):
                                                     else "shuffle"),
                                  what="columns 32 x 4 and rows 8 x 16 through shared-memory exchanges, or "
                                       "radix-2 stages across threads by warp shuffles")
+    # the deterministic gradient (mpbp_set_deterministic) on the same state:
+    # time per evaluation, and whether repeated evaluations give the same bits
+    prob.set_deterministic(True)
+    d_ms, dk_ms = time_evals(torch, prob, [t.clone() for t in x], max(3, min(args.steps, 10)), flush, stream)
+    r1 = [t.clone() for t in prob.loss_grad(*x)]
+    r2 = prob.loss_grad(*x)
+    same = all(torch.equal(a.contiguous().view(torch.uint8), b.contiguous().view(torch.uint8)) for a, b in zip(r1, r2))
+    prob.set_deterministic(False)
+    line["deterministic"] = {"ms_per_eval": d_ms, "frames_and_sum_ms": dk_ms,
+                             "atomic_ms_per_eval": sched["exchange"]["ms_per_eval"],
+                             "value": spec.nframes / (d_ms / 1e3), "unit": UNIT, "bitwise_repeat": same,
+                             "what": "gradient windows written back into per-block pieces of column strips, "
+                                     "summed per pixel in a fixed order (frames_and_sum_ms: the pieces' clearing, "
+                                     "the frame kernel and the sum)"}
     # scan positions off the pixel grid (not the headline): seeded offsets in
     # [-1/2, 1/2] per scan position, one shifted probe per position; loss and
     # gradient evaluations on the same state, CUDA events, L2 flushed between
