@@ -47,7 +47,9 @@ struct FramesKernel<M, false> {
   using C = T1Cfg<M>;
   static constexpr int NG = C::NG;
   static constexpr int kTileGrad = 0, kTileFwd = 0;
-  static KernelShape grad(bool, bool = false, int = 0, bool = false) { return {frames_t1<M, false>, C::T, C::SMEM}; }
+  static KernelShape grad(bool, bool = false, int = 0, bool = false, bool = false) {
+    return {frames_t1<M, false>, C::T, C::SMEM};
+  }
   static KernelShape fwd(bool) { return {frames_t1<M, true>, C::T, C::SMEM}; }
   static KernelShape loss(bool, bool = false, int = 0, bool = false) {
     return {frames_t1<M, false, true>, C::T, C::SMEM};
@@ -66,8 +68,12 @@ struct FramesKernel<M, true> {
   static constexpr int kTileGrad = kQuads ? T4Cfg<M>::PW : (C::SWZ ? 0 : C::PW);
   // tpr: the probe stays in tensor memory (four threads per line; probes
   // shared by the frames of a peak)
-  static KernelShape grad(bool tma, bool tpr = false, int layout = kLayoutDefault, bool bg = false) {
+  static KernelShape grad(bool tma, bool tpr = false, int layout = kLayoutDefault, bool bg = false,
+                          bool det = false) {
     if constexpr (kQuads) {
+      if (layout == kLayoutExchange && det) {   // deterministic gradient: tile copies only
+        return {bg ? frames_x3<true, false, true, true> : frames_x3<true, false, false, true>, X3Cfg::T, X3Cfg::SMEM};
+      }
       if (layout == kLayoutExchange) {   // the probe always in tensor memory
         if (bg) return {tma ? frames_x3<true, false, true> : frames_x3<false, false, true>, X3Cfg::T, X3Cfg::SMEM};
         return {tma ? frames_x3<true> : frames_x3<false>, X3Cfg::T, X3Cfg::SMEM};
@@ -128,9 +134,9 @@ template <int M>
 bool frames_prepare_impl(FrameKernelInfo* info) {
   using K = FramesKernel<M>;
   bool ok = true;
-  for (int t = 0; t < 16; ++t)
-    ok = set_smem(K::grad(t & 1, (t >> 1) & 1, (t >> 2) & 1, t >> 3)) && set_smem(K::fwd(t & 1)) &&
-         set_smem(K::loss(t & 1, (t >> 1) & 1, (t >> 2) & 1, t >> 3)) && ok;
+  for (int t = 0; t < 32; ++t)
+    ok = set_smem(K::grad(t & 1, (t >> 1) & 1, (t >> 2) & 1, (t >> 3) & 1, t >> 4)) && set_smem(K::fwd(t & 1)) &&
+         set_smem(K::loss(t & 1, (t >> 1) & 1, (t >> 2) & 1, (t >> 3) & 1)) && ok;
   if (K::kRaw) ok = set_smem(K::raw(false)) && set_smem(K::raw(true)) && ok;
   if (K::kRaw16) ok = set_smem(K::raw(true, true)) && ok;
   if (!ok) return false;
@@ -157,7 +163,8 @@ cudaError_t frames_launch_impl(const FrameArgs& a, int grid, bool forward, cudaS
   using K = FramesKernel<M>;
   static const TmaMap kNone{};
   const bool tile = tm != nullptr && (forward ? K::kTileFwd : K::kTileGrad) > 0;
-  const KernelShape k = forward ? K::fwd(tile) : K::grad(tile, a.probe_stride >= 0, layout, a.bgT != nullptr);
+  const KernelShape k = forward ? K::fwd(tile)
+                                : K::grad(tile, a.probe_stride >= 0, layout, a.bgT != nullptr, a.det != nullptr);
   k.fn<<<grid, k.threads, k.smem, s>>>(a, tile ? *tm : kNone);
   return cudaGetLastError();
 }

@@ -136,6 +136,7 @@ struct X3Win {
 // deterministic plan the rows go to the block's current piece instead, by
 // plain loads and stores (the piece has no other writer, and successive
 // write-backs of a row are separated by block barriers).
+template <bool DET>
 MPBP_DI void x3_flush(const FrameArgs& p, const X3Roles& r, const X3Win& w, int x0, int d, uint32_t ta,
                       bool zero) {
   const int col = w.y + r.c;
@@ -143,7 +144,7 @@ MPBP_DI void x3_flush(const FrameArgs& p, const X3Roles& r, const X3Win& w, int 
   cf* const base = p.acc + (long long)w.mpk * p.obj_stride + col;
   const unsigned n1 = (unsigned)p.n1;
   cf* pbase = nullptr;   // the piece's column c at row 0
-  if (p.det) {
+  if constexpr (DET) {
     const DetPiece pc = p.det->pieces[w.piece];
     pbase = p.det->pool + pc.off - (long long)pc.row0 * X3Cfg::M + r.c;
   }
@@ -160,7 +161,7 @@ MPBP_DI void x3_flush(const FrameArgs& p, const X3Roles& r, const X3Win& w, int 
       if (i0 + j < cnt) {
         const int row = x0 + r.h + 4 * (i0 + j);
         const cf g = cf{__uint_as_float(v[j][0]), __uint_as_float(v[j][1])};
-        if (pbase) {
+        if constexpr (DET) {
           cf* q = pbase + (long long)row * X3Cfg::M;
           const cf o = *q;
           *q = cf{o.x + g.x, o.y + g.y};
@@ -253,7 +254,7 @@ MPBP_DI void x3_fetch(const FrameArgs& p, const X3Roles& r, const FrameRef& fr, 
 // One frame's loss and gradient (inputs in flight); fetches the next frame's
 // inputs as soon as their buffers are free.  TMA: a wait that runs out clears
 // bs.ok and returns at once.
-template <bool TMA, bool LOSS, bool BG, typename AddLoss>
+template <bool TMA, bool LOSS, bool BG, bool DET, typename AddLoss>
 MPBP_DI void x3_frame(const FrameArgs& p, const X3Roles& r, const FrameRef& cur, const FrameRef& nxt,
                       AddLoss&& add_loss, BulkState& bs, const TmaMap* tm, cf* buf, float* abuf, uint32_t tp,
                       uint32_t ta, const X3Tables& tab, X3Win& win) {
@@ -450,7 +451,7 @@ MPBP_DI void x3_frame(const FrameArgs& p, const X3Roles& r, const FrameRef& cur,
   if (cur.valid) {
     const bool slide = win.ok && cur.mpk == win.mpk && cur.s.y == win.y && cur.s.x >= win.x &&
                        cur.s.x - win.x < X3Cfg::M;
-    if (win.ok) x3_flush(p, r, win, win.x, slide ? cur.s.x - win.x : X3Cfg::M, ta, true);
+    if (win.ok) x3_flush<DET>(p, r, win, win.x, slide ? cur.s.x - win.x : X3Cfg::M, ta, true);
     // a new strip starts the block's next piece (the host splits them there)
     const bool strip = !win.ok || cur.mpk != win.mpk || cur.s.y != win.y;
     win = X3Win{true, cur.mpk, cur.s.y, cur.s.x, win.piece + (strip ? 1 : 0)};
@@ -506,14 +507,15 @@ MPBP_DI void x3_frame(const FrameArgs& p, const X3Roles& r, const FrameRef& cur,
   tmem_fence_before_sync();
 }
 
-// loss and gradient (LOSS: loss only; BG: with the background of Eq. 2): a
+// loss and gradient (LOSS: loss only; BG: with the background of Eq. 2;
+// DET: the gradient through the deterministic plan p.det): a
 // persistent grid, block b taking frames [N b / G, N (b + 1) / G) of the
 // order given (p.frames, else 0..N-1); TMA: inputs by tile and bulk copies
 // (tm: the objects' tensor map), else by cp.async.  The probe values of a
 // thread sit in tensor memory and are reloaded when the frame's probe
 // changes: once per block for one probe, per peak for one probe per peak,
 // per frame for probes shifted per scan position.
-template <bool TMA, bool LOSS = false, bool BG = false>
+template <bool TMA, bool LOSS = false, bool BG = false, bool DET = false>
 __global__ void __launch_bounds__(X3Cfg::T, 1) frames_x3(const FrameArgs p, const __grid_constant__ TmaMap tm) {
   using C = X3Cfg;
   constexpr int M = C::M;
@@ -547,7 +549,7 @@ __global__ void __launch_bounds__(X3Cfg::T, 1) frames_x3(const FrameArgs p, cons
     tmem_wait_st();
     tmem_fence_before_sync();   // ordered before the first frame's barriers
   }
-  X3Win win{false, 0, 0, 0, p.det ? p.det->block_piece0[blockIdx.x] - 1 : 0};
+  X3Win win{false, 0, 0, 0, DET ? p.det->block_piece0[blockIdx.x] - 1 : 0};
   const cf* tp_src = nullptr;   // the probe held in tensor memory (block-uniform)
   double lsum = 0.0;
   const int lo = (int)((long long)p.nframes * blockIdx.x / gridDim.x);
@@ -570,7 +572,7 @@ __global__ void __launch_bounds__(X3Cfg::T, 1) frames_x3(const FrameArgs p, cons
         tp_src = P;
       }
     }
-    x3_frame<TMA, LOSS, BG>(p, r, cur, nxt, [&](float fl) { lsum += (double)fl; }, bs, &tm, buf, abuf, tp, ta,
+    x3_frame<TMA, LOSS, BG, DET>(p, r, cur, nxt, [&](float fl) { lsum += (double)fl; }, bs, &tm, buf, abuf, tp, ta,
                             tab, win);
     if (TMA && !bs.ok) {
       if (threadIdx.x == 0) atomicOr(p.err, kErrTimeout);
@@ -583,7 +585,7 @@ __global__ void __launch_bounds__(X3Cfg::T, 1) frames_x3(const FrameArgs p, cons
     if (bs.ok && win.ok) {   // what is left of the window
       __syncthreads();
       tmem_fence_after_sync();
-      x3_flush(p, r, win, win.x, M, ta, false);
+      x3_flush<DET>(p, r, win, win.x, M, ta, false);
     }
   }
   const double tot = block_sum_d<C::T>(lsum, red);
