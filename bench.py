@@ -987,6 +987,8 @@ def run_drive(args):
     del yd
     x = [torch.from_numpy(a.astype(np.float32)).cuda() for a in synth.init_state(spec)]
     prob.set_precision(args.drive_precision)
+    if args.drive_deterministic:
+        prob.set_deterministic(True)
     for _ in range(args.drive_evals):
         prob.loss_grad(*x)
     if args.drive_projector:
@@ -1021,6 +1023,8 @@ def main():
     ap.add_argument("--drive-steps", type=int, default=0)
     ap.add_argument("--drive-projector", type=int, default=0,
                     help="profiling driver: projector calls (Pi_U on the displacement)")
+    ap.add_argument("--drive-deterministic", action="store_true",
+                    help="profiling driver: the deterministic gradient (mpbp_set_deterministic)")
     ap.add_argument("--drive-precision", type=int, default=0,
                     help="profiling driver: 0 = FP32 FFT kernels, 1 = tensor-core DFTs (M = 64)")
     args = ap.parse_args()

@@ -47,6 +47,8 @@
 #include "frames_t4.cuh"
 #include "tmem.cuh"
 
+#include <climits>
+
 namespace mpbp {
 
 struct X3Cfg {
@@ -123,19 +125,23 @@ MPBP_DI void x3_twiddles(const X3Tables& t, const X3Roles& r, X3Tw& tw) {
 }
 
 // the gradient window of a block: strip (peak, first column) and its first
-// row; with a deterministic plan, the block's current piece
+// row; with a deterministic plan, the block's current piece and the hull
+// [wlo, whi) of the rows written into it so far
 struct X3Win {
   bool ok;
   int mpk, y, x;
   int piece;
+  int wlo, whi;
 };
 
 // Add rows [x0, x0 + d) of the window to the accumulator (A7) and, if zero,
 // clear their slots; thread (c, h) takes rows x0 + h + 4 i.  Whole block,
 // converged; ta: the thread's lane at the window's first column.  With a
-// deterministic plan the rows go to the block's current piece instead, by
-// plain loads and stores (the piece has no other writer, and successive
-// write-backs of a row are separated by block barriers).
+// deterministic plan the rows go to the block's current piece instead:
+// rows outside the hull of those written so far are stored, the others
+// loaded, added and stored (the piece has no other writer, it starts
+// cleared, and successive write-backs of a row are separated by block
+// barriers); on a strip the window slides down, so every row is a store.
 template <bool DET>
 MPBP_DI void x3_flush(const FrameArgs& p, const X3Roles& r, const X3Win& w, int x0, int d, uint32_t ta,
                       bool zero) {
@@ -163,8 +169,12 @@ MPBP_DI void x3_flush(const FrameArgs& p, const X3Roles& r, const X3Win& w, int 
         const cf g = cf{__uint_as_float(v[j][0]), __uint_as_float(v[j][1])};
         if constexpr (DET) {
           cf* q = pbase + (long long)row * X3Cfg::M;
-          const cf o = *q;
-          *q = cf{o.x + g.x, o.y + g.y};
+          if (row >= w.wlo && row < w.whi) {   // warp-uniform
+            const cf o = *q;
+            *q = cf{o.x + g.x, o.y + g.y};
+          } else {
+            *q = g;
+          }
         } else {
           red_add_v2_if(base + (long long)row * p.n2, g, cok && (unsigned)row < n1);
         }
@@ -451,10 +461,20 @@ MPBP_DI void x3_frame(const FrameArgs& p, const X3Roles& r, const FrameRef& cur,
   if (cur.valid) {
     const bool slide = win.ok && cur.mpk == win.mpk && cur.s.y == win.y && cur.s.x >= win.x &&
                        cur.s.x - win.x < X3Cfg::M;
-    if (win.ok) x3_flush<DET>(p, r, win, win.x, slide ? cur.s.x - win.x : X3Cfg::M, ta, true);
+    const int dd = slide ? cur.s.x - win.x : X3Cfg::M;
+    if (win.ok) x3_flush<DET>(p, r, win, win.x, dd, ta, true);
     // a new strip starts the block's next piece (the host splits them there)
     const bool strip = !win.ok || cur.mpk != win.mpk || cur.s.y != win.y;
-    win = X3Win{true, cur.mpk, cur.s.y, cur.s.x, win.piece + (strip ? 1 : 0)};
+    int wlo = win.wlo, whi = win.whi;
+    if (win.ok && dd > 0) {
+      wlo = min(wlo, win.x);
+      whi = max(whi, win.x + dd);
+    }
+    if (strip) {
+      wlo = INT_MAX;
+      whi = INT_MIN;
+    }
+    win = X3Win{true, cur.mpk, cur.s.y, cur.s.x, win.piece + (strip ? 1 : 0), wlo, whi};
   }
   tmem_wait_st();
   tmem_fence_before_sync();
@@ -549,7 +569,7 @@ __global__ void __launch_bounds__(X3Cfg::T, 1) frames_x3(const FrameArgs p, cons
     tmem_wait_st();
     tmem_fence_before_sync();   // ordered before the first frame's barriers
   }
-  X3Win win{false, 0, 0, 0, DET ? p.det->block_piece0[blockIdx.x] - 1 : 0};
+  X3Win win{false, 0, 0, 0, DET ? p.det->block_piece0[blockIdx.x] - 1 : 0, INT_MAX, INT_MIN};
   const cf* tp_src = nullptr;   // the probe held in tensor memory (block-uniform)
   double lsum = 0.0;
   const int lo = (int)((long long)p.nframes * blockIdx.x / gridDim.x);
