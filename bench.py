@@ -708,7 +708,7 @@ def secondary_block(torch, mpbp, args, flush, stream, pk):
     tr = traffic_record("frames_m%d_traffic.json" % spec.m, rev)
     out = {"config": workload_config(spec), "ms_per_step": ms, "value": spec.nframes / (ms / 1e3),
            "unit": UNIT, "eager_ms_per_step": eager_ms, "iterations_per_s": 1e3 / ms,
-           "roofline": {"bound": "alu", "kernel": "frames_t2<64, tile copies>", "kernel_ms": kavg_ms,
+           "roofline": {"bound": "alu", "kernel": "frames_t2<64, tile copies, probe in TMEM>", "kernel_ms": kavg_ms,
                         "achieved": achieved, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
                         "frac": achieved / pk["fp32_tflops"],
                         "traffic": tr["bytes_per_launch"] if tr else None}}

@@ -6,6 +6,8 @@
 //   loss and gradient at M = 128, four threads per line (frames_t4), whose
 //   32 values a thread fit in registers where the pair's 64 spill.
 #pragma once
+#include <algorithm>
+
 #include "frames.cuh"
 #include "frames_launch.h"
 #include "frames_t4.cuh"
@@ -37,7 +39,38 @@ struct KernelShape {
   void (*fn)(const FrameArgs, const TmaMap);
   int threads;
   int smem;
+  int tmem_cols = 0;   // tensor-memory columns a block allocates, where the
+                       // schedule has to count them (occupancy below)
 };
+
+// Resident blocks per SM of kernel k.  For a kernel that allocates a part of
+// tensor memory the runtime's calculator answers one block per SM whatever
+// the part (measured: four such blocks of 128 columns run together), so the
+// count is formed here from its registers (in units of 256 a warp), shared
+// memory (with the per-block reservation), threads and columns.
+inline bool occupancy(const KernelShape& k, int* blocks) {
+  if (k.tmem_cols == 0)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k.fn, k.threads, k.smem) == cudaSuccess;
+  cudaFuncAttributes a{};
+  int dev = 0, regs = 0, smem = 0, resv = 0, thr = 0, blk = 0;
+  if (cudaFuncGetAttributes(&a, k.fn) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&regs, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&thr, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&blk, cudaDevAttrMaxBlocksPerMultiprocessor, dev) != cudaSuccess)
+    return false;
+  const int warps = (k.threads + 31) / 32;
+  const int regs_warp = (a.numRegs * 32 + 255) / 256 * 256;
+  const int smem_block = ((int)a.sharedSizeBytes + k.smem + 127) / 128 * 128 + resv;
+  int b = regs_warp > 0 ? regs / (warps * regs_warp) : blk;
+  b = std::min(b, smem / smem_block);
+  b = std::min(b, thr / k.threads);
+  b = std::min(b, blk);
+  b = std::min(b, 512 / k.tmem_cols);
+  *blocks = b;
+  return true;
+}
 
 // M = 128 loss-and-gradient layouts (FrameLayout): radix-2 stages across
 // threads by shuffles (frames_t4) or three register layouts joined by
@@ -83,6 +116,10 @@ struct FramesKernel<M, true> {
       return {tma ? frames_t4<M, true> : frames_t4<M, false>, T4Cfg<M>::T, T4Cfg<M>::SMEM};
     } else if constexpr (C::SWZ) {
       return {frames_t2<M, false>, C::T, C::SMEM};
+    } else if constexpr (M == 64) {
+      // tile copies: the probe in tensor memory
+      return tma ? KernelShape{frames_t2<M, false, false, true, false, false, true>, C::T, C::SMEM_TMA, M}
+                 : KernelShape{frames_t2<M, false>, C::T, C::SMEM};
     } else {
       return tma ? KernelShape{frames_t2<M, false, false, true>, C::T, C::SMEM_TMA}
                  : KernelShape{frames_t2<M, false>, C::T, C::SMEM};
@@ -150,7 +187,7 @@ bool frames_prepare_impl(FrameKernelInfo* info) {
   for (int t = 0; t < 4; ++t) {
     const KernelShape k = K::grad(t & 1, false, t >> 1);
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k.fn, k.threads, k.smem) != cudaSuccess) return false;
+    if (!occupancy(k, &b)) return false;
     nb = b < nb ? b : nb;
   }
   info->blocks_per_sm = nb;
