@@ -71,11 +71,14 @@ def test_shifted_probes_match_oracle(m):
 
 
 # (n, m, side, step, offset, peaks, comps): the pair (M = 32, 64) and
-# quad (M = 128) kernels, frames over every edge
+# M = 128 kernels, frames over every edge; the last with 338 frames, so that
+# every block of the M = 128 grid takes two or three frames and reloads its
+# probe (one per scan position) while its gradient window slides
 SIZES = [
     (64, 32, 6, 7, -3, 3, 3),
     (128, 64, 5, 17, -9, 3, 3),
     (200, 128, 3, 41, -20, 2, 3),
+    (256, 128, 13, 10, -6, 2, 3),
 ]
 
 
