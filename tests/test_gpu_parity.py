@@ -228,6 +228,32 @@ def test_frame_index_out_of_range_is_reported():
     p.sync_status()
 
 
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_m128_out_of_range_inside_a_block_run(schedule):
+    """At M = 128 a block takes a contiguous run of a frame list (exchange
+    schedule) or every 152nd entry (shuffle schedule); out-of-range indices in
+    the middle of the runs are reported as MPBP_ERR_BOUNDS, leave the valid
+    frames' results equal to the oracle's over those frames, and the context
+    stays usable."""
+    from paper_2312_14907_gb300 import mpbp
+    spec, scan = custom_spec(256, 128, 13, 10, npeaks=2, offset=-6)
+    case = Case(spec, scan=scan, state="perturbed")
+    p, x = _gpu(case)
+    p.set_fft_schedule(schedule)
+    rng = np.random.default_rng(7)
+    good = rng.permutation(spec.nframes)[:320].astype(np.int32)
+    bad = good.copy()
+    bad[rng.choice(320, 12, replace=False)] = np.array([-1, 10_000] * 6, np.int32)
+    got = p.loss_grad(*x, frames=torch.from_numpy(bad).cuda())
+    with pytest.raises(mpbp.MPBPError) as ei:
+        p.sync_status()
+    assert ei.value.status == 6
+    valid = bad[(bad >= 0) & (bad < spec.nframes)]
+    _check_loss_grad(case, got, frames=valid)
+    _check_loss_grad(case, p.loss_grad(*x, frames=torch.from_numpy(good).cuda()), frames=good)
+    p.sync_status()
+
+
 def _check_loss_only(case, got):
     f = case.oracle_loss_grad()[0]
     assert abs(got[0].item() - f) <= LOSS_TOL * abs(f), (got[0].item(), f)
