@@ -420,18 +420,20 @@ mpbp_status mpbp_loss_grad_noalloc(const mpbp_problem *problem, const float *pro
 mpbp_status mpbp_set_fft_schedule(mpbp_ctx *ctx, int32_t schedule);
 
 /* Deterministic gradient (the A7 sums of Eq. 11 in a fixed order).  With on
- * != 0 the frame kernel's gradient windows write back into per-block pieces
- * (a run of frames of one scan column strip) with plain stores, and a second
+ * != 0 the frame kernel keeps each column's gradient rows in a window in
+ * tensor memory and writes them back into per-block pieces (a run of frames
+ * of one scan column strip) with plain stores, and a second
  * kernel sums, for every object pixel, the pieces covering it in a fixed
  * order, in place of red.global.add into one accumulator: loss, g_rho, g_u
  * and g_alpha are then the same bits on every call with the same inputs and
  * schedule (with the atomic sums they agree only to rounding).  Costs a
  * device workspace of about 8 x 128 x (rows spanned by a strip + 128) bytes
- * per piece (about 1 GB for 87,846 frames of 128 x 128 on a 1024^2 object),
+ * per piece for frame side 128 (about 1 GB for 87,846 frames of 128 x 128
+ * on a 1024^2 object; 8 x 64 x (rows + 64) at side 64),
  * allocated here and kept while the context lives, and the clearing and
- * summing of it on each evaluation.  Needs frame side 128 on FP32 FFTs with
- * the exchange schedule and tile copies (rows of O a multiple of 16 bytes):
- * else MPBP_ERR_UNSUPPORTED.  While on, evaluations over a frame list
+ * summing of it on each evaluation.  Needs frame side 64 or 128 on FP32 FFTs
+ * (at 128 the exchange schedule) and tile copies (rows of O a multiple of 16
+ * bytes): else MPBP_ERR_UNSUPPORTED.  While on, evaluations over a frame list
  * (mpbp_loss_grad with frames, mpbp_adam_step minibatches), the host-buffer
  * calls, mpbp_loss_grad_batched and mpbp_autotune return
  * MPBP_ERR_UNSUPPORTED, and so do mpbp_set_precision / mpbp_set_fft_schedule

@@ -117,7 +117,9 @@ struct FramesKernel<M, true> {
     } else if constexpr (C::SWZ) {
       return {frames_t2<M, false>, C::T, C::SMEM};
     } else if constexpr (M == 64) {
-      // tile copies: the probe in tensor memory
+      // tile copies: the probe in tensor memory; deterministic gradient: its
+      // window beside it (tile copies only)
+      if (det) return {frames_t2<M, false, false, true, false, false, true, true>, C::T, C::SMEM_TMA, 2 * M};
       return tma ? KernelShape{frames_t2<M, false, false, true, false, false, true>, C::T, C::SMEM_TMA, M}
                  : KernelShape{frames_t2<M, false>, C::T, C::SMEM};
     } else {

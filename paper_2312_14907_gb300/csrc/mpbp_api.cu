@@ -225,7 +225,7 @@ bool full_launch(const mpbp_ctx* c, const FrameArgs& fa) {
 // window does.  A piece spans its frames' rows plus a frame, 128 columns.
 mpbp_status det_prepare(mpbp_ctx* c, int grid) {
   if (c->det_grid == grid && c->det_plan) return MPBP_OK;
-  constexpr int W = 128;
+  const int W = c->M;
   const long long N = c->nframes;
   std::vector<DetPiece> pieces;
   std::vector<int> b0(grid);
@@ -315,7 +315,7 @@ cudaError_t launch_frames(const mpbp_ctx* c, const FrameArgs& fa, int grid, cuda
     // only launches over every frame with the plan's grid get here (the
     // entry points refuse the others); anything else is a library bug
     if (!full_launch(c, fa) || grid != c->det_grid || !c->det_plan || c->precision != MPBP_PRECISION_FP32 ||
-        c->fft_schedule != kLayoutExchange || !c->tile_grad)
+        (c->M == 128 && c->fft_schedule != kLayoutExchange) || !c->tile_grad)
       return cudaErrorNotSupported;
   } else if (c->precision == MPBP_PRECISION_TC_SPLIT16) {
     return tc_launch(c->M, fa, c->tc_w, grid, s, c->test_tx_extra != 0);
@@ -323,7 +323,7 @@ cudaError_t launch_frames(const mpbp_ctx* c, const FrameArgs& fa, int grid, cuda
   FrameArgs f2 = fa;
   // every frame of the context: the exchange kernel at M = 128 takes them in
   // column strips (any order gives the same sums up to rounding)
-  if (c->M == 128 && c->fft_schedule == kLayoutExchange && !fa.frames && fa.frame0 == 0 &&
+  if (((c->M == 128 && c->fft_schedule == kLayoutExchange) || c->det) && !fa.frames && fa.frame0 == 0 &&
       fa.nframes == c->nframes && fa.aT == c->aT)
     f2.frames = c->strip_order;
   if (c->det) {
@@ -334,7 +334,7 @@ cudaError_t launch_frames(const mpbp_ctx* c, const FrameArgs& fa, int grid, cuda
     tm.tx_extra = c->test_tx_extra;
     e = frames_launch(c->M, f2, grid, false, s, &tm, c->fft_schedule);
     if (e != cudaSuccess) return e;
-    return launch_det_reduce(c->det_plan, c->acc, c->D, c->n1, c->n2, 128, c->num_sms, s);
+    return launch_det_reduce(c->det_plan, c->acc, c->D, c->n1, c->n2, c->M, c->num_sms, s);
   }
   if (!c->tile_grad || fa.O != c->O) return frames_launch(c->M, f2, grid, false, s, nullptr, c->fft_schedule);
   TmaMap tm = c->tm_grad;
@@ -744,9 +744,10 @@ mpbp_status mpbp_set_deterministic(mpbp_ctx* c, int32_t on) {
     c->det = false;
     return MPBP_OK;
   }
-  if (c->M != 128) return fail(c, MPBP_ERR_UNSUPPORTED, "the deterministic gradient needs frame side 128");
-  if (c->precision != MPBP_PRECISION_FP32 || c->fft_schedule != kLayoutExchange)
-    return fail(c, MPBP_ERR_UNSUPPORTED, "the deterministic gradient needs FP32 FFTs on the exchange schedule");
+  if (c->M != 64 && c->M != 128)
+    return fail(c, MPBP_ERR_UNSUPPORTED, "the deterministic gradient needs frame side 64 or 128");
+  if (c->precision != MPBP_PRECISION_FP32 || (c->M == 128 && c->fft_schedule != kLayoutExchange))
+    return fail(c, MPBP_ERR_UNSUPPORTED, "the deterministic gradient needs FP32 FFTs (at 128: the exchange schedule)");
   if (!c->tile_grad)
     return fail(c, MPBP_ERR_UNSUPPORTED, "the deterministic gradient needs tile copies (rows of O a multiple of 16 bytes)");
   const mpbp_status r = det_prepare(c, frames_grid_for(c, c->nframes));
@@ -759,7 +760,7 @@ mpbp_status mpbp_set_fft_schedule(mpbp_ctx* c, int32_t schedule) {
   if (!c) return MPBP_ERR_INVALID_ARG;
   if (schedule != MPBP_FFT_SHUFFLE && schedule != MPBP_FFT_EXCHANGE)
     return fail(c, MPBP_ERR_INVALID_ARG, "unknown FFT schedule");
-  if (c->det && schedule != MPBP_FFT_EXCHANGE)
+  if (c->det && c->M == 128 && schedule != MPBP_FFT_EXCHANGE)
     return fail(c, MPBP_ERR_UNSUPPORTED, "the deterministic gradient runs on the exchange schedule");
   c->fft_schedule = schedule;
   return MPBP_OK;

@@ -298,7 +298,7 @@ class Problem:
 
     def set_deterministic(self, on=True):
         """Bitwise-reproducible gradient sums (mpbp_set_deterministic; frame
-        side 128, every frame of the context per evaluation)."""
+        sides 64 and 128, every frame of the context per evaluation)."""
         self._check(self._lib.mpbp_set_deterministic(self._h, 1 if on else 0), "mpbp_set_deterministic")
 
     def set_schedule(self, blocks_per_sm):

@@ -1,9 +1,10 @@
 """The deterministic gradient (mpbp_set_deterministic): the gradient windows
-of the M = 128 exchange kernel write back into per-block pieces of column
-strips, and a second kernel sums the pieces covering each pixel in a fixed
-order.  Against the FP64 oracle at the parity tolerances; bit for bit
-against itself on repeated calls and through the captured step; within
-rounding of the atomic sums; and the calls it cannot serve are refused.
+of the frame kernels (M = 128 exchange schedule, M = 64 thread pairs) write
+back into per-block pieces of column strips, and a second kernel sums the
+pieces covering each pixel in a fixed order.  Against the FP64 oracle at
+the parity tolerances; bit for bit against itself on repeated calls and
+through the captured step; within rounding of the atomic sums; and the calls
+it cannot serve are refused.
 """
 import numpy as np
 import pytest
@@ -44,23 +45,32 @@ def _same_bits(a, b):
                            t.view(torch.uint8) if t.dtype != torch.uint8 else t)
 
 
-def _irregular_scan(n2):
-    rng = np.random.default_rng(1701)
-    pos = np.stack([rng.integers(-40, 200, 150), rng.integers(-40, n2 - 88, 150)], axis=1)
-    cols = rng.integers(-20, n2 - 100, 4)
-    extra = np.array([[r, c] for c in cols for r in sorted(rng.integers(-30, 180, 5))])
+def _irregular_scan(n, m, count):
+    rng = np.random.default_rng(1701 + m)
+    lo, hi = -m // 3, n - 2 * m // 3
+    pos = np.stack([rng.integers(lo, hi, count), rng.integers(lo, hi, count)], axis=1)
+    cols = rng.integers(lo, hi, 4)
+    # strips with several rows each (odd and even steps), and repeats
+    extra = np.array([[r, c] for c in cols for r in sorted(rng.integers(lo, hi, 5))])
     return np.concatenate([pos, extra, pos[:3]]).astype(np.int32)
 
 
+# (m, n, scan side, step, irregular positions): more than two frames a block
+# (M = 128: 152 blocks; M = 64: 608)
+GEOM = {128: (256, 13, 10, 150), 64: (170, 26, 6, 660)}
+
+
+@pytest.mark.parametrize("m", [128, 64])
 @pytest.mark.parametrize("kind", ["grid", "irregular", "background"])
-def test_deterministic_matches_oracle_and_itself(kind):
-    """338 or 346 frames: every block of the 152-block grid takes two or
-    three frames.  Regular 13 x 13 scans (strips of 13 frames sliding down by
-    10 rows), seeded positions off any grid (repeats, jumps past the window,
-    column and peak changes inside a block's run), and a background."""
-    spec, scan = custom_spec(256, 128, 13, 10, npeaks=2, offset=-6)
+def test_deterministic_matches_oracle_and_itself(kind, m):
+    """Every block takes two or three frames.  Regular scans (strips sliding
+    down by an even step), seeded positions off any grid (repeats, odd steps,
+    jumps past the window, column and peak changes inside a block's run),
+    and a background."""
+    n, side, step, count = GEOM[m]
+    spec, scan = custom_spec(n, m, side, step, npeaks=2, offset=-6)
     if kind == "irregular":
-        scan = _irregular_scan(256)
+        scan = _irregular_scan(n, m, count)
     case = Case(spec, scan=scan, state="perturbed", bg=(kind == "background"))
     p, x = _gpu(case)
     atomic = [t.clone() for t in p.loss_grad(*x)]
@@ -81,10 +91,12 @@ def test_deterministic_matches_oracle_and_itself(kind):
     p.sync_status()
 
 
-def test_deterministic_step_and_captured_replay():
+@pytest.mark.parametrize("m", [128, 64])
+def test_deterministic_step_and_captured_replay(m):
     """Eager steps and the captured step's replays from the same state give
     the same bits, run after run."""
-    spec, scan = custom_spec(256, 128, 13, 10, npeaks=2, offset=-6)
+    n, side, step, _ = GEOM[m]
+    spec, scan = custom_spec(n, m, side, step, npeaks=2, offset=-6)
     case = Case(spec, scan=scan, state="perturbed")
     p, x = _gpu(case)
     p.set_deterministic(True)
@@ -140,9 +152,11 @@ def test_deterministic_refusals():
     f = case.oracle_loss_grad(frames=frames.cpu().numpy())[0]
     assert abs(got[0].item() - f) <= LOSS_TOL * abs(f)
     p.sync_status()
-    # frame sides other than 128, and objects without tile copies (odd n2)
-    for sp, sc in (custom_spec(96, 64, 3, 16, npeaks=2, offset=-4), custom_spec(256, 128, 3, 40, npeaks=2, n2=255,
-                                                                                offset=-6)):
+    # frame sides other than 64 and 128, and objects without tile copies
+    # (odd n2)
+    for sp, sc in (custom_spec(64, 32, 3, 10, npeaks=2, offset=-4), custom_spec(256, 128, 3, 40, npeaks=2, n2=255,
+                                                                                offset=-6),
+                   custom_spec(150, 64, 3, 20, npeaks=2, n2=149, offset=-4)):
         q, _ = _gpu(Case(sp, scan=sc, state="perturbed"))
         refused(lambda: q.set_deterministic(True))
         assert q.info()["deterministic"] == 0
