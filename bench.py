@@ -712,6 +712,17 @@ def secondary_block(torch, mpbp, args, flush, stream, pk):
                         "achieved": achieved, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
                         "frac": achieved / pk["fp32_tflops"],
                         "traffic": tr["bytes_per_launch"] if tr else None}}
+    # the deterministic gradient (mpbp_set_deterministic) on the same state
+    xd = [t.clone() for t in x]
+    a_ms, _ = time_evals(torch, prob, xd, steps, flush, stream)
+    prob.set_deterministic(True)
+    d_ms, _ = time_evals(torch, prob, xd, steps, flush, stream)
+    r1 = [t.clone() for t in prob.loss_grad(*xd)]
+    r2 = prob.loss_grad(*xd)
+    same = all(torch.equal(a.contiguous().view(torch.uint8), b.contiguous().view(torch.uint8)) for a, b in zip(r1, r2))
+    prob.set_deterministic(False)
+    out["deterministic"] = {"ms_per_eval": d_ms, "atomic_ms_per_eval": a_ms, "value": spec.nframes / (d_ms / 1e3),
+                            "unit": UNIT, "bitwise_repeat": same}
     # the tensor-core precision mode on the same steps
     prob.set_precision(mpbp.PRECISION_TC_SPLIT16)
     xs = [t.clone() for t in x]
