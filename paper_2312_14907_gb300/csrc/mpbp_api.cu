@@ -251,20 +251,24 @@ mpbp_status det_prepare(mpbp_ctx* c, int grid) {
     pc.off = off;
     off += (long long)pc.rows * W;
   }
-  // per (peak, column): the pieces that cover it, in piece order
-  const long long ncol = (long long)c->D * c->n2;
-  std::vector<int> cnt((size_t)ncol + 1, 0);
-  for (const DetPiece& pc : pieces)
-    for (int col = std::max(pc.y, 0); col < std::min(pc.y + W, c->n2); ++col) cnt[(size_t)(pc.mpk * (long long)c->n2 + col + 1)]++;
-  for (long long i = 0; i < ncol; ++i) cnt[(size_t)i + 1] += cnt[(size_t)i];
-  std::vector<int> lists((size_t)cnt[(size_t)ncol]);
+  // per (peak, column, band of W rows): the pieces that reach into it, in
+  // piece order (a pixel's candidates; the sum takes those covering it)
+  const int nband = (c->n1 + W - 1) / W;
+  const long long nkey = (long long)c->D * c->n2 * nband;
+  std::vector<int> cnt((size_t)nkey + 1, 0);
+  auto each_key = [&](const DetPiece& pc, auto&& fn) {
+    const int b0 = std::max(pc.row0, 0) / W, b1 = (std::min(pc.row0 + pc.rows, c->n1) - 1) / W;
+    if (std::min(pc.row0 + pc.rows, c->n1) <= std::max(pc.row0, 0)) return;
+    for (int col = std::max(pc.y, 0); col < std::min(pc.y + W, c->n2); ++col)
+      for (int b = b0; b <= b1; ++b) fn(((long long)pc.mpk * c->n2 + col) * nband + b);
+  };
+  for (const DetPiece& pc : pieces) each_key(pc, [&](long long k) { cnt[(size_t)k + 1]++; });
+  for (long long i = 0; i < nkey; ++i) cnt[(size_t)i + 1] += cnt[(size_t)i];
+  std::vector<int> lists((size_t)cnt[(size_t)nkey]);
   {
     std::vector<int> fill(cnt.begin(), cnt.end() - 1);
-    for (size_t p = 0; p < pieces.size(); ++p) {
-      const DetPiece& pc = pieces[p];
-      for (int col = std::max(pc.y, 0); col < std::min(pc.y + W, c->n2); ++col)
-        lists[(size_t)fill[(size_t)(pc.mpk * (long long)c->n2 + col)]++] = (int)p;
-    }
+    for (size_t p = 0; p < pieces.size(); ++p)
+      each_key(pieces[p], [&](long long k) { lists[(size_t)fill[(size_t)k]++] = (int)p; });
   }
   // device copies: one block of tables, and the pool (kept if large enough)
   Carver cv;

@@ -438,7 +438,8 @@ __global__ void loss_reduce_kernel(const double* __restrict__ part, long long n,
 // ----------------------------------------------------------------------------
 // The deterministic gradient (A7): acc_m(row, col) = the sum, in piece
 // order, of the pieces covering that pixel (a piece holds the gradient rows
-// one block wrote back for a run of frames of one column strip; DetPlan).
+// one block wrote back for a run of frames of one column strip; DetPlan),
+// the candidates listed per (peak, column, band of w rows).
 // One thread per pixel of the D object-sized accumulators, consecutive
 // threads on consecutive columns; every pixel is written, so acc needs no
 // clearing before.
@@ -448,6 +449,7 @@ constexpr int kDetThreads = 256;
 __global__ void __launch_bounds__(kDetThreads) det_reduce_kernel(const DetPlan* __restrict__ plan, cf* acc, int D,
                                                                   int n1, int n2, int w) {
   const long long npix = (long long)n1 * n2;
+  const int nband = (n1 + w - 1) / w;
   const cf* pool = plan->pool;
   const DetPiece* pieces = plan->pieces;
   const int* col_start = plan->col_start;
@@ -457,7 +459,8 @@ __global__ void __launch_bounds__(kDetThreads) det_reduce_kernel(const DetPlan* 
     const int m = (int)(i / npix);
     const long long rc = i - m * npix;
     const int row = (int)(rc / n2), col = (int)(rc - (long long)row * n2);
-    const int k0 = col_start[m * n2 + col], k1 = col_start[m * n2 + col + 1];
+    const long long key = ((long long)m * n2 + col) * nband + row / w;
+    const int k0 = col_start[key], k1 = col_start[key + 1];
     float sx = 0.0f, sy = 0.0f;
     for (int k = k0; k < k1; ++k) {
       const DetPiece pc = pieces[col_piece[k]];

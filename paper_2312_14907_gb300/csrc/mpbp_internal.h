@@ -86,8 +86,9 @@ struct DetPiece {
 };
 
 // The deterministic gradient's plan for one grid size: pieces in order,
-// each block's first piece, and per (peak, column) the pieces covering that
-// column (CSR: col_start[D * n2 + 1], col_piece[...]) in piece order.
+// each block's first piece, and per (peak, column, band of w rows) the
+// pieces reaching into it (CSR: col_start[D * n2 * bands + 1],
+// col_piece[...]) in piece order.
 struct DetPlan {
   cf* pool;
   const DetPiece* pieces;
