@@ -123,6 +123,25 @@ def test_deterministic_step_and_captured_replay(m):
     p.sync_status()
 
 
+def test_deterministic_plan_follows_the_schedule():
+    """At M = 64 the grid follows the resident blocks per SM; each schedule
+    gets its own plan, matches the oracle and repeats its own bits."""
+    n, side, step, _ = GEOM[64]
+    spec, scan = custom_spec(n, 64, side, step, npeaks=2, offset=-6)
+    case = Case(spec, scan=scan, state="perturbed")
+    p, x = _gpu(case)
+    p.set_deterministic(True)
+    grids = set()
+    for b in (1, 2, 4):
+        p.set_schedule(b)
+        grids.add(p.info()["frames_grid"])
+        first = [t.clone() for t in p.loss_grad(*x)]
+        _check(case, first)
+        _same_bits(first, p.loss_grad(*x))
+    assert len(grids) == 3, grids
+    p.sync_status()
+
+
 def test_deterministic_refusals():
     from paper_2312_14907_gb300 import mpbp
     spec, scan = custom_spec(256, 128, 5, 24, npeaks=2, offset=-6)
