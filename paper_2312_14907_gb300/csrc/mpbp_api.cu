@@ -143,7 +143,7 @@ struct mpbp_ctx {
   cf* det_pool = nullptr;
   size_t det_pool_elems = 0, det_pool_cap = 0;
   const DetPlan* det_plan = nullptr;
-  std::vector<void*> det_old;   // earlier plans' buffers (a captured step may use them)
+  std::vector<void*> det_old;   // earlier plans' buffers a captured step may still use
   std::string last_error;
 };
 
@@ -277,7 +277,14 @@ mpbp_status det_prepare(mpbp_ctx* c, int grid) {
   const size_t oS = cv.take<int>(cnt.size());
   const size_t oL = cv.take<int>(std::max<size_t>(lists.size(), 1));
   const size_t oD = cv.take<DetPlan>(1);
-  if (c->det_meta) c->det_old.push_back(c->det_meta);
+  // an earlier plan's buffers: freed now (cudaFree waits for the work that
+  // uses them), or kept while a captured step may still point at them
+  auto retire = [c](void* q) {
+    if (!q) return;
+    if (c->step_exec) c->det_old.push_back(q);
+    else cudaFree(q);
+  };
+  retire(c->det_meta);
   c->det_meta = nullptr;
   c->det_plan = nullptr;
   c->det_grid = 0;
@@ -287,7 +294,7 @@ mpbp_status det_prepare(mpbp_ctx* c, int grid) {
     return fail(c, MPBP_ERR_OOM, "deterministic gradient: tables");
   }
   if ((size_t)off > c->det_pool_cap) {
-    if (c->det_pool) c->det_old.push_back(c->det_pool);
+    retire(c->det_pool);
     c->det_pool = nullptr;
     c->det_pool_cap = 0;
     if (cudaMalloc(&c->det_pool, sizeof(cf) * (size_t)off) != cudaSuccess) {
